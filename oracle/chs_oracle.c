@@ -1,0 +1,762 @@
+/*
+ * chs_oracle.c -- plain, slow CPU oracle for the chaos-indicator hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or helper with the CUDA library: every formula here
+ * is written out again from the paper (arXiv 2507.00622, "Chaoticus") and
+ * from the textbook definitions of the indicators the paper cites.
+ *
+ * Arithmetic: IEEE double, compiled with -ffp-contract=off so that every
+ * expression is evaluated exactly in the order written.
+ *
+ * Layout of every ensemble array: structure of arrays, a[c * n + o] for
+ * component c of orbit o.  Phase-space vectors are ordered (q_1..q_N,
+ * p_1..p_N); deviation vector j occupies components [j*d, (j+1)*d) of w.
+ *
+ * What each routine follows:
+ *   o_energy / o_rhs / o_hessian   Hamiltonians and Hamilton's equations:
+ *                                  Henon-Heiles (Eqs. Ham_HH, ham_eqs_HH),
+ *                                  FPUT chain with fixed ends (Eqs. ham_FPU,
+ *                                  ham_eqs_FPU and q_0 = q_{N+1} = 0), the
+ *                                  3-DOF quartic oscillator, and the harmonic
+ *                                  and inverted test oscillators.
+ *   o_integrate                    classic fixed-step RK4 (the configs' fixed
+ *                                  step integrator in place of the paper's
+ *                                  DOP8, Sec. Functionalities) on the joint
+ *                                  system (x, w_1..w_k, L): deviation vectors
+ *                                  obey the variational equations (Sec.
+ *                                  Statement of need), are renormalised after
+ *                                  every step (the "normalization of the
+ *                                  deviation vectors" item of Sec.
+ *                                  Functionalities) and L is the Lagrangian
+ *                                  descriptor M_p = int sum_i |dx_i/dt|^p dt
+ *                                  (Sec. Statement of need, refs mancho2013,
+ *                                  lopesino2017).  A 4th-order Yoshida
+ *                                  splitting with its tangent map is kept as
+ *                                  an independent cross-check integrator.
+ *   o_indicators                   SALI (refs Skokos2001/03/04) and GALI_k as
+ *                                  the product of the singular values of the
+ *                                  d x k matrix of unit deviation vectors,
+ *                                  from a one-sided Jacobi SVD (GALI item of
+ *                                  Sec. Functionalities, ref Skokos2008).
+ *   o_ld_indicators                LD-based indicators D_L and S_L from grid
+ *                                  neighbours (LD-indicator and neighbouring-
+ *                                  trajectory items of Sec. Functionalities).
+ *   o_lyapunov                     Lyapunov spectrum by periodic QR (modified
+ *                                  Gram-Schmidt) of the 2N deviation vectors
+ *                                  (Lyapunov item of Sec. Functionalities and
+ *                                  the FPU example, Sec. Examples).
+ *   o_grid_ics / o_fput_mode_ics   initial conditions: the x = 0 section grid
+ *                                  of Henon-Heiles and normal-mode FPUT states
+ *                                  scaled onto an energy shell.
+ *   o_seed_vectors                 deviation vectors uniform in [-1, 1) from
+ *                                  the SplitMix64 generator (Steele, Lea and
+ *                                  Flood, OOPSLA 2014), then normalised.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { O_HENON_HEILES = 1, O_FPUT = 2, O_QUARTIC3 = 3, O_HARMONIC = 100, O_INVERTED = 101 };
+enum { OS_OK = 0, OS_FORBIDDEN = 1, OS_ESCAPED = 2, OS_NONFINITE = 3, OS_ENERGY_DRIFT = 4 };
+enum { OI_RK4 = 0, OI_YOSHIDA4 = 1 };
+
+typedef struct {
+    int model;
+    int n_dof;
+    double kk;     /* FPUT linear spring constant k */
+    double alpha;  /* FPUT cubic coefficient */
+    double beta;   /* FPUT quartic coefficient */
+    double eps;    /* quartic-oscillator coupling */
+} o_system;
+
+typedef struct {
+    double dt;
+    int64_t n_steps;
+    int64_t step0;        /* absolute index of the last step taken before this call */
+    int n_dev;            /* number k of deviation vectors */
+    int renorm;           /* 1: normalise every deviation vector after each step */
+    int sample_every;     /* health checks at absolute steps divisible by this */
+    int qr_every;         /* Lyapunov: QR at steps divisible by this (and the last) */
+    int integrator;       /* OI_RK4 or OI_YOSHIDA4 */
+    double ld_p;          /* exponent p of the LD; 0 switches the LD off */
+    double escape_r2;     /* escape when sum_i q_i^2 exceeds this; 0 = off */
+    double dh_limit;      /* ENERGY_DRIFT when |H - H0| exceeds this; 0 = off */
+} o_params;
+
+/* ------------------------------------------------------------------------ */
+/* Hamiltonians                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Spring potential of the FPUT chain, per bond: k/2 r^2 + alpha/3 r^3 + beta/4 r^4 (Eq. ham_FPU). */
+static double fput_bond_v(const o_system* s, double r)
+{
+    return s->kk / 2.0 * r * r + s->alpha / 3.0 * r * r * r + s->beta / 4.0 * r * r * r * r;
+}
+
+/* FPUT bond elongation D_i = q_i - q_{i-1}, i = 1..N+1, with q_0 = q_{N+1} = 0. */
+static double fput_bond(const double* q, int N, int i)
+{
+    double qi = (i >= 1 && i <= N) ? q[i - 1] : 0.0;
+    double qm = (i - 1 >= 1 && i - 1 <= N) ? q[i - 2] : 0.0;
+    return qi - qm;
+}
+
+double o_energy(const o_system* s, const double* x)
+{
+    int N = s->n_dof;
+    const double* q = x;
+    const double* p = x + N;
+    double T = 0.0;
+    for (int i = 0; i < N; ++i) T += p[i] * p[i] / 2.0;
+    double V = 0.0;
+    switch (s->model) {
+    case O_HENON_HEILES:  /* Eq. Ham_HH: 1/2 (x^2 + y^2) + x^2 y - y^3 / 3 */
+        V = (q[0] * q[0] + q[1] * q[1]) / 2.0 + q[0] * q[0] * q[1] - q[1] * q[1] * q[1] / 3.0;
+        break;
+    case O_FPUT:  /* Eq. ham_FPU, summed over the N+1 bonds that the fixed ends create */
+        for (int i = 1; i <= N + 1; ++i) V += fput_bond_v(s, fput_bond(q, N, i));
+        break;
+    case O_QUARTIC3:  /* 1/2 sum q_i^2 + eps (q1^2 q2^2 + q2^2 q3^2 + q1^2 q3^2) */
+        V = (q[0] * q[0] + q[1] * q[1] + q[2] * q[2]) / 2.0
+          + s->eps * (q[0] * q[0] * q[1] * q[1] + q[1] * q[1] * q[2] * q[2] + q[0] * q[0] * q[2] * q[2]);
+        break;
+    case O_HARMONIC:
+        for (int i = 0; i < N; ++i) V += q[i] * q[i] / 2.0;
+        break;
+    case O_INVERTED:  /* 1/2 (p1^2 - q1^2) + 1/2 (p2^2 + q2^2) */
+        V = -q[0] * q[0] / 2.0 + q[1] * q[1] / 2.0;
+        break;
+    }
+    return T + V;
+}
+
+/* Gradient of the potential, dV/dq_i. */
+static void o_grad_v(const o_system* s, const double* q, double* g)
+{
+    int N = s->n_dof;
+    switch (s->model) {
+    case O_HENON_HEILES:  /* from Eq. ham_eqs_HH: p_x' = -x - 2xy, p_y' = -y - x^2 + y^2 */
+        g[0] = q[0] + 2.0 * q[0] * q[1];
+        g[1] = q[1] + q[0] * q[0] - q[1] * q[1];
+        break;
+    case O_FPUT:  /* from Eq. ham_eqs_FPU: dV/dq_i = V'(D_i) - V'(D_{i+1}) */
+        for (int i = 1; i <= N; ++i) {
+            double a = fput_bond(q, N, i), b = fput_bond(q, N, i + 1);
+            double fa = s->kk * a + s->alpha * a * a + s->beta * a * a * a;
+            double fb = s->kk * b + s->alpha * b * b + s->beta * b * b * b;
+            g[i - 1] = fa - fb;
+        }
+        break;
+    case O_QUARTIC3: {
+        double S = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        for (int i = 0; i < 3; ++i) g[i] = q[i] + 2.0 * s->eps * q[i] * (S - q[i] * q[i]);
+        break;
+    }
+    case O_HARMONIC:
+        for (int i = 0; i < N; ++i) g[i] = q[i];
+        break;
+    case O_INVERTED:
+        g[0] = -q[0];
+        g[1] = q[1];
+        break;
+    }
+}
+
+/* Hamilton's equations: dq/dt = p, dp/dt = -grad V. */
+void o_rhs(const o_system* s, const double* x, double* f)
+{
+    int N = s->n_dof;
+    double g[256];
+    o_grad_v(s, x, g);
+    for (int i = 0; i < N; ++i) {
+        f[i] = x[N + i];
+        f[N + i] = -g[i];
+    }
+}
+
+/* Dense Hessian of the potential, Hm[i * N + j] = d^2 V / dq_i dq_j. */
+void o_hessian(const o_system* s, const double* q, double* Hm)
+{
+    int N = s->n_dof;
+    for (int i = 0; i < N * N; ++i) Hm[i] = 0.0;
+    switch (s->model) {
+    case O_HENON_HEILES:
+        Hm[0] = 1.0 + 2.0 * q[1];
+        Hm[1] = 2.0 * q[0];
+        Hm[2] = 2.0 * q[0];
+        Hm[3] = 1.0 - 2.0 * q[1];
+        break;
+    case O_FPUT:
+        /* bond i (D_i) couples q_{i-1} and q_i with stiffness c_i = V''(D_i) */
+        for (int i = 1; i <= N + 1; ++i) {
+            double r = fput_bond(q, N, i);
+            double c = s->kk + 2.0 * s->alpha * r + 3.0 * s->beta * r * r;
+            int a = i - 2, b = i - 1; /* zero-based indices of q_{i-1}, q_i */
+            if (a >= 0) Hm[a * N + a] += c;
+            if (b <= N - 1) Hm[b * N + b] += c;
+            if (a >= 0 && b <= N - 1) {
+                Hm[a * N + b] -= c;
+                Hm[b * N + a] -= c;
+            }
+        }
+        break;
+    case O_QUARTIC3: {
+        double S = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                Hm[i * 3 + j] = (i == j) ? 1.0 + 2.0 * s->eps * (S - q[i] * q[i])
+                                         : 4.0 * s->eps * q[i] * q[j];
+        break;
+    }
+    case O_HARMONIC:
+        for (int i = 0; i < N; ++i) Hm[i * N + i] = 1.0;
+        break;
+    case O_INVERTED:
+        Hm[0] = -1.0;
+        Hm[3] = 1.0;
+        break;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Joint system (x, w_1..w_k, L) and its RK4 step                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const o_system* s;
+    int d, k, ld;
+    double ld_p;
+    double* Hm;   /* N*N scratch */
+} o_joint;
+
+/* F(z): z = [x | w_1 | ... | w_k | L].  Variational equations: for w = (dq, dp),
+ * d(dq)/dt = dp and d(dp)/dt = -Hess V(q) dq.  LD integrand: sum_i |f_i(x)|^p. */
+static void o_joint_f(const o_joint* J, const double* z, double* dz)
+{
+    int d = J->d, N = d / 2;
+    o_rhs(J->s, z, dz);
+    o_hessian(J->s, z, J->Hm);
+    for (int j = 0; j < J->k; ++j) {
+        const double* w = z + d + j * d;
+        double* dw = dz + d + j * d;
+        for (int i = 0; i < N; ++i) dw[i] = w[N + i];
+        for (int i = 0; i < N; ++i) {
+            double acc = 0.0;
+            for (int m = 0; m < N; ++m) acc += J->Hm[i * N + m] * w[m];
+            dw[N + i] = -acc;
+        }
+    }
+    if (J->ld) {
+        double acc = 0.0;
+        for (int i = 0; i < d; ++i) acc += pow(fabs(dz[i]), J->ld_p);
+        dz[d + J->k * d] = acc;
+    }
+}
+
+/* Classic RK4: k1 = F(z), k2 = F(z + h/2 k1), k3 = F(z + h/2 k2), k4 = F(z + h k3),
+ * z <- z + h/6 (k1 + 2 k2 + 2 k3 + k4). */
+static void o_rk4_step(const o_joint* J, double* z, int D, double h, double* k1, double* k2,
+                       double* k3, double* k4, double* zt)
+{
+    o_joint_f(J, z, k1);
+    for (int i = 0; i < D; ++i) zt[i] = z[i] + h / 2.0 * k1[i];
+    o_joint_f(J, zt, k2);
+    for (int i = 0; i < D; ++i) zt[i] = z[i] + h / 2.0 * k2[i];
+    o_joint_f(J, zt, k3);
+    for (int i = 0; i < D; ++i) zt[i] = z[i] + h * k3[i];
+    o_joint_f(J, zt, k4);
+    for (int i = 0; i < D; ++i) z[i] = z[i] + h / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+/* 4th-order Yoshida composition of the drift-kick-drift leapfrog, for
+ * separable H = |p|^2/2 + V(q), carried over to the deviation vectors by its
+ * tangent map (drift: dq += tau dp; kick: dp -= tau Hess V(q) dq).  Yoshida
+ * (Phys. Lett. A 150, 1990): w1 = 1/(2 - 2^(1/3)), w0 = -2^(1/3)/(2 - 2^(1/3)). */
+static void o_yoshida_drift(const o_joint* J, double* z, double tau)
+{
+    int d = J->d, N = d / 2;
+    for (int i = 0; i < N; ++i) z[i] += tau * z[N + i];
+    for (int j = 0; j < J->k; ++j) {
+        double* w = z + d + j * d;
+        for (int i = 0; i < N; ++i) w[i] += tau * w[N + i];
+    }
+}
+
+static void o_yoshida_kick(const o_joint* J, double* z, double tau)
+{
+    int d = J->d, N = d / 2;
+    double g[256];
+    o_grad_v(J->s, z, g);
+    o_hessian(J->s, z, J->Hm);
+    for (int j = 0; j < J->k; ++j) {
+        double* w = z + d + j * d;
+        for (int i = 0; i < N; ++i) {
+            double acc = 0.0;
+            for (int m = 0; m < N; ++m) acc += J->Hm[i * N + m] * w[m];
+            w[N + i] -= tau * acc;
+        }
+    }
+    for (int i = 0; i < N; ++i) z[N + i] -= tau * g[i];
+}
+
+static void o_yoshida_step(const o_joint* J, double* z, double h)
+{
+    double cbrt2 = cbrt(2.0);
+    double w1 = 1.0 / (2.0 - cbrt2);
+    double w0 = -cbrt2 / (2.0 - cbrt2);
+    double c[3] = {w1, w0, w1};
+    for (int m = 0; m < 3; ++m) {
+        o_yoshida_drift(J, z, c[m] * h / 2.0);
+        o_yoshida_kick(J, z, c[m] * h);
+        o_yoshida_drift(J, z, c[m] * h / 2.0);
+    }
+}
+
+static double o_norm(const double* v, int d)
+{
+    double acc = 0.0;
+    for (int i = 0; i < d; ++i) acc += v[i] * v[i];
+    return sqrt(acc);
+}
+
+static int o_all_finite(const double* z, int D)
+{
+    for (int i = 0; i < D; ++i)
+        if (!isfinite(z[i])) return 0;
+    return 1;
+}
+
+static int o_threads(int nthreads)
+{
+#ifdef _OPENMP
+    return nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+int o_max_threads(void) { return o_threads(0); }
+
+/* ------------------------------------------------------------------------ */
+/* Ensemble set-up                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64: the state advances by the golden-ratio increment and each output
+ * is the published finaliser applied to the new state. */
+uint64_t o_splitmix64_next(uint64_t* state)
+{
+    uint64_t z = (*state += 0x9e3779b97f4a7c15ULL);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+/* Component c of deviation vector j of orbit o is the m-th output (m = 1, 2, ...)
+ * of the SplitMix64 stream that starts from `seed`, with m = (o*k + j)*d + c + 1,
+ * mapped to [-1, 1) through its top 53 bits.  Each vector is then normalised. */
+void o_seed_vectors(uint64_t seed, int64_t n, int k, int d, double* w)
+{
+    for (int64_t o = 0; o < n; ++o) {
+        for (int j = 0; j < k; ++j) {
+            double v[256];
+            for (int c = 0; c < d; ++c) {
+                uint64_t st = seed + (uint64_t)(((uint64_t)o * (uint64_t)k + (uint64_t)j) * (uint64_t)d + (uint64_t)c)
+                                     * 0x9e3779b97f4a7c15ULL;
+                uint64_t z = o_splitmix64_next(&st);
+                double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+                v[c] = 2.0 * u - 1.0;
+            }
+            double nr = o_norm(v, d);
+            for (int c = 0; c < d; ++c) w[((int64_t)j * d + c) * n + o] = v[c] / nr;
+        }
+    }
+}
+
+/* Henon-Heiles initial conditions on the x = 0 surface of section: a
+ * cell-centred ny x npy grid over [y0, y1] x [py0, py1], orbit index
+ * o = iy * npy + ipy, p_x >= 0 fixed by H = E (Eq. Ham_HH at x = 0):
+ *   p_x^2 = 2E - p_y^2 - y^2 + 2 y^3 / 3.
+ * A negative radicand marks the cell FORBIDDEN (state set to NaN). */
+void o_grid_ics(double E, double y0, double y1, int ny, double py0, double py1, int npy,
+                double* ics, int32_t* status)
+{
+    int64_t n = (int64_t)ny * npy;
+    double dy = (y1 - y0) / ny;
+    double dpy = (py1 - py0) / npy;
+    for (int iy = 0; iy < ny; ++iy) {
+        for (int ip = 0; ip < npy; ++ip) {
+            int64_t o = (int64_t)iy * npy + ip;
+            double y = y0 + ((double)iy + 0.5) * dy;
+            double py = py0 + ((double)ip + 0.5) * dpy;
+            double rad = 2.0 * E - py * py - y * y + 2.0 * y * y * y / 3.0;
+            if (rad < 0.0) {
+                status[o] = OS_FORBIDDEN;
+                for (int c = 0; c < 4; ++c) ics[c * n + o] = NAN;
+            } else {
+                status[o] = OS_OK;
+                ics[0 * n + o] = 0.0;
+                ics[1 * n + o] = y;
+                ics[2 * n + o] = sqrt(rad);
+                ics[3 * n + o] = py;
+            }
+        }
+    }
+}
+
+/* FPUT initial conditions from normal-mode amplitudes (Q_m, P_m), m = 1..N:
+ *   q_i = sqrt(2/(N+1)) sum_m Q_m sin(i m pi/(N+1)),  p_i likewise from P_m,
+ * then the whole state is scaled by s > 0 so that H(s x) = E_o.  With
+ * alpha = 0, H(s x) = s^2 H2 + s^4 H4 and s^2 = 2E / (H2 + sqrt(H2^2 + 4 H4 E)).
+ * Returns -1 when alpha != 0 (no closed form). */
+int o_fput_mode_ics(const o_system* s, int64_t n, const double* Qm, const double* Pm,
+                    const double* E, double* ics)
+{
+    int N = s->n_dof;
+    if (s->alpha != 0.0) return -1;
+    double pi = acos(-1.0);
+    for (int64_t o = 0; o < n; ++o) {
+        double x[512];
+        for (int i = 1; i <= N; ++i) {
+            double aq = 0.0, ap = 0.0;
+            for (int m = 1; m <= N; ++m) {
+                double sn = sin((double)i * (double)m * pi / (double)(N + 1));
+                aq += Qm[(int64_t)(m - 1) * n + o] * sn;
+                ap += Pm[(int64_t)(m - 1) * n + o] * sn;
+            }
+            x[i - 1] = sqrt(2.0 / (double)(N + 1)) * aq;
+            x[N + i - 1] = sqrt(2.0 / (double)(N + 1)) * ap;
+        }
+        double H2 = 0.0, H4 = 0.0;
+        for (int i = 0; i < N; ++i) H2 += x[N + i] * x[N + i] / 2.0;
+        for (int i = 1; i <= N + 1; ++i) {
+            double r = fput_bond(x, N, i);
+            H2 += s->kk / 2.0 * r * r;
+            H4 += s->beta / 4.0 * r * r * r * r;
+        }
+        double s2 = 2.0 * E[o] / (H2 + sqrt(H2 * H2 + 4.0 * H4 * E[o]));
+        double sc = sqrt(s2);
+        for (int c = 0; c < 2 * N; ++c) ics[(int64_t)c * n + o] = sc * x[c];
+    }
+    return 0;
+}
+
+/* Initial ensemble: x <- ics, w <- w_in (or seeded), normalised when renorm
+ * is set, L <- 0, H0 <- H(x), dH_max <- 0, n_exec <- 0.  A cell whose
+ * ic_status is not OK keeps that status; a non-finite state becomes NONFINITE. */
+void o_ensemble_init(const o_system* s, const o_params* prm, int64_t n, const double* ics,
+                     const int32_t* ic_status, const double* w_in, uint64_t seed, double* x,
+                     double* w, double* ld, double* h0, double* dh_max, int64_t* n_exec,
+                     int32_t* status)
+{
+    int d = 2 * s->n_dof, k = prm->n_dev;
+    if (k > 0) {
+        if (w_in)
+            memcpy(w, w_in, sizeof(double) * (size_t)k * d * n);
+        else
+            o_seed_vectors(seed, n, k, d, w);
+    }
+    for (int64_t o = 0; o < n; ++o) {
+        double xo[512];
+        for (int c = 0; c < d; ++c) {
+            x[c * n + o] = ics[c * n + o];
+            xo[c] = ics[c * n + o];
+        }
+        if (k > 0 && prm->renorm) {
+            for (int j = 0; j < k; ++j) {
+                double v[512];
+                for (int c = 0; c < d; ++c) v[c] = w[((int64_t)j * d + c) * n + o];
+                double nr = o_norm(v, d);
+                for (int c = 0; c < d; ++c) w[((int64_t)j * d + c) * n + o] = v[c] / nr;
+            }
+        }
+        if (ld) ld[o] = 0.0;
+        dh_max[o] = 0.0;
+        n_exec[o] = 0;
+        int32_t st = ic_status ? ic_status[o] : OS_OK;
+        if (st == OS_OK && !o_all_finite(xo, d)) st = OS_NONFINITE;
+        status[o] = st;
+        h0[o] = (st == OS_OK) ? o_energy(s, xo) : NAN;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Integration                                                               */
+/* ------------------------------------------------------------------------ */
+
+/* Advance every orbit by prm->n_steps steps.  After each step: renormalise
+ * the vectors (if prm->renorm), then freeze the orbit as ESCAPED if
+ * sum_i q_i^2 > escape_r2.  At absolute steps divisible by sample_every:
+ * freeze as NONFINITE on any non-finite value, update dH_max = max |H - H0|,
+ * and freeze as ENERGY_DRIFT when it exceeds dh_limit.  A frozen orbit keeps
+ * the state of the step at which it froze; n_exec counts executed steps. */
+void o_integrate(const o_system* s, const o_params* prm, int64_t n, double* x, double* w,
+                 double* ld, const double* h0, double* dh_max, int64_t* n_exec, int32_t* status,
+                 int nthreads)
+{
+    int d = 2 * s->n_dof, k = prm->n_dev, N = s->n_dof;
+    int use_ld = (prm->ld_p != 0.0) && ld != NULL;
+    int D = d + k * d + (use_ld ? 1 : 0);
+    int nt = o_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t o = 0; o < n; ++o) {
+        if (status[o] != OS_OK) continue;
+        double* z = (double*)malloc(sizeof(double) * (size_t)D * 6);
+        double* Hm = (double*)malloc(sizeof(double) * (size_t)N * N);
+        double *k1 = z + D, *k2 = z + 2 * D, *k3 = z + 3 * D, *k4 = z + 4 * D, *zt = z + 5 * D;
+        o_joint J = {s, d, k, use_ld, prm->ld_p, Hm};
+        for (int c = 0; c < d; ++c) z[c] = x[c * n + o];
+        for (int j = 0; j < k; ++j)
+            for (int c = 0; c < d; ++c) z[d + j * d + c] = w[((int64_t)j * d + c) * n + o];
+        if (use_ld) z[D - 1] = ld[o];
+        double dhm = dh_max[o];
+        int32_t st = OS_OK;
+        int64_t done = 0;
+        for (int64_t sidx = 1; sidx <= prm->n_steps; ++sidx) {
+            if (prm->integrator == OI_YOSHIDA4)
+                o_yoshida_step(&J, z, prm->dt);
+            else
+                o_rk4_step(&J, z, D, prm->dt, k1, k2, k3, k4, zt);
+            done = sidx;
+            int64_t abs_step = prm->step0 + sidx;
+            if (prm->renorm) {
+                for (int j = 0; j < k; ++j) {
+                    double* v = z + d + j * d;
+                    double nr = o_norm(v, d);
+                    for (int c = 0; c < d; ++c) v[c] = v[c] / nr;
+                }
+            }
+            if (prm->escape_r2 > 0.0) {
+                double r2 = 0.0;
+                for (int i = 0; i < N; ++i) r2 += z[i] * z[i];
+                if (r2 > prm->escape_r2) {
+                    st = OS_ESCAPED;
+                    break;
+                }
+            }
+            if (prm->sample_every > 0 && abs_step % prm->sample_every == 0) {
+                if (!o_all_finite(z, D)) {
+                    st = OS_NONFINITE;
+                    break;
+                }
+                double dH = fabs(o_energy(s, z) - h0[o]);
+                if (dH > dhm) dhm = dH;
+                if (prm->dh_limit > 0.0 && dH > prm->dh_limit) {
+                    st = OS_ENERGY_DRIFT;
+                    break;
+                }
+            }
+        }
+        for (int c = 0; c < d; ++c) x[c * n + o] = z[c];
+        for (int j = 0; j < k; ++j)
+            for (int c = 0; c < d; ++c) w[((int64_t)j * d + c) * n + o] = z[d + j * d + c];
+        if (use_ld) ld[o] = z[D - 1];
+        dh_max[o] = dhm;
+        n_exec[o] += done;
+        status[o] = st;
+        free(Hm);
+        free(z);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Indicators                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* One-sided Jacobi SVD (Hestenes 1958) of the d x k matrix A (column-major,
+ * A[c * d + i] = row i of column c): plane rotations of column pairs until
+ * every pair is orthogonal to working precision; the singular values are the
+ * final column norms (returned unsorted). */
+void o_jacobi_sv(int d, int k, const double* A, double* sv)
+{
+    double* U = (double*)malloc(sizeof(double) * (size_t)d * k);
+    memcpy(U, A, sizeof(double) * (size_t)d * k);
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        int rotated = 0;
+        for (int p = 0; p < k - 1; ++p) {
+            for (int q = p + 1; q < k; ++q) {
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < d; ++i) {
+                    al += U[p * d + i] * U[p * d + i];
+                    be += U[q * d + i] * U[q * d + i];
+                    ga += U[p * d + i] * U[q * d + i];
+                }
+                if (fabs(ga) <= 1e-15 * sqrt(al * be) || ga == 0.0) continue;
+                rotated = 1;
+                double zeta = (be - al) / (2.0 * ga);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+                double c = 1.0 / sqrt(1.0 + t * t);
+                double sn = c * t;
+                for (int i = 0; i < d; ++i) {
+                    double up = U[p * d + i], uq = U[q * d + i];
+                    U[p * d + i] = c * up - sn * uq;
+                    U[q * d + i] = sn * up + c * uq;
+                }
+            }
+        }
+        if (!rotated) break;
+    }
+    for (int c = 0; c < k; ++c) {
+        double acc = 0.0;
+        for (int i = 0; i < d; ++i) acc += U[c * d + i] * U[c * d + i];
+        sv[c] = sqrt(acc);
+    }
+    free(U);
+}
+
+/* Per orbit, from the k deviation vectors (each first normalised):
+ *   SALI = min(|w1 + w2|, |w1 - w2|)                      (needs k >= 2)
+ *   GALI_m = product of the singular values of [w1..wm]   for m = 2..k
+ *   label: status OK -> 1 (chaotic) if SALI < sali_threshold else 0 (regular);
+ *          ESCAPED -> 2; any other status -> -1.
+ * FORBIDDEN orbits get NaN indicators. */
+void o_indicators(const o_system* s, int64_t n, int k, const double* w, const int32_t* status,
+                  double sali_threshold, double* sali, double* gali, int8_t* label)
+{
+    int d = 2 * s->n_dof;
+    double* A = (double*)malloc(sizeof(double) * (size_t)d * (k > 0 ? k : 1));
+    double* svals = (double*)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    for (int64_t o = 0; o < n; ++o) {
+        for (int j = 0; j < k; ++j) {
+            for (int c = 0; c < d; ++c) A[j * d + c] = w[((int64_t)j * d + c) * n + o];
+            double nr = o_norm(A + j * d, d);
+            for (int c = 0; c < d; ++c) A[j * d + c] = A[j * d + c] / nr;
+        }
+        int forb = (status[o] == OS_FORBIDDEN);
+        double sv = NAN;
+        if (k >= 2 && !forb) {
+            double sp[512], sm[512];
+            for (int c = 0; c < d; ++c) {
+                sp[c] = A[c] + A[d + c];
+                sm[c] = A[c] - A[d + c];
+            }
+            double a = o_norm(sp, d), b = o_norm(sm, d);
+            sv = a < b ? a : b;
+        }
+        if (sali) sali[o] = sv;
+        if (gali) {
+            for (int m = 2; m <= k; ++m) {
+                double g = NAN;
+                if (!forb) {
+                    o_jacobi_sv(d, m, A, svals);
+                    g = 1.0;
+                    for (int c = 0; c < m; ++c) g *= svals[c];
+                }
+                gali[(int64_t)(m - 2) * n + o] = g;
+            }
+        }
+        if (label) {
+            int8_t lb;
+            if (status[o] == OS_OK)
+                lb = (sv < sali_threshold) ? 1 : 0;
+            else if (status[o] == OS_ESCAPED)
+                lb = 2;
+            else
+                lb = -1;
+            label[o] = lb;
+        }
+    }
+    free(svals);
+    free(A);
+}
+
+/* LD-based indicators on the ny x npy section grid (o = iy * npy + ipy), with
+ * n = 2 grid directions and a one-cell offset sigma:
+ *   D_L = 1/(2n) sum_i |LD(x + s e_i) - LD(x - s e_i)| / LD(x)
+ *   S_L = 1/n    sum_i |2 - (LD(x + s e_i) + LD(x - s e_i)) / LD(x)|
+ * NaN on the grid border and wherever the cell or one of its four
+ * neighbours does not have status OK. */
+void o_ld_indicators(int ny, int npy, const double* ld, const int32_t* status, double* dl, double* sl)
+{
+    for (int iy = 0; iy < ny; ++iy) {
+        for (int ip = 0; ip < npy; ++ip) {
+            int64_t o = (int64_t)iy * npy + ip;
+            dl[o] = NAN;
+            sl[o] = NAN;
+            if (iy == 0 || iy == ny - 1 || ip == 0 || ip == npy - 1) continue;
+            int64_t nb[4] = {o - npy, o + npy, o - 1, o + 1};
+            int ok = status[o] == OS_OK;
+            for (int m = 0; m < 4; ++m) ok = ok && status[nb[m]] == OS_OK;
+            if (!ok) continue;
+            double c = ld[o];
+            double Dsum = fabs(ld[o + npy] - ld[o - npy]) / c + fabs(ld[o + 1] - ld[o - 1]) / c;
+            double Ssum = fabs(2.0 - (ld[o + npy] + ld[o - npy]) / c)
+                        + fabs(2.0 - (ld[o + 1] + ld[o - 1]) / c);
+            dl[o] = Dsum / 4.0;
+            sl[o] = Ssum / 2.0;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lyapunov spectrum by periodic QR                                          */
+/* ------------------------------------------------------------------------ */
+
+/* d deviation vectors start as the identity basis and follow the variational
+ * equations under RK4 together with the orbit.  At every step divisible by
+ * qr_every, and at the last step, the matrix W of vectors (columns) is
+ * factorised W = QR by modified Gram-Schmidt (so R_ii > 0); S_i += ln R_ii
+ * and W <- Q.  Finally lambda_i = S_i / (n_steps * dt), in column order.
+ * NONFINITE at a health check freezes the orbit and sets lambda to NaN. */
+void o_lyapunov(const o_system* s, const o_params* prm, int64_t n, const double* ics,
+                const int32_t* ic_status, double* lambda, int32_t* status, int nthreads)
+{
+    int d = 2 * s->n_dof, N = s->n_dof;
+    int D = d + d * d;
+    int nt = o_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t o = 0; o < n; ++o) {
+        int32_t st = ic_status ? ic_status[o] : OS_OK;
+        if (st != OS_OK) {
+            status[o] = st;
+            for (int i = 0; i < d; ++i) lambda[(int64_t)i * n + o] = NAN;
+            continue;
+        }
+        double* z = (double*)malloc(sizeof(double) * (size_t)D * 6);
+        double* Hm = (double*)malloc(sizeof(double) * (size_t)N * N);
+        double* S = (double*)calloc((size_t)d, sizeof(double));
+        double *k1 = z + D, *k2 = z + 2 * D, *k3 = z + 3 * D, *k4 = z + 4 * D, *zt = z + 5 * D;
+        o_joint J = {s, d, d, 0, 0.0, Hm};
+        for (int c = 0; c < d; ++c) z[c] = ics[(int64_t)c * n + o];
+        for (int j = 0; j < d; ++j)
+            for (int c = 0; c < d; ++c) z[d + j * d + c] = (c == j) ? 1.0 : 0.0;
+        for (int64_t sidx = 1; sidx <= prm->n_steps; ++sidx) {
+            if (prm->integrator == OI_YOSHIDA4)
+                o_yoshida_step(&J, z, prm->dt);
+            else
+                o_rk4_step(&J, z, D, prm->dt, k1, k2, k3, k4, zt);
+            if ((prm->qr_every > 0 && sidx % prm->qr_every == 0) || sidx == prm->n_steps) {
+                for (int j = 0; j < d; ++j) {
+                    double* wj = z + d + j * d;
+                    for (int i = 0; i < j; ++i) {
+                        double* qi = z + d + i * d;
+                        double r = 0.0;
+                        for (int c = 0; c < d; ++c) r += qi[c] * wj[c];
+                        for (int c = 0; c < d; ++c) wj[c] = wj[c] - r * qi[c];
+                    }
+                    double rjj = o_norm(wj, d);
+                    for (int c = 0; c < d; ++c) wj[c] = wj[c] / rjj;
+                    S[j] += log(rjj);
+                }
+            }
+            if (prm->sample_every > 0 && sidx % prm->sample_every == 0 && !o_all_finite(z, D)) {
+                st = OS_NONFINITE;
+                break;
+            }
+        }
+        double T = (double)prm->n_steps * prm->dt;
+        for (int i = 0; i < d; ++i) lambda[(int64_t)i * n + o] = (st == OS_OK) ? S[i] / T : NAN;
+        status[o] = st;
+        free(S);
+        free(Hm);
+        free(z);
+    }
+}
