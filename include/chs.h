@@ -1,0 +1,222 @@
+/*
+ * chs.h -- C ABI of the GB300 chaos-indicator library (libchs.so).
+ *
+ * The library integrates large ensembles of Hamiltonian orbits together with
+ * their variational equations and accumulates the chaos indicators described
+ * in "Chaoticus: a parallel approach to the computation of chaos indicators"
+ * (arXiv 2507.00622): SALI, GALI_k, Lagrangian-descriptor (LD) based
+ * indicators and the Lyapunov spectrum by periodic QR (Sec. Functionalities).
+ *
+ * Conventions shared by every entry point
+ *   - Array arguments are DEVICE pointers allocated and owned by the caller.
+ *     The library never frees them and never allocates device memory in a
+ *     call; it keeps nothing beyond the opaque system handle.
+ *   - Ensemble arrays are structure-of-arrays: element (c, o) of an array
+ *     with C components over n orbits is at a[c * n + o].  Phase-space
+ *     vectors are ordered (q_1..q_N, p_1..p_N), d = 2N.  Deviation vector j
+ *     occupies components j*d .. j*d + d - 1 of the vector array.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *     legacy default stream).  Argument errors are detected on the host
+ *     before anything is launched and returned as a chs_status; launch
+ *     failures return CHS_E_CUDA.  No exception crosses the ABI and no
+ *     kernel traps.  chs_last_error() gives a message for the last non-OK
+ *     status returned on the calling thread.
+ *   - Per-orbit failures are written to the orbit's status word
+ *     (CHS_ORBIT_*), never to the return value.
+ *   - All state is FP64 unless chs_params.vec_precision selects FP32
+ *     deviation vectors.
+ */
+#ifndef CHS_H
+#define CHS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CHS_OK = 0,
+    CHS_E_INVALID = 1,     /* bad pointer, size, or parameter */
+    CHS_E_UNSUPPORTED = 2, /* valid request this build does not implement */
+    CHS_E_CUDA = 3,        /* a CUDA launch or runtime call failed */
+    CHS_E_NOMEM = 4,       /* host allocation failed */
+    CHS_E_SIZE = 5         /* a size exceeds a documented maximum */
+} chs_status;
+
+/* Hamiltonian systems.
+ *   CHS_HENON_HEILES  H = (px^2 + py^2)/2 + (x^2 + y^2)/2 + x^2 y - y^3/3
+ *                     (Eq. Ham_HH; equations of motion Eq. ham_eqs_HH).  n_dof = 2.
+ *   CHS_FPUT          FPU(T) chain with fixed ends q_0 = q_{N+1} = 0 (Eqs.
+ *                     ham_FPU, ham_eqs_FPU), params = {k, alpha, beta}; the
+ *                     energy sums the N+1 bonds D_i = q_i - q_{i-1}.
+ *   CHS_QUARTIC3      H = sum (p_i^2 + q_i^2)/2 + eps (q1^2 q2^2 + q2^2 q3^2 +
+ *                     q1^2 q3^2), params = {eps}.  n_dof = 3.
+ *   CHS_HARMONIC      H = sum (p_i^2 + q_i^2)/2 (test system).  n_dof = 2.
+ *   CHS_INVERTED      H = (p1^2 - q1^2)/2 + (p2^2 + q2^2)/2 (test system).  n_dof = 2. */
+typedef enum {
+    CHS_HENON_HEILES = 1,
+    CHS_FPUT = 2,
+    CHS_QUARTIC3 = 3,
+    CHS_HARMONIC = 100,
+    CHS_INVERTED = 101
+} chs_model;
+
+/* Orbit status words. */
+enum {
+    CHS_ORBIT_OK = 0,
+    CHS_ORBIT_FORBIDDEN = 1,    /* no initial condition exists in this cell */
+    CHS_ORBIT_ESCAPED = 2,      /* sum_i q_i^2 exceeded escape_r2; frozen */
+    CHS_ORBIT_NONFINITE = 3,    /* a non-finite value at a health check; frozen */
+    CHS_ORBIT_ENERGY_DRIFT = 4  /* |H - H0| exceeded dh_limit at a health check; frozen */
+};
+
+/* Deviation-vector storage precision. */
+enum { CHS_VEC_FP64 = 0, CHS_VEC_FP32 = 1 };
+
+/* Integration and indicator parameters (plain old data). */
+typedef struct {
+    double dt;               /* fixed RK4 step h */
+    int64_t n_steps;         /* steps to take in this call */
+    int64_t step0;           /* absolute index of the last step already taken */
+    int32_t n_dev;           /* number k of deviation vectors (0..6; must match the ensemble) */
+    int32_t renorm;          /* 1: normalise each deviation vector after every step */
+    int32_t sample_every;    /* health checks at absolute steps divisible by this (0 = never) */
+    int32_t qr_every;        /* Lyapunov: QR of the vectors every qr_every steps and at the end */
+    int32_t vec_precision;   /* CHS_VEC_FP64 or CHS_VEC_FP32 */
+    int32_t reserved;        /* must be 0 */
+    double ld_p;             /* LD exponent p (LD integrand sum_i |dx_i/dt|^p); 0 = no LD */
+    double escape_r2;        /* ESCAPED when sum_i q_i^2 > escape_r2; 0 = off */
+    double dh_limit;         /* ENERGY_DRIFT when |H - H0| > dh_limit; 0 = off */
+    double sali_threshold;   /* label: chaotic when SALI < sali_threshold */
+    uint64_t seed;           /* SplitMix64 seed for device-seeded deviation vectors */
+} chs_params;
+
+/* Resumable ensemble state: caller-owned device arrays over n_orbits orbits.
+ *   x       [d][n]    phase-space state (FP64)
+ *   w       [k*d][n]  deviation vectors, FP64 or FP32 per vec_precision (NULL when k = 0)
+ *   ld      [n]       forward LD accumulator M_p (NULL when ld_p = 0)
+ *   h0      [n]       energy at t = 0
+ *   dh_max  [n]       largest |H - H0| seen at health checks
+ *   n_exec  [n]       integration steps executed so far (frozen orbits stop counting)
+ *   status  [n]       CHS_ORBIT_* */
+typedef struct {
+    int64_t n_orbits;
+    double* x;
+    void* w;
+    double* ld;
+    double* h0;
+    double* dh_max;
+    int64_t* n_exec;
+    int32_t* status;
+} chs_ensemble;
+
+typedef struct chs_system_s* chs_system;
+
+/* Creates a system handle on the current CUDA device.  `params` (host) holds
+ * n_params model constants: FPUT {k, alpha, beta}; QUARTIC3 {eps}; none for
+ * the others.  CHS_E_INVALID for an unknown model or a bad n_dof. */
+chs_status chs_create_system(chs_system* out, chs_model model, int32_t n_dof,
+                             const double* params, int32_t n_params);
+
+/* Destroys a handle created by chs_create_system (NULL is accepted). */
+chs_status chs_destroy_system(chs_system s);
+
+/* Phase-space dimension d = 2N of the system, or -1 for a NULL handle. */
+int32_t chs_system_dim(chs_system s);
+
+/* Henon-Heiles initial conditions on the x = 0 surface of section (Eq. Ham_HH,
+ * Examples of Sec. Examples): a cell-centred ny x npy grid over [y0, y1] x
+ * [py0, py1], orbit o = iy * npy + ipy at y = y0 + (iy + 1/2)(y1 - y0)/ny,
+ * p_y = py0 + (ipy + 1/2)(py1 - py0)/npy, x = 0 and
+ *   p_x = +sqrt(2E - p_y^2 - y^2 + 2y^3/3).
+ * A negative radicand sets status FORBIDDEN and the state to NaN; the
+ * FORBIDDEN decision is made in IEEE double without contraction, in the
+ * order written above.  ics_out [4][ny*npy], status_out [ny*npy]. */
+chs_status chs_section_grid_ics(chs_system s, double E, double y0, double y1, int32_t ny,
+                                double py0, double py1, int32_t npy, double* ics_out,
+                                int32_t* status_out, void* stream);
+
+/* FPUT initial conditions from normal-mode amplitudes (Q_m, P_m), m = 1..N
+ * (Sec. Examples, FPU system): q_i = sqrt(2/(N+1)) sum_m Q_m sin(i m pi/(N+1)),
+ * p_i likewise from P_m; the state is then scaled by s > 0 with H(s x) = E_o,
+ * s^2 = 2E / (H2 + sqrt(H2^2 + 4 H4 E)) where H2, H4 are the quadratic and
+ * quartic parts at s = 1.  Qm, Pm [N][n], E [n], ics_out [2N][n].
+ * CHS_E_UNSUPPORTED unless alpha = 0. */
+chs_status chs_fput_mode_ics(chs_system s, int64_t n, const double* Qm, const double* Pm,
+                             const double* E, double* ics_out, void* stream);
+
+/* Initialises an ensemble from initial conditions `ics` [d][n]:
+ * x <- ics; status <- ic_status (or OK when NULL), NONFINITE for a non-finite
+ * OK state; h0 <- H(x); dh_max, n_exec, ld <- 0; the k = p->n_dev deviation
+ * vectors are copied from w_in ([k*d][n], same precision as the ensemble) or,
+ * when w_in is NULL, seeded on the device: component c of vector j of orbit o
+ * is the m-th SplitMix64 output (m = (o*k + j)*d + c + 1) of the stream seeded
+ * with p->seed, mapped to [-1, 1) by its top 53 bits.  Vectors are normalised
+ * when p->renorm is set. */
+chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemble* e,
+                             const double* ics, const int32_t* ic_status, const void* w_in,
+                             void* stream);
+
+/* Advances every OK orbit of the ensemble by p->n_steps classic RK4 steps of
+ * size p->dt on the joint system (x, w_1..w_k, M_p):
+ *   x' = f(x) (Hamilton's equations), w_j' = J(x) w_j (variational equations,
+ *   Sec. Statement of need), M_p' = sum_i |f_i(x)|^p (the LD, Sec. Statement
+ *   of need),
+ * the fixed-step integrator of Sec. Functionalities (RK4 in place of DOP8).
+ * After each step: vectors are renormalised when p->renorm is set ("DOP 8 ODE
+ * solver with fixed step size that includes the normalization of the
+ * deviation vectors"); an orbit with sum_i q_i^2 > escape_r2 freezes as
+ * ESCAPED.  At absolute steps divisible by sample_every: non-finite -> frozen
+ * NONFINITE; dh_max <- max(dh_max, |H - h0|); |H - h0| > dh_limit -> frozen
+ * ENERGY_DRIFT.  Splitting a run into calls with consecutive step0 gives
+ * bit-identical results.  Supported: HENON_HEILES, HARMONIC, INVERTED
+ * (k <= 4) and QUARTIC3 (k <= 6). */
+chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ensemble* e,
+                               void* stream);
+
+/* Indicators of the current ensemble state (Sec. Functionalities):
+ *   sali_out [n]        SALI = min(|w1 + w2|, |w1 - w2|) of the first two unit
+ *                       vectors (refs Skokos2001/03/04); needs k >= 2.
+ *   gali_out [k-1][n]   GALI_m, m = 2..k: the product of the singular values
+ *                       of the d x m matrix of the first m unit vectors (ref
+ *                       Skokos2008), computed as prod |R_ii| of its QR.
+ *   label_out [n]       1 chaotic (SALI < sali_threshold), 0 regular,
+ *                       2 ESCAPED, -1 any other non-OK status.
+ *   ld_ind_out [2][n]   when grid_ny * grid_npy == n and the ensemble has an
+ *                       LD: D_L and S_L from the four grid neighbours (LD-based
+ *                       indicators and neighbouring trajectories):
+ *                         D_L = 1/4 sum_dir |LD(+) - LD(-)| / LD,
+ *                         S_L = 1/2 sum_dir |2 - (LD(+) + LD(-)) / LD|;
+ *                       NaN on the border and next to any non-OK cell.
+ * Any output may be NULL.  FORBIDDEN orbits get NaN indicators. */
+chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble* e,
+                          int32_t grid_ny, int32_t grid_npy, double* sali_out,
+                          double* gali_out, double* ld_ind_out, int8_t* label_out,
+                          void* stream);
+
+/* Lyapunov spectrum by periodic QR (Sec. Functionalities, Lyapunov item;
+ * FPU example of Sec. Examples).  d deviation vectors start as the identity
+ * and follow the variational equations under RK4 with the orbit; every
+ * p->qr_every steps and at the last step the vector matrix W is factorised
+ * W = QR with R_ii > 0, S_i += ln R_ii and W <- Q.  lambda_out [d][n] gets
+ * S_i / (n_steps * dt) in column order; status_out [n] gets the orbit status
+ * (a non-finite state at a health check gives NONFINITE and NaN exponents).
+ * ic_status may be NULL.  Supported: FPUT with N in {4, 8, 16, 32, 64} (the
+ * vectors live in shared memory, propagated by the exact one-step RK4
+ * propagator), and HENON_HEILES, HARMONIC, INVERTED.  FP64 throughout. */
+chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n,
+                                 const double* ics, const int32_t* ic_status,
+                                 double* lambda_out, int32_t* status_out, void* stream);
+
+/* Message for the last non-OK status returned on this thread ("" if none). */
+const char* chs_last_error(void);
+
+/* Library version string. */
+const char* chs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHS_H */

@@ -1,0 +1,303 @@
+// chs_api.cu -- the C ABI (include/chs.h): argument validation on the host,
+// then asynchronous kernel launches on the caller's stream.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "chs_internal.cuh"
+
+struct chs_system_s {
+    chs::SysPar sp;
+    int device;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+chs_status fail(chs_status code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+
+chs_status fail(chs_status code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+chs_status ok()
+{
+    return CHS_OK;
+}
+
+chs_status cuda_status(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return ok();
+    return fail(CHS_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+chs::EnsPtrs ens_ptrs(const chs_ensemble* e)
+{
+    return chs::EnsPtrs{e->n_orbits, e->x, e->w, e->ld, e->h0, e->dh_max, e->n_exec, e->status};
+}
+
+// Largest number of deviation vectors an ensemble of the system may carry.
+int max_dev(const chs::SysPar& sp)
+{
+    return sp.n_dof == 2 ? 4 : 6;
+}
+
+chs_status check_params(const chs_params* p, const chs::SysPar& sp)
+{
+    if (!p) return fail(CHS_E_INVALID, "params is NULL");
+    if (!isfinite(p->dt) || p->dt == 0.0) return fail(CHS_E_INVALID, "dt must be finite and non-zero");
+    if (p->n_steps < 0) return fail(CHS_E_INVALID, "n_steps must be >= 0");
+    if (p->step0 < 0) return fail(CHS_E_INVALID, "step0 must be >= 0");
+    if (p->n_dev < 0 || p->n_dev > max_dev(sp))
+        return fail(CHS_E_INVALID, "n_dev must be in 0..%d for this system", max_dev(sp));
+    if (p->sample_every < 0) return fail(CHS_E_INVALID, "sample_every must be >= 0");
+    if (p->renorm != 0 && p->renorm != 1) return fail(CHS_E_INVALID, "renorm must be 0 or 1");
+    if (p->vec_precision != CHS_VEC_FP64 && p->vec_precision != CHS_VEC_FP32)
+        return fail(CHS_E_INVALID, "vec_precision must be CHS_VEC_FP64 or CHS_VEC_FP32");
+    if (p->reserved != 0) return fail(CHS_E_INVALID, "reserved must be 0");
+    if (!(p->ld_p >= 0.0) || !isfinite(p->ld_p)) return fail(CHS_E_INVALID, "ld_p must be finite and >= 0");
+    if (!(p->escape_r2 >= 0.0)) return fail(CHS_E_INVALID, "escape_r2 must be >= 0");
+    if (!(p->dh_limit >= 0.0)) return fail(CHS_E_INVALID, "dh_limit must be >= 0");
+    return ok();
+}
+
+chs_status check_ensemble(const chs_ensemble* e, const chs_params* p)
+{
+    if (!e) return fail(CHS_E_INVALID, "ensemble is NULL");
+    if (e->n_orbits < 0) return fail(CHS_E_INVALID, "n_orbits must be >= 0");
+    if (e->n_orbits > ((int64_t)1 << 40)) return fail(CHS_E_SIZE, "n_orbits exceeds 2^40");
+    if (e->n_orbits == 0) return ok();
+    if (!e->x || !e->h0 || !e->dh_max || !e->n_exec || !e->status)
+        return fail(CHS_E_INVALID, "ensemble x, h0, dh_max, n_exec and status must be non-NULL");
+    if (p->n_dev > 0 && !e->w) return fail(CHS_E_INVALID, "ensemble w is NULL but n_dev > 0");
+    if (p->ld_p > 0.0 && !e->ld) return fail(CHS_E_INVALID, "ensemble ld is NULL but ld_p > 0");
+    return ok();
+}
+
+chs::StepArgs step_args(const chs_params* p)
+{
+    chs::StepArgs a;
+    a.dt = p->dt;
+    a.n_steps = p->n_steps;
+    a.step0 = p->step0;
+    a.sample_every = p->sample_every;
+    a.renorm = p->renorm;
+    a.qr_every = p->qr_every;
+    a.ld_sqrt = p->ld_p == 0.5 ? 1 : 0;
+    a.ld_p = p->ld_p;
+    a.escape_r2 = p->escape_r2;
+    a.dh_limit = p->dh_limit;
+    return a;
+}
+
+chs_status check_handle(chs_system s)
+{
+    if (!s) return fail(CHS_E_INVALID, "system handle is NULL");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(CHS_E_CUDA, "cudaGetDevice failed");
+    if (dev != s->device)
+        return fail(CHS_E_INVALID, "system was created on device %d but device %d is current", s->device, dev);
+    return ok();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* chs_version(void) { return "chs 0.1.0 (sm_103a)"; }
+
+const char* chs_last_error(void) { return g_err.c_str(); }
+
+chs_status chs_create_system(chs_system* out, chs_model model, int32_t n_dof, const double* params,
+                             int32_t n_params)
+{
+    if (!out) return fail(CHS_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n_params < 0 || (n_params > 0 && !params)) return fail(CHS_E_INVALID, "bad params array");
+    chs::SysPar sp{(int)model, n_dof, 1.0, 0.0, 1.0, 0.1};
+    switch (model) {
+    case CHS_HENON_HEILES:
+    case CHS_HARMONIC:
+    case CHS_INVERTED:
+        if (n_dof != 2) return fail(CHS_E_INVALID, "this model has n_dof = 2");
+        if (n_params != 0) return fail(CHS_E_INVALID, "this model takes no parameters");
+        break;
+    case CHS_QUARTIC3:
+        if (n_dof != 3) return fail(CHS_E_INVALID, "QUARTIC3 has n_dof = 3");
+        if (n_params > 1) return fail(CHS_E_INVALID, "QUARTIC3 takes {eps}");
+        if (n_params == 1) sp.eps = params[0];
+        if (!isfinite(sp.eps)) return fail(CHS_E_INVALID, "eps must be finite");
+        break;
+    case CHS_FPUT:
+        if (n_dof < 1 || n_dof > 4096) return fail(CHS_E_INVALID, "FPUT n_dof must be in 1..4096");
+        if (n_params != 0 && n_params != 3) return fail(CHS_E_INVALID, "FPUT takes {k, alpha, beta}");
+        if (n_params == 3) {
+            sp.kk = params[0];
+            sp.alpha = params[1];
+            sp.beta = params[2];
+        }
+        if (!isfinite(sp.kk) || !isfinite(sp.alpha) || !isfinite(sp.beta))
+            return fail(CHS_E_INVALID, "FPUT constants must be finite");
+        break;
+    default:
+        return fail(CHS_E_INVALID, "unknown model %d", (int)model);
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+    chs_system s = new (std::nothrow) chs_system_s;
+    if (!s) return fail(CHS_E_NOMEM, "out of host memory");
+    s->sp = sp;
+    s->device = dev;
+    *out = s;
+    return ok();
+}
+
+chs_status chs_destroy_system(chs_system s)
+{
+    delete s;
+    return ok();
+}
+
+int32_t chs_system_dim(chs_system s) { return s ? 2 * s->sp.n_dof : -1; }
+
+chs_status chs_section_grid_ics(chs_system s, double E, double y0, double y1, int32_t ny, double py0,
+                                double py1, int32_t npy, double* ics_out, int32_t* status_out,
+                                void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (s->sp.model != CHS_HENON_HEILES) return fail(CHS_E_UNSUPPORTED, "section grid is for HENON_HEILES");
+    if (ny <= 0 || npy <= 0) return fail(CHS_E_INVALID, "ny and npy must be > 0");
+    if ((int64_t)ny * npy > ((int64_t)1 << 34)) return fail(CHS_E_SIZE, "grid too large");
+    if (!isfinite(E) || !isfinite(y0) || !isfinite(y1) || !isfinite(py0) || !isfinite(py1))
+        return fail(CHS_E_INVALID, "grid bounds and energy must be finite");
+    if (!(y1 > y0) || !(py1 > py0)) return fail(CHS_E_INVALID, "need y1 > y0 and py1 > py0");
+    if (!ics_out || !status_out) return fail(CHS_E_INVALID, "output pointers must be non-NULL");
+    return cuda_status(chs::launch_grid_ics(E, y0, y1, ny, py0, py1, npy, ics_out, status_out,
+                                            as_stream(stream)),
+                       "section grid launch");
+}
+
+chs_status chs_fput_mode_ics(chs_system s, int64_t n, const double* Qm, const double* Pm,
+                             const double* E, double* ics_out, void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (s->sp.model != CHS_FPUT) return fail(CHS_E_UNSUPPORTED, "normal-mode ICs are for FPUT");
+    if (s->sp.alpha != 0.0) return fail(CHS_E_UNSUPPORTED, "normal-mode energy scaling needs alpha = 0");
+    if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
+    if (n == 0) return ok();
+    if (!Qm || !Pm || !E || !ics_out) return fail(CHS_E_INVALID, "pointers must be non-NULL");
+    return cuda_status(chs::launch_fput_mode_ics(s->sp, n, Qm, Pm, E, ics_out, as_stream(stream)),
+                       "normal-mode launch");
+}
+
+chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemble* e,
+                             const double* ics, const int32_t* ic_status, const void* w_in,
+                             void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (!chs::small_model(s->sp.model))
+        return fail(CHS_E_UNSUPPORTED, "ensembles are implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
+    if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ensemble(e, p)) != CHS_OK) return r;
+    if (e->n_orbits == 0) return ok();
+    if (!ics) return fail(CHS_E_INVALID, "ics is NULL");
+    return cuda_status(chs::launch_init(s->sp, p->n_dev, p->vec_precision, p->renorm, p->seed, ics,
+                                        ic_status, w_in, ens_ptrs(e), as_stream(stream)),
+                       "ensemble init launch");
+}
+
+chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ensemble* e, void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (!chs::small_model(s->sp.model))
+        return fail(CHS_E_UNSUPPORTED, "integration is implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
+    if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ensemble(e, p)) != CHS_OK) return r;
+    if (e->n_orbits == 0 || p->n_steps == 0) return ok();
+    return cuda_status(chs::launch_integrate(s->sp, p->n_dev, p->vec_precision, p->ld_p > 0.0,
+                                             step_args(p), ens_ptrs(e), as_stream(stream)),
+                       "integrate launch");
+}
+
+chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble* e, int32_t grid_ny,
+                          int32_t grid_npy, double* sali_out, double* gali_out, double* ld_ind_out,
+                          int8_t* label_out, void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (!chs::small_model(s->sp.model))
+        return fail(CHS_E_UNSUPPORTED, "indicators are implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
+    if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ensemble(e, p)) != CHS_OK) return r;
+    if ((sali_out || label_out) && p->n_dev < 2) return fail(CHS_E_INVALID, "SALI and labels need n_dev >= 2");
+    if (gali_out && p->n_dev < 2) return fail(CHS_E_INVALID, "GALI needs n_dev >= 2");
+    if (ld_ind_out) {
+        if (grid_ny < 3 || grid_npy < 3 || (int64_t)grid_ny * grid_npy != e->n_orbits)
+            return fail(CHS_E_INVALID, "LD indicators need a grid_ny x grid_npy grid (each >= 3) covering n_orbits");
+        if (!e->ld) return fail(CHS_E_INVALID, "LD indicators need the ensemble LD");
+    }
+    if (e->n_orbits == 0) return ok();
+    cudaStream_t st = as_stream(stream);
+    const chs::EnsPtrs ep = ens_ptrs(e);
+    if (sali_out || gali_out || label_out) {
+        r = cuda_status(chs::launch_indicators(s->sp, p->n_dev, p->vec_precision, p->sali_threshold, ep,
+                                               sali_out, gali_out, label_out, st),
+                        "indicator launch");
+        if (r != CHS_OK) return r;
+    }
+    if (ld_ind_out)
+        return cuda_status(chs::launch_ld_stencil(grid_ny, grid_npy, e->ld, e->status, ld_ind_out, st),
+                           "LD stencil launch");
+    return ok();
+}
+
+chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n, const double* ics,
+                                 const int32_t* ic_status, double* lambda_out, int32_t* status_out,
+                                 void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (!p) return fail(CHS_E_INVALID, "params is NULL");
+    if (!isfinite(p->dt) || p->dt == 0.0) return fail(CHS_E_INVALID, "dt must be finite and non-zero");
+    if (p->n_steps < 1) return fail(CHS_E_INVALID, "n_steps must be >= 1");
+    if (p->qr_every < 1) return fail(CHS_E_INVALID, "qr_every must be >= 1");
+    if (p->sample_every < 0) return fail(CHS_E_INVALID, "sample_every must be >= 0");
+    if (p->vec_precision != CHS_VEC_FP64) return fail(CHS_E_UNSUPPORTED, "the Lyapunov path is FP64 only");
+    if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
+    if (n > ((int64_t)1 << 31)) return fail(CHS_E_SIZE, "n exceeds 2^31");
+    if (n == 0) return ok();
+    if (!ics || !lambda_out || !status_out) return fail(CHS_E_INVALID, "pointers must be non-NULL");
+    const chs::StepArgs a = step_args(p);
+    cudaStream_t st = as_stream(stream);
+    if (s->sp.model == CHS_FPUT) {
+        if (!chs::fput_lyap_supported(s->sp.n_dof))
+            return fail(CHS_E_UNSUPPORTED, "FPUT Lyapunov supports N in {4, 8, 16, 32, 64}");
+        return cuda_status(chs::launch_fput_lyap(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
+                           "FPUT Lyapunov launch");
+    }
+    if (s->sp.model == CHS_HENON_HEILES || s->sp.model == CHS_HARMONIC || s->sp.model == CHS_INVERTED)
+        return cuda_status(chs::launch_lyap_small(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
+                           "Lyapunov launch");
+    return fail(CHS_E_UNSUPPORTED, "Lyapunov spectrum not implemented for this model");
+}
+
+}  // extern "C"

@@ -1,0 +1,608 @@
+// k_small.cu -- one orbit per thread: ensemble set-up, RK4 integration of the
+// orbit with its deviation vectors and LD, indicators, and the Lyapunov
+// spectrum of the 2-DOF systems.
+//
+// Design: the whole joint state (x, w_1..w_k, M_p) of an orbit lives in
+// registers for the entire call; the only global traffic is one coalesced SoA
+// load and one store per component per call, so the kernels are bound by the
+// FP64 pipe (GB300: 2 DFMA/clk/SM), not by HBM.
+#include <math.h>
+
+#include "chs_internal.cuh"
+#include "systems.cuh"
+
+namespace chs {
+
+// --------------------------------------------------------------------------
+// Ensemble set-up
+// --------------------------------------------------------------------------
+
+// SplitMix64 finaliser applied to the state seed + m * 0x9e3779b97f4a7c15,
+// i.e. the m-th output of the stream seeded with `seed`.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t m)
+{
+    uint64_t z = seed + m * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+template <class Sys, int K, typename VT>
+__global__ void __launch_bounds__(kSmallBlock)
+k_init(const SysPar sp, const int renorm, const uint64_t seed, const double* __restrict__ ics,
+       const int32_t* __restrict__ ic_status, const VT* __restrict__ w_in, const EnsPtrs e)
+{
+    constexpr int D = 2 * Sys::N;
+    const int64_t n = e.n;
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    double x[D];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        x[c] = ics[c * n + o];
+        e.x[c * n + o] = x[c];
+        finite = finite && isfinite(x[c]);
+    }
+    int32_t st = ic_status ? ic_status[o] : CHS_ORBIT_OK;
+    if (st == CHS_ORBIT_OK && !finite) st = CHS_ORBIT_NONFINITE;
+    e.status[o] = st;
+    e.h0[o] = (st == CHS_ORBIT_OK) ? Sys::energy(x, sp) : __longlong_as_double(0x7ff8000000000000LL);
+    e.dh_max[o] = 0.0;
+    e.n_exec[o] = 0;
+    if (e.ld) e.ld[o] = 0.0;
+    VT* wg = static_cast<VT*>(e.w);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        double v[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            if (w_in) {
+                v[c] = (double)w_in[(j * D + c) * n + o];
+            } else {
+                const uint64_t m = ((uint64_t)o * K + j) * D + c + 1;
+                const uint64_t z = splitmix64_at(seed, m);
+                v[c] = __dsub_rn(__dmul_rn(2.0, __dmul_rn((double)(z >> 11), 0x1.0p-53)), 1.0);
+            }
+        }
+        if (renorm) {
+            // sum of squares in index order, no contraction: the same rounding as a
+            // plain sequential loop
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc = __dadd_rn(acc, __dmul_rn(v[c], v[c]));
+            const double nr = __dsqrt_rn(acc);
+#pragma unroll
+            for (int c = 0; c < D; ++c) v[c] = __ddiv_rn(v[c], nr);
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = (VT)v[c];
+    }
+}
+
+// --------------------------------------------------------------------------
+// RK4 on the joint system
+// --------------------------------------------------------------------------
+
+// dw = J(x) w for w = (dq, dp): d(dq) = dp, d(dp) = -Hess V dq.
+template <int N, int NH, typename VT>
+__device__ __forceinline__ void var_rhs(const VT* Hc, const VT* w, VT* dw)
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) dw[i] = w[N + i];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        VT acc = Hc[hidx<N>(i, 0)] * w[0];
+#pragma unroll
+        for (int m = 1; m < N; ++m) acc = fma(Hc[hidx<N>(i, m)], w[m], acc);
+        dw[N + i] = -acc;
+    }
+}
+
+// LD integrand sum_i |f_i|^p.
+template <int D>
+__device__ __forceinline__ double ld_integrand(const double* f, int ld_sqrt, double p)
+{
+    double acc = 0.0;
+    if (ld_sqrt) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc += sqrt(fabs(f[i]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc += pow(fabs(f[i]), p);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ float rsqrt_vt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_vt(double v) { return rsqrt(v); }
+
+// One classic RK4 step of (x, w_1..w_K, L):
+//   k1 = F(z), k2 = F(z + h/2 k1), k3 = F(z + h/2 k2), k4 = F(z + h k3),
+//   z <- z + h/6 (k1 + 2 k2 + 2 k3 + k4),
+// with each stage's Jacobian evaluated at that stage's state.
+template <class Sys, int K, bool LD, typename VT>
+__device__ __forceinline__ void rk4_step(double* x, VT (*w)[2 * Sys::N], double& L, const double h,
+                                         const int ld_sqrt, const double ld_p, const SysPar& sp)
+{
+    constexpr int N = Sys::N, D = 2 * N, NH = Sys::NH;
+    constexpr int KK = K > 0 ? K : 1;
+    const double hh = 0.5 * h, h6 = h / 6.0;
+    const VT hhv = (VT)hh, hv = (VT)h, h6v = (VT)h6;
+    double ax[D], xs[D], f[D], H[NH];
+    VT aw[KK][D], ws[KK][D], dw[D], Hc[NH];
+    double aL = 0.0;
+
+    // stage 1 at (x, w)
+    Sys::eval(x, f, H, sp);
+#pragma unroll
+    for (int i = 0; i < NH; ++i) Hc[i] = (VT)H[i];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        ax[c] = f[c];
+        xs[c] = fma(hh, f[c], x[c]);
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        var_rhs<N, NH, VT>(Hc, w[j], dw);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            aw[j][c] = dw[c];
+            ws[j][c] = fma(hhv, dw[c], w[j][c]);
+        }
+    }
+    if (LD) aL = ld_integrand<D>(f, ld_sqrt, ld_p);
+
+    // stages 2 and 3 at (xs, ws); the next stage input uses h/2 then h
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const double cs = (s == 0) ? hh : h;
+        const VT csv = (s == 0) ? hhv : hv;
+        Sys::eval(xs, f, H, sp);
+#pragma unroll
+        for (int i = 0; i < NH; ++i) Hc[i] = (VT)H[i];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            ax[c] = fma(2.0, f[c], ax[c]);
+            xs[c] = fma(cs, f[c], x[c]);
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            var_rhs<N, NH, VT>(Hc, ws[j], dw);
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                aw[j][c] = fma((VT)2, dw[c], aw[j][c]);
+                ws[j][c] = fma(csv, dw[c], w[j][c]);
+            }
+        }
+        if (LD) aL = fma(2.0, ld_integrand<D>(f, ld_sqrt, ld_p), aL);
+    }
+
+    // stage 4 at (xs, ws)
+    Sys::eval(xs, f, H, sp);
+#pragma unroll
+    for (int i = 0; i < NH; ++i) Hc[i] = (VT)H[i];
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = fma(h6, ax[c] + f[c], x[c]);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        var_rhs<N, NH, VT>(Hc, ws[j], dw);
+#pragma unroll
+        for (int c = 0; c < D; ++c) w[j][c] = fma(h6v, aw[j][c] + dw[c], w[j][c]);
+    }
+    if (LD) L = fma(h6, aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
+}
+
+template <class Sys, int K, bool LD, typename VT>
+__global__ void __launch_bounds__(kSmallBlock)
+k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e)
+{
+    constexpr int N = Sys::N, D = 2 * N;
+    constexpr int KK = K > 0 ? K : 1;
+    const int64_t n = e.n;
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    if (e.status[o] != CHS_ORBIT_OK) return;
+
+    VT* wg = static_cast<VT*>(e.w);
+    double x[D];
+    VT w[KK][D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int c = 0; c < D; ++c) w[j][c] = wg[(j * D + c) * n + o];
+    double L = LD ? e.ld[o] : 0.0;
+    const double h0 = e.h0[o];
+    double dhm = e.dh_max[o];
+
+    int32_t st = CHS_ORBIT_OK;
+    int64_t until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
+    int64_t s = 0;
+    while (s < a.n_steps) {
+        ++s;
+        rk4_step<Sys, K, LD, VT>(x, w, L, a.dt, a.ld_sqrt, a.ld_p, sp);
+        if (a.renorm) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                VT n2 = w[j][0] * w[j][0];
+#pragma unroll
+                for (int c = 1; c < D; ++c) n2 = fma(w[j][c], w[j][c], n2);
+                const VT inv = rsqrt_vt(n2);
+#pragma unroll
+                for (int c = 0; c < D; ++c) w[j][c] *= inv;
+            }
+        }
+        if (a.escape_r2 > 0.0) {
+            double r2 = x[0] * x[0];
+#pragma unroll
+            for (int i = 1; i < N; ++i) r2 = fma(x[i], x[i], r2);
+            if (r2 > a.escape_r2) {
+                st = CHS_ORBIT_ESCAPED;
+                break;
+            }
+        }
+        if (--until == 0) {
+            until = a.sample_every;
+            bool fin = isfinite(L);
+#pragma unroll
+            for (int c = 0; c < D; ++c) fin = fin && isfinite(x[c]);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int c = 0; c < D; ++c) fin = fin && isfinite((double)w[j][c]);
+            if (!fin) {
+                st = CHS_ORBIT_NONFINITE;
+                break;
+            }
+            const double dH = fabs(Sys::energy(x, sp) - h0);
+            dhm = fmax(dhm, dH);
+            if (a.dh_limit > 0.0 && dH > a.dh_limit) {
+                st = CHS_ORBIT_ENERGY_DRIFT;
+                break;
+            }
+        }
+    }
+
+#pragma unroll
+    for (int c = 0; c < D; ++c) e.x[c * n + o] = x[c];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = w[j][c];
+    if (LD) e.ld[o] = L;
+    e.dh_max[o] = dhm;
+    e.n_exec[o] += s;
+    e.status[o] = st;
+}
+
+// --------------------------------------------------------------------------
+// Indicators: SALI, GALI_2..k (prod R_ii of a modified Gram-Schmidt QR of the
+// unit vectors), labels
+// --------------------------------------------------------------------------
+
+template <int D, int K, typename VT>
+__global__ void __launch_bounds__(kSmallBlock)
+k_indicators(const int64_t n, const VT* __restrict__ wg, const int32_t* __restrict__ status,
+             const double thr, double* __restrict__ sali, double* __restrict__ gali,
+             int8_t* __restrict__ label)
+{
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int32_t st = status[o];
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    double A[K][D];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        double n2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            A[j][c] = (double)wg[(j * D + c) * n + o];
+            n2 = fma(A[j][c], A[j][c], n2);
+        }
+        const double inv = 1.0 / sqrt(n2);
+#pragma unroll
+        for (int c = 0; c < D; ++c) A[j][c] *= inv;
+    }
+    double sv = qnan;
+    if (K >= 2 && st != CHS_ORBIT_FORBIDDEN) {
+        double a2 = 0.0, b2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const double sp = A[0][c] + A[1 % K][c], sm = A[0][c] - A[1 % K][c];
+            a2 = fma(sp, sp, a2);
+            b2 = fma(sm, sm, b2);
+        }
+        sv = sqrt(fmin(a2, b2));
+    }
+    if (sali) sali[o] = sv;
+    if (gali && K >= 2) {
+        // modified Gram-Schmidt on the columns; GALI_m = prod_{j < m} R_jj
+        double prod = 1.0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+#pragma unroll
+            for (int i = 0; i < j; ++i) {
+                double r = 0.0;
+#pragma unroll
+                for (int c = 0; c < D; ++c) r = fma(A[i][c], A[j][c], r);
+#pragma unroll
+                for (int c = 0; c < D; ++c) A[j][c] = fma(-r, A[i][c], A[j][c]);
+            }
+            double n2 = 0.0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) n2 = fma(A[j][c], A[j][c], n2);
+            const double rjj = sqrt(n2);
+            prod *= rjj;
+            if (rjj > 0.0) {
+                const double inv = 1.0 / rjj;
+#pragma unroll
+                for (int c = 0; c < D; ++c) A[j][c] *= inv;
+            }
+            if (j >= 1) gali[(int64_t)(j - 1) * n + o] = (st == CHS_ORBIT_FORBIDDEN) ? qnan : prod;
+        }
+    }
+    if (label) {
+        int8_t lb;
+        if (st == CHS_ORBIT_OK)
+            lb = (sv < thr) ? 1 : 0;
+        else if (st == CHS_ORBIT_ESCAPED)
+            lb = 2;
+        else
+            lb = -1;
+        label[o] = lb;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Lyapunov spectrum of the 2-DOF systems: W (4 x 4) in registers
+// --------------------------------------------------------------------------
+
+template <class Sys>
+__global__ void __launch_bounds__(kSmallBlock)
+k_lyap_small(const StepArgs a, const SysPar sp, const int64_t n, const double* __restrict__ ics,
+             const int32_t* __restrict__ ic_status, double* __restrict__ lambda,
+             int32_t* __restrict__ status_out)
+{
+    constexpr int D = 2 * Sys::N;
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    int32_t st = ic_status ? ic_status[o] : CHS_ORBIT_OK;
+    double x[D], W[D][D], S[D];
+    bool fin = true;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        x[c] = ics[c * n + o];
+        fin = fin && isfinite(x[c]);
+        S[c] = 0.0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) W[j][c] = (j == c) ? 1.0 : 0.0;
+    }
+    if (st == CHS_ORBIT_OK && !fin) st = CHS_ORBIT_NONFINITE;
+    if (st == CHS_ORBIT_OK) {
+        double L = 0.0;
+        int64_t until_qr = a.qr_every;
+        int64_t until = a.sample_every > 0 ? a.sample_every : -1;
+        for (int64_t s = 1; s <= a.n_steps; ++s) {
+            rk4_step<Sys, D, false, double>(x, W, L, a.dt, 0, 0.0, sp);
+            if (--until_qr == 0 || s == a.n_steps) {
+                until_qr = a.qr_every;
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+#pragma unroll
+                    for (int i = 0; i < j; ++i) {
+                        double r = 0.0;
+#pragma unroll
+                        for (int c = 0; c < D; ++c) r = fma(W[i][c], W[j][c], r);
+#pragma unroll
+                        for (int c = 0; c < D; ++c) W[j][c] = fma(-r, W[i][c], W[j][c]);
+                    }
+                    double n2 = 0.0;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) n2 = fma(W[j][c], W[j][c], n2);
+                    S[j] += 0.5 * log(n2);
+                    const double inv = rsqrt(n2);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) W[j][c] *= inv;
+                }
+            }
+            if (--until == 0) {
+                until = a.sample_every;
+                bool f2 = true;
+#pragma unroll
+                for (int c = 0; c < D; ++c) f2 = f2 && isfinite(x[c]) && isfinite(S[c]);
+                if (!f2) {
+                    st = CHS_ORBIT_NONFINITE;
+                    break;
+                }
+            }
+        }
+    }
+    const double T = (double)a.n_steps * a.dt;
+#pragma unroll
+    for (int c = 0; c < D; ++c) lambda[c * n + o] = (st == CHS_ORBIT_OK) ? S[c] / T : qnan;
+    status_out[o] = st;
+}
+
+// --------------------------------------------------------------------------
+// Host-side dispatch
+// --------------------------------------------------------------------------
+
+bool small_model(int model)
+{
+    return model == CHS_HENON_HEILES || model == CHS_HARMONIC || model == CHS_INVERTED ||
+           model == CHS_QUARTIC3;
+}
+
+template <class Sys, typename VT>
+static cudaError_t init_k(int k, const SysPar& sp, int renorm, uint64_t seed, const double* ics,
+                          const int32_t* ics_st, const void* w_in, const EnsPtrs& e, cudaStream_t st)
+{
+    const unsigned g = blocks_for(e.n, kSmallBlock);
+    const VT* wi = static_cast<const VT*>(w_in);
+    switch (k) {
+#define CHS_CASE(KV)                                                                           \
+    case KV:                                                                                   \
+        k_init<Sys, KV, VT><<<g, kSmallBlock, 0, st>>>(sp, renorm, seed, ics, ics_st, wi, e); \
+        break;
+        CHS_CASE(0) CHS_CASE(1) CHS_CASE(2) CHS_CASE(3) CHS_CASE(4)
+#undef CHS_CASE
+    case 5:
+        if constexpr (Sys::N >= 3) {
+            k_init<Sys, 5, VT><<<g, kSmallBlock, 0, st>>>(sp, renorm, seed, ics, ics_st, wi, e);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    case 6:
+        if constexpr (Sys::N >= 3) {
+            k_init<Sys, 6, VT><<<g, kSmallBlock, 0, st>>>(sp, renorm, seed, ics, ics_st, wi, e);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <class Sys>
+static cudaError_t init_sys(int k, int fp32, const SysPar& sp, int renorm, uint64_t seed,
+                            const double* ics, const int32_t* ics_st, const void* w_in,
+                            const EnsPtrs& e, cudaStream_t st)
+{
+    return fp32 ? init_k<Sys, float>(k, sp, renorm, seed, ics, ics_st, w_in, e, st)
+                : init_k<Sys, double>(k, sp, renorm, seed, ics, ics_st, w_in, e, st);
+}
+
+cudaError_t launch_init(const SysPar& sp, int k, int vec_fp32, int renorm, uint64_t seed,
+                        const double* ics, const int32_t* ic_status, const void* w_in,
+                        const EnsPtrs& e, cudaStream_t st)
+{
+    if (e.n == 0) return cudaSuccess;
+    switch (sp.model) {
+    case CHS_HENON_HEILES:
+        return init_sys<SysHenonHeiles>(k, vec_fp32, sp, renorm, seed, ics, ic_status, w_in, e, st);
+    case CHS_HARMONIC:
+        return init_sys<SysHarmonic>(k, vec_fp32, sp, renorm, seed, ics, ic_status, w_in, e, st);
+    case CHS_INVERTED:
+        return init_sys<SysInverted>(k, vec_fp32, sp, renorm, seed, ics, ic_status, w_in, e, st);
+    case CHS_QUARTIC3:
+        return init_sys<SysQuartic3>(k, vec_fp32, sp, renorm, seed, ics, ic_status, w_in, e, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class Sys, typename VT, bool LD>
+static cudaError_t integ_k(int k, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
+                           cudaStream_t st)
+{
+    const unsigned g = blocks_for(e.n, kSmallBlock);
+    switch (k) {
+#define CHS_CASE(KV)                                                          \
+    case KV:                                                                  \
+        k_integrate<Sys, KV, LD, VT><<<g, kSmallBlock, 0, st>>>(a, sp, e); \
+        break;
+        CHS_CASE(0) CHS_CASE(1) CHS_CASE(2) CHS_CASE(3) CHS_CASE(4)
+#undef CHS_CASE
+    case 5:
+        if constexpr (Sys::N >= 3) {
+            k_integrate<Sys, 5, LD, VT><<<g, kSmallBlock, 0, st>>>(a, sp, e);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    case 6:
+        if constexpr (Sys::N >= 3) {
+            k_integrate<Sys, 6, LD, VT><<<g, kSmallBlock, 0, st>>>(a, sp, e);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <class Sys>
+static cudaError_t integ_sys(int k, int fp32, bool ld, const StepArgs& a, const SysPar& sp,
+                             const EnsPtrs& e, cudaStream_t st)
+{
+    if (fp32)
+        return ld ? integ_k<Sys, float, true>(k, a, sp, e, st)
+                  : integ_k<Sys, float, false>(k, a, sp, e, st);
+    return ld ? integ_k<Sys, double, true>(k, a, sp, e, st)
+              : integ_k<Sys, double, false>(k, a, sp, e, st);
+}
+
+cudaError_t launch_integrate(const SysPar& sp, int k, int vec_fp32, bool ld, const StepArgs& a,
+                             const EnsPtrs& e, cudaStream_t st)
+{
+    if (e.n == 0 || a.n_steps == 0) return cudaSuccess;
+    switch (sp.model) {
+    case CHS_HENON_HEILES: return integ_sys<SysHenonHeiles>(k, vec_fp32, ld, a, sp, e, st);
+    case CHS_HARMONIC: return integ_sys<SysHarmonic>(k, vec_fp32, ld, a, sp, e, st);
+    case CHS_INVERTED: return integ_sys<SysInverted>(k, vec_fp32, ld, a, sp, e, st);
+    case CHS_QUARTIC3: return integ_sys<SysQuartic3>(k, vec_fp32, ld, a, sp, e, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int D, typename VT>
+static cudaError_t ind_k(int k, double thr, const EnsPtrs& e, double* sali, double* gali,
+                         int8_t* label, cudaStream_t st)
+{
+    const unsigned g = blocks_for(e.n, kSmallBlock);
+    const VT* w = static_cast<const VT*>(e.w);
+    switch (k) {
+#define CHS_CASE(KV)                                                                          \
+    case KV:                                                                                  \
+        k_indicators<D, KV, VT><<<g, kSmallBlock, 0, st>>>(e.n, w, e.status, thr, sali, gali, \
+                                                           label);                            \
+        break;
+        CHS_CASE(1) CHS_CASE(2) CHS_CASE(3) CHS_CASE(4) CHS_CASE(5) CHS_CASE(6)
+#undef CHS_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_indicators(const SysPar& sp, int k, int vec_fp32, double sali_threshold,
+                              const EnsPtrs& e, double* sali, double* gali, int8_t* label,
+                              cudaStream_t st)
+{
+    if (e.n == 0) return cudaSuccess;
+    const int D = 2 * sp.n_dof;
+    if (D == 4)
+        return vec_fp32 ? ind_k<4, float>(k, sali_threshold, e, sali, gali, label, st)
+                        : ind_k<4, double>(k, sali_threshold, e, sali, gali, label, st);
+    if (D == 6)
+        return vec_fp32 ? ind_k<6, float>(k, sali_threshold, e, sali, gali, label, st)
+                        : ind_k<6, double>(k, sali_threshold, e, sali, gali, label, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lyap_small(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
+                              const int32_t* ic_status, double* lambda, int32_t* status,
+                              cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned g = blocks_for(n, kSmallBlock);
+    switch (sp.model) {
+    case CHS_HENON_HEILES:
+        k_lyap_small<SysHenonHeiles><<<g, kSmallBlock, 0, st>>>(a, sp, n, ics, ic_status, lambda, status);
+        break;
+    case CHS_HARMONIC:
+        k_lyap_small<SysHarmonic><<<g, kSmallBlock, 0, st>>>(a, sp, n, ics, ic_status, lambda, status);
+        break;
+    case CHS_INVERTED:
+        k_lyap_small<SysInverted><<<g, kSmallBlock, 0, st>>>(a, sp, n, ics, ic_status, lambda, status);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace chs
