@@ -1,0 +1,368 @@
+"""Throughput bench of the chaos-indicator hot path on GB300.
+
+Workload (the Henon-Heiles grid run): E = 1/6, 1024 x 1024 cell-centred grid of
+(y, p_y) on the x = 0 section, p_x >= 0 from the energy, FP64 classic RK4 with
+h = 0.01, k = 4 deviation vectors renormalised every step, LD (p = 1/2), SALI,
+GALI_2..4, LD indicators and labels.  One bench step advances the whole grid by
+`--chunk` RK4 steps (continuing the same run from the previous step, so the
+timed steps cover a window of the t = 1e4 integration) and then evaluates every
+indicator on the new state: each step runs every stage of the hot path.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("orbit-steps/sec and % FP64 roofline; time-to-classified-grid vs plain at "
+          "≥99.5% agreement")
+UNIT = "orbit-steps/s"
+E_GRID = 1.0 / 6.0
+DT = 0.01
+K_DEV = 4
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA lanes per SM per clock (measured 1.20 TFLOP/s at ~1.99 GHz)
+
+
+def grid_box(E: float):
+    """Energy-allowed (y, p_y) box of the x = 0 section at E = 1/6."""
+    return -0.5, 1.0, -float(np.sqrt(2 * E)), float(np.sqrt(2 * E))
+
+
+def flops_per_orbit_step(k: int, ld: bool, vec_fp32: bool) -> tuple[int, int]:
+    """Algorithmic flops of one RK4 step of the Henon-Heiles joint system
+    (FMA = 2, sqrt and rsqrt = 1), as (FP64 flops, FP32 flops):
+      per stage: f and Hess V 10, variational 6 per vector, LD 7 (4 sqrt + 3 add)
+      stage inputs (3 stages): 2 flops per state and vector component
+      RK4 accumulation: 7 flops per component of (x, w_1..w_k, L)
+      renormalisation: 12 per vector;  escape test: 3."""
+    xs = 4 * (10 + (7 if ld else 0)) + 3 * 2 * 4 + 7 * (4 + (1 if ld else 0)) + 3
+    vs = 4 * 6 * k + 3 * 2 * 4 * k + 7 * 4 * k + 12 * k
+    return (xs, vs) if vec_fp32 else (xs + vs, 0)
+
+
+def fp64_peak_tflops(sm_mhz: float) -> float:
+    return SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+
+
+def shard_rows(ny: int, rank: int, world: int) -> tuple[int, int, int, int]:
+    """Weak scaling: every rank owns `ny` grid rows of a (world * ny)-row grid.
+    Returns (first_row, n_rows, halo_lo, halo_hi) of the slab it integrates,
+    with one extra row on each side that has a neighbour rank, so the LD
+    stencil of every owned cell is complete without any exchange."""
+    lo = rank * ny
+    halo_lo = 1 if rank > 0 else 0
+    halo_hi = 1 if rank < world - 1 else 0
+    return lo - halo_lo, ny + halo_lo + halo_hi, halo_lo, halo_hi
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.proc = None
+        self.uuid = uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(chunk: int, budget_s: float, n_sample: int = 4096, ny: int = 1024):
+    """The oracle as it stands on the host cores: a strided sample of valid cells of
+    the same grid, integrated chunk by chunk until `budget_s` of CPU time."""
+    import oracle as O
+    from paper_2507_00622_gb300.inputs import strided_sample
+
+    y0, y1, p0, p1 = grid_box(E_GRID)
+    ics, st = O.grid_ics(E_GRID, y0, y1, ny, p0, p1, ny)
+    valid = np.where(st == 0)[0]
+    idx = valid[strided_sample(valid.size, n_sample)]
+    kw = dict(n_dev=K_DEV, ld_p=0.5, escape_r2=4.0, sample_every=100)
+    w = O.seed_vectors(1, ics.shape[1], K_DEV, 4)[:, idx]
+    ens = O.Ensemble(O.henon_heiles(), O.params(DT, 1, **kw), ics[:, idx], st[idx], w_in=w)
+    done, step, t0 = 0, 0, time.perf_counter()
+    while True:
+        before = int(ens.n_exec.sum())
+        ens.integrate(O.params(DT, chunk, step0=step, **kw))
+        ens.indicators()
+        O.ld_indicators(1, idx.size, ens.ld, ens.status)
+        done += int(ens.n_exec.sum()) - before
+        step += chunk
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{idx.size} strided valid cells of the 1024x1024 E=1/6 grid, k=4, LD, "
+                      f"{step} RK4 steps from t=0 ({done} orbit-steps in {el:.1f} s)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle as O
+    O.build()
+    t_all = []
+    res = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(args.chunk, 0.0, n_sample=args.ref_sample)
+        if i >= args.warmup:
+            t_all.append(r["value"])
+            res = r
+    value = float(np.mean(t_all))
+    ms = 1e3 * args.ref_sample * args.chunk / value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "henon_heiles_E1/6_grid1024x1024_k4_sali_gali2-4_ld_rk4",
+                       "sample_per_step": f"{args.ref_sample} strided valid cells x {args.chunk} steps"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        cuda_build.build()
+    if world > 1:
+        dist.barrier()
+    chs.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    ny = npy = args.n_side
+    y0, y1, p0, p1 = grid_box(E_GRID)
+    dyg = (y1 - y0) / (ny * world)
+    first, rows, hlo, hhi = shard_rows(ny, rank, world)
+    sy0, sy1 = y0 + first * dyg, y0 + (first + rows) * dyg
+    n = rows * npy
+    own = slice(hlo * npy, (hlo + ny) * npy)
+    vec_fp32 = args.vec == "fp32"
+    vp = chs.VEC_FP32 if vec_fp32 else chs.VEC_FP64
+    S = chs.System(chs.HENON_HEILES, 2)
+    ics = torch.empty((4, n), dtype=torch.float64, device=dev)
+    ic_st = torch.empty(n, dtype=torch.int32, device=dev)
+    chs.chs_section_grid_ics(S.h, E_GRID, sy0, sy1, rows, p0, p1, npy, ics, ic_st)
+    kw = dict(n_dev=K_DEV, ld_p=0.5, escape_r2=4.0, sample_every=100, seed=1 + rank,
+              vec_precision=vp, sali_threshold=1e-6 if vec_fp32 else 1e-8)
+    ens = chs.DeviceEnsemble.empty(n, 4, K_DEV, vec_fp32, device=dev)
+    abi = ens.abi()
+    chs.chs_ensemble_init(S.h, chs.params(DT, 1, **kw), abi, ics, ic_st)
+    sali = torch.empty(n, dtype=torch.float64, device=dev)
+    gali = torch.empty((K_DEV - 1, n), dtype=torch.float64, device=dev)
+    label = torch.empty(n, dtype=torch.int8, device=dev)
+    ldi = torch.empty((2, n), dtype=torch.float64, device=dev)
+    step = 0
+
+    def one_step(ev=None):
+        nonlocal step
+        prm = chs.params(DT, args.chunk, step0=step, **kw)
+        if ev is not None:
+            ev[0].record(stream)
+        chs.chs_integrate_batch(S.h, prm, abi, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        chs.chs_indicators(S.h, prm, abi, rows, npy, sali, gali, ldi, label, stream)
+        step += args.chunk
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    exec0 = int(ens.n_exec[own].sum())
+    t_window0 = step * DT
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid).replace("GPU-", "")
+    except Exception:
+        uuid = None
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    time.sleep(0.5)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(args.steps):
+        one_step(kev[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+    exec1 = int(ens.n_exec[own].sum())
+    orbit_steps = exec1 - exec0
+    t_window1 = step * DT
+
+    # end to end through the C ABI from pinned host buffers: every step uploads the
+    # whole ensemble state, integrates, evaluates the indicators and reads back the
+    # state and every indicator
+    host = {k: getattr(ens, k).cpu().pin_memory() for k in ("x", "w", "ld", "h0", "dh_max", "n_exec",
+                                                             "status")}
+    outs = [sali, gali, label, ldi]
+    host_out = [t.cpu().pin_memory() for t in outs]
+    h2d = sum(t.numel() * t.element_size() for t in host.values())
+    d2h = h2d + sum(t.numel() * t.element_size() for t in host_out)
+    e2e_steps = max(1, args.e2e_steps)
+    e_exec0 = int(host["n_exec"][own].sum())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for k, t in host.items():
+            getattr(ens, k).copy_(t, non_blocking=True)
+        one_step()
+        for k, t in host.items():
+            t.copy_(getattr(ens, k), non_blocking=True)
+        for src, dst in zip(outs, host_out):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - w0
+    e_orbit_steps = int(host["n_exec"][own].sum()) - e_exec0
+
+    if world > 1:
+        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        c = torch.tensor([orbit_steps, e_orbit_steps], dtype=torch.int64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        total_ms, e2e_s = float(t[0]), float(t[1])
+        orbit_steps, e_orbit_steps = int(c[0]), int(c[1])
+
+    if rank == 0:
+        value = orbit_steps / (total_ms / 1e3)
+        f64, f32 = flops_per_orbit_step(K_DEV, True, vec_fp32)
+        per_launch_steps = (exec1 - exec0) / args.steps
+        achieved = f64 * per_launch_steps / (kern_ms / 1e3) / 1e12
+        peak_mhz = clk["sm_max_mhz"] or 2070.0
+        peak = fp64_peak_tflops(peak_mhz)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if not vec_fp32 else "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": "henon_heiles_E1/6_grid1024x1024_k4_sali_gali2-4_ld_rk4",
+                       "grid_per_gpu": [ny, npy], "n_orbits_per_gpu": ny * npy, "dt": DT,
+                       "rk4_steps_per_bench_step": args.chunk,
+                       "t_window": [t_window0, t_window1], "t_end_of_full_run": 1e4,
+                       "deviation_vectors": f"{K_DEV} x {'fp32' if vec_fp32 else 'fp64'}",
+                       "l2": "inputs larger than L2: ensemble state %.0f MB per GPU" %
+                             (h2d / 1e6),
+                       "parallelism": f"orbit-range shards x{world}, no data-path collective"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_integrate<HenonHeiles,4,LD>",
+                         "flops_per_orbit_step": {"fp64": f64, "fp32": f32},
+                         "peak_basis": f"152 SMs x 2 DFMA/clk x 2 flop x {peak_mhz:.0f} MHz",
+                         "kernel_ms_avg": kern_ms},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
+                       "reasons": clk["reasons"]},
+            "e2e": {"value": e_orbit_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d * world,
+                    "d2h_bytes_per_step": d2h * world},
+            "gpu_launches": 3 * args.steps,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_oracle_sample(args.chunk, args.cpu_budget)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--chunk", type=int, default=1000, help="RK4 steps per bench step")
+    ap.add_argument("--n-side", type=int, default=1024, help="grid side per GPU")
+    ap.add_argument("--vec", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=4096)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -110,8 +110,10 @@ def test_hh_grid_short_horizon_all_orbits(hh_small):
 def test_hh_grid_full_length_regular_orbits_and_labels(hh_small):
     _, st, _, (g, r), lam1 = hh_small
     v = st == 0
-    reg = v & (lam1 < 0.03)  # finite-time exponent at t = 200 from the oracle's QR method
-    assert reg.sum() > 200
+    # regular: finite-time largest exponent at t = 200 (oracle QR method) below 0.02;
+    # on this grid a 1e-15 perturbation of those orbits grows to at most ~3e-12
+    reg = v & (lam1 < 0.02)
+    assert reg.sum() > 300
     assert state_rel_err(g["x"][:, reg], r["x"][:, reg]).max() < STATE_RTOL
     assert ind_err(g["ld"][reg], r["ld"][reg]).max() < IND_TOL
     assert ind_err(g["sali"][reg], r["sali"][reg]).max() < IND_TOL
@@ -204,13 +206,15 @@ def test_status_paths_match_oracle():
                     [0.2, 0.5, 0.3, 0.3, 0.3],
                     [0.55, 0.2, 0.1, 0.1, 0.1]])
     st = np.array([0, 0, 0, 1, 0], dtype=np.int32)
+    seen = set()
     for dh_limit in (0.0, 1e-13):
         kw = dict(dt=0.01, n_steps=5000, k=2, ld_p=0.5, escape_r2=4.0, dh_limit=dh_limit)
         g, r = gpu_run(HH, 2, ics, st, **kw), oracle_run(HH, 2, ics, st, **kw)
         np.testing.assert_array_equal(g["status"], r["status"])
         np.testing.assert_array_equal(g["n_exec"], r["n_exec"])
         np.testing.assert_array_equal(g["label"], r["label"])
-    assert chs.ORBIT_ESCAPED in g["status"] and chs.ORBIT_NONFINITE in g["status"]
+        seen |= set(g["status"].tolist())
+    assert {chs.ORBIT_ESCAPED, chs.ORBIT_NONFINITE, chs.ORBIT_FORBIDDEN, chs.ORBIT_ENERGY_DRIFT} <= seen
 
 
 def test_invalid_arguments_are_rejected():
@@ -249,7 +253,7 @@ def test_fp32_vectors_error_against_fp64_oracle():
     v = st == 0
     # the state and LD do not depend on the vectors: FP64 parity holds for them
     lam, _ = O.lyapunov(O.henon_heiles(), O.params(0.01, 20000, qr_every=10), np.nan_to_num(ics), st)
-    reg = v & (lam[0] < 0.03)
+    reg = v & (lam[0] < 0.02)
     assert state_rel_err(g["x"][:, reg], r["x"][:, reg]).max() < STATE_RTOL
     assert ind_err(g["ld"][reg], r["ld"][reg]).max() < IND_TOL
     # SALI of regular orbits carries FP32 rounding only
@@ -305,7 +309,9 @@ def test_fput_lyapunov_matches_oracle(N):
     r, rs = O.lyapunov(O.fput(N), O.params(0.05, 2000, qr_every=10, sample_every=100), ics)
     np.testing.assert_array_equal(gs, rs)
     assert np.abs(g - r).max() < 1e-8
-    assert np.abs(g.sum(axis=0)).max() < 1e-6
+    # the sum of the spectrum is (1/T) ln det of the RK4 tangent map: RK4 is not
+    # volume preserving, so it is small but not zero; both sides agree on it
+    assert np.abs(g.sum(axis=0) - r.sum(axis=0)).max() < 1e-9
 
 
 # --------------------------------------------------------------------------
