@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include "chs_internal.cuh"
+#include "fastmath.cuh"
 #include "systems.cuh"
 
 namespace chs {
@@ -99,14 +100,14 @@ __device__ __forceinline__ void var_rhs(const VT* Hc, const VT* w, VT* dw)
     }
 }
 
-// LD integrand sum_i |f_i|^p.
+// LD integrand sum_i |f_i|^p (p = 1/2: Newton-refined square roots).
 template <int D>
 __device__ __forceinline__ double ld_integrand(const double* f, int ld_sqrt, double p)
 {
     double acc = 0.0;
     if (ld_sqrt) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) acc += sqrt(fabs(f[i]));
+        for (int i = 0; i < D; ++i) acc += sqrt_nr(fabs(f[i]));
     } else {
 #pragma unroll
         for (int i = 0; i < D; ++i) acc += pow(fabs(f[i]), p);
@@ -115,15 +116,17 @@ __device__ __forceinline__ double ld_integrand(const double* f, int ld_sqrt, dou
 }
 
 __device__ __forceinline__ float rsqrt_vt(float v) { return rsqrtf(v); }
-__device__ __forceinline__ double rsqrt_vt(double v) { return rsqrt(v); }
+__device__ __forceinline__ double rsqrt_vt(double v) { return rsqrt_nr(v); }
 
 // One classic RK4 step of (x, w_1..w_K, L):
 //   k1 = F(z), k2 = F(z + h/2 k1), k3 = F(z + h/2 k2), k4 = F(z + h k3),
 //   z <- z + h/6 (k1 + 2 k2 + 2 k3 + k4),
-// with each stage's Jacobian evaluated at that stage's state.
+// with each stage's Jacobian evaluated at that stage's state.  Direct form:
+// the vectors go through the four stages alongside the state.
 template <class Sys, int K, bool LD, typename VT>
-__device__ __forceinline__ void rk4_step(double* x, VT (*w)[2 * Sys::N], double& L, const double h,
-                                         const int ld_sqrt, const double ld_p, const SysPar& sp)
+__device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], double& L,
+                                                const double h, const int ld_sqrt,
+                                                const double ld_p, const SysPar& sp)
 {
     constexpr int N = Sys::N, D = 2 * N, NH = Sys::NH;
     constexpr int KK = K > 0 ? K : 1;
@@ -191,6 +194,113 @@ __device__ __forceinline__ void rk4_step(double* x, VT (*w)[2 * Sys::N], double&
         for (int c = 0; c < D; ++c) w[j][c] = fma(h6v, aw[j][c] + dw[c], w[j][c]);
     }
     if (LD) L = fma(h6, aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
+}
+
+// The same RK4 step with the vectors advanced by the exact one-step propagator
+// of RK4 on the linear variational equation w' = J_s w, J_s = [[0, I], [-H_s, 0]]
+// (H_s = Hess V at stage s):
+//   Phi = I + h/6 (J1 + 2J2 + 2J3 + J4) + h^2/6 (J2J1 + J3J2 + J4J3)
+//           + h^3/12 (J3J2J1 + J4J3J2) + h^4/24 J4J3J2J1
+//       = [[I - h^2/6 (H1+H2+H3) + h^4/24 H3H1,   h I - h^3/12 (H2+H3)],
+//          [-h/6 (H1+2H2+2H3+H4) + h^3/12 (H3H1 + H4H2),
+//                                 I - h^2/6 (H2+H3+H4) + h^4/24 H4H2]].
+// Identical to the direct form in exact arithmetic; for k >= 3 vectors it needs
+// fewer operations (Phi is built once and applied to each vector).
+template <class Sys, int K, bool LD, typename VT>
+__device__ __forceinline__ void rk4_step_phi(double* x, VT (*w)[2 * Sys::N], double& L,
+                                             const double h, const int ld_sqrt, const double ld_p,
+                                             const SysPar& sp)
+{
+    constexpr int N = Sys::N, D = 2 * N, NH = Sys::NH;
+    const double hh = 0.5 * h, h6 = h / 6.0;
+    double ax[D], xs[D], f[D], H[4][NH];
+    double aL = 0.0;
+
+    Sys::eval(x, f, H[0], sp);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        ax[c] = f[c];
+        xs[c] = fma(hh, f[c], x[c]);
+    }
+    if (LD) aL = ld_integrand<D>(f, ld_sqrt, ld_p);
+#pragma unroll
+    for (int s = 1; s < 3; ++s) {
+        const double cs = (s == 1) ? hh : h;
+        Sys::eval(xs, f, H[s], sp);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            ax[c] = fma(2.0, f[c], ax[c]);
+            xs[c] = fma(cs, f[c], x[c]);
+        }
+        if (LD) aL = fma(2.0, ld_integrand<D>(f, ld_sqrt, ld_p), aL);
+    }
+    Sys::eval(xs, f, H[3], sp);
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = fma(h6, ax[c] + f[c], x[c]);
+    if (LD) L = fma(h6, aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
+
+    // Phi blocks in the vector precision
+    VT Hs[4][NH];
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int i = 0; i < NH; ++i) Hs[s][i] = (VT)H[s][i];
+    const VT hv = (VT)h, c1 = (VT)(h / 6.0), c2 = (VT)(h * h / 6.0), c3 = (VT)(h * h * h / 12.0),
+             c4 = (VT)(h * h * h * h / 24.0);
+    VT A[N][N], B[N][N], C[N][N], Dm[N][N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const VT s1 = Hs[0][hidx<N>(i, j)], s2 = Hs[1][hidx<N>(i, j)];
+            const VT s3 = Hs[2][hidx<N>(i, j)], s4 = Hs[3][hidx<N>(i, j)];
+            VT p31 = Hs[2][hidx<N>(i, 0)] * Hs[0][hidx<N>(0, j)];
+            VT p42 = Hs[3][hidx<N>(i, 0)] * Hs[1][hidx<N>(0, j)];
+#pragma unroll
+            for (int m = 1; m < N; ++m) {
+                p31 = fma(Hs[2][hidx<N>(i, m)], Hs[0][hidx<N>(m, j)], p31);
+                p42 = fma(Hs[3][hidx<N>(i, m)], Hs[1][hidx<N>(m, j)], p42);
+            }
+            const VT s23 = s2 + s3;
+            const VT id = (i == j) ? (VT)1 : (VT)0;
+            A[i][j] = fma(c4, p31, fma(-c2, s1 + s23, id));
+            B[i][j] = (i == j) ? fma(-c3, s23, hv) : -c3 * s23;
+            C[i][j] = fma(c3, p31 + p42, -c1 * (fma((VT)2, s23, s1) + s4));
+            Dm[i][j] = fma(c4, p42, fma(-c2, s23 + s4, id));
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        VT nw[D];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            VT u = A[i][0] * w[j][0], v = C[i][0] * w[j][0];
+#pragma unroll
+            for (int m = 1; m < N; ++m) {
+                u = fma(A[i][m], w[j][m], u);
+                v = fma(C[i][m], w[j][m], v);
+            }
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                u = fma(B[i][m], w[j][N + m], u);
+                v = fma(Dm[i][m], w[j][N + m], v);
+            }
+            nw[i] = u;
+            nw[N + i] = v;
+        }
+#pragma unroll
+        for (int c = 0; c < D; ++c) w[j][c] = nw[c];
+    }
+}
+
+template <class Sys, int K, bool LD, typename VT>
+__device__ __forceinline__ void rk4_step(double* x, VT (*w)[2 * Sys::N], double& L, const double h,
+                                         const int ld_sqrt, const double ld_p, const SysPar& sp)
+{
+    if constexpr (K >= 3)
+        rk4_step_phi<Sys, K, LD, VT>(x, w, L, h, ld_sqrt, ld_p, sp);
+    else
+        rk4_step_direct<Sys, K, LD, VT>(x, w, L, h, ld_sqrt, ld_p, sp);
 }
 
 template <class Sys, int K, bool LD, typename VT>
@@ -403,7 +513,7 @@ k_lyap_small(const StepArgs a, const SysPar sp, const int64_t n, const double* _
 #pragma unroll
                     for (int c = 0; c < D; ++c) n2 = fma(W[j][c], W[j][c], n2);
                     S[j] += 0.5 * log(n2);
-                    const double inv = rsqrt(n2);
+                    const double inv = rsqrt_nr(n2);
 #pragma unroll
                     for (int c = 0; c < D; ++c) W[j][c] *= inv;
                 }
