@@ -43,14 +43,24 @@ def grid_box(E: float):
 
 def flops_per_orbit_step(k: int, ld: bool, vec_fp32: bool) -> tuple[int, int]:
     """Algorithmic flops of one RK4 step of the Henon-Heiles joint system
-    (FMA = 2, sqrt and rsqrt = 1), as (FP64 flops, FP32 flops):
-      per stage: f and Hess V 10, variational 6 per vector, LD 7 (4 sqrt + 3 add)
-      stage inputs (3 stages): 2 flops per state and vector component
-      RK4 accumulation: 7 flops per component of (x, w_1..w_k, L)
-      renormalisation: 12 per vector;  escape test: 3."""
+    (FMA = 2, sqrt and rsqrt = 1), as (FP64 flops, FP32 flops).
+    Orbit (FP64): per stage f and Hess V 10, LD 7 (4 sqrt + 3 add); stage
+      inputs 2 per component (3 stages); accumulation 7 per component of
+      (x, L); escape test 3.
+    FP64 vectors (direct RK4, as the oracle computes them): variational 6 per
+      vector and stage, stage inputs 2 per component (3 stages), accumulation
+      7 per component, renormalisation 12 per vector.
+    FP32 frame: propagator blocks 104, application 32 per vector, Gram-Schmidt
+      16 per vector pair and 13 per vector, triangle update and normalisation
+      74 (for k = 4)."""
     xs = 4 * (10 + (7 if ld else 0)) + 3 * 2 * 4 + 7 * (4 + (1 if ld else 0)) + 3
+    if vec_fp32:
+        tri = sum(2 * (j - i + 1) for j in range(k) for i in range(j + 1))
+        nr = k * (k + 1) // 2
+        vs = 104 + 32 * k + 16 * k * (k - 1) // 2 + 13 * k + tri + 2 * nr + k + nr
+        return xs, vs
     vs = 4 * 6 * k + 3 * 2 * 4 * k + 7 * 4 * k + 12 * k
-    return (xs, vs) if vec_fp32 else (xs + vs, 0)
+    return xs + vs, 0
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
@@ -215,7 +225,7 @@ def run_gpu(args):
     ic_st = torch.empty(n, dtype=torch.int32, device=dev)
     chs.chs_section_grid_ics(S.h, E_GRID, sy0, sy1, rows, p0, p1, npy, ics, ic_st)
     kw = dict(n_dev=K_DEV, ld_p=0.5, escape_r2=4.0, sample_every=100, seed=1 + rank,
-              vec_precision=vp, sali_threshold=1e-6 if vec_fp32 else 1e-8)
+              vec_precision=vp, sali_threshold=1e-8)
     ens = chs.DeviceEnsemble.empty(n, 4, K_DEV, vec_fp32, device=dev)
     abi = ens.abi()
     chs.chs_ensemble_init(S.h, chs.params(DT, 1, **kw), abi, ics, ic_st)

@@ -83,7 +83,7 @@ typedef struct {
     int32_t renorm;          /* 1: normalise each deviation vector after every step */
     int32_t sample_every;    /* health checks at absolute steps divisible by this (0 = never) */
     int32_t qr_every;        /* Lyapunov: QR of the vectors every qr_every steps and at the end */
-    int32_t vec_precision;   /* CHS_VEC_FP64 or CHS_VEC_FP32 */
+    int32_t vec_precision;   /* CHS_VEC_FP64 or CHS_VEC_FP32 (FP32 requires renorm = 1) */
     int32_t reserved;        /* must be 0 */
     double ld_p;             /* LD exponent p (LD integrand sum_i |dx_i/dt|^p); 0 = no LD */
     double escape_r2;        /* ESCAPED when sum_i q_i^2 > escape_r2; 0 = off */
@@ -94,7 +94,15 @@ typedef struct {
 
 /* Resumable ensemble state: caller-owned device arrays over n_orbits orbits.
  *   x       [d][n]    phase-space state (FP64)
- *   w       [k*d][n]  deviation vectors, FP64 or FP32 per vec_precision (NULL when k = 0)
+ *   w       deviation vectors (NULL when k = 0):
+ *           CHS_VEC_FP64: [k*d][n] FP64, row j*d + c = component c of vector j;
+ *           CHS_VEC_FP32: [k*d + k(k+1)/2][n] FP32, the vectors as W = Q R D:
+ *             rows j*d + c hold the orthonormal frame Q (column j, component c),
+ *             rows k*d + j(j+1)/2 + i hold the upper-triangular R (i <= j) with
+ *             unit columns; D is a positive diagonal that is not stored.  The
+ *             unit vectors are w_j / |w_j| = sum_i R_ij q_i.  Each diagonal entry
+ *             of R keeps its relative precision however small it gets, so SALI
+ *             and GALI do not stall at the FP32 rounding level.
  *   ld      [n]       forward LD accumulator M_p (NULL when ld_p = 0)
  *   h0      [n]       energy at t = 0
  *   dh_max  [n]       largest |H - H0| seen at health checks
@@ -149,11 +157,13 @@ chs_status chs_fput_mode_ics(chs_system s, int64_t n, const double* Qm, const do
 /* Initialises an ensemble from initial conditions `ics` [d][n]:
  * x <- ics; status <- ic_status (or OK when NULL), NONFINITE for a non-finite
  * OK state; h0 <- H(x); dh_max, n_exec, ld <- 0; the k = p->n_dev deviation
- * vectors are copied from w_in ([k*d][n], same precision as the ensemble) or,
+ * vectors are copied from w_in ([k*d][n] plain vectors, FP64 or FP32 per
+ * vec_precision) or,
  * when w_in is NULL, seeded on the device: component c of vector j of orbit o
  * is the m-th SplitMix64 output (m = (o*k + j)*d + c + 1) of the stream seeded
  * with p->seed, mapped to [-1, 1) by its top 53 bits.  Vectors are normalised
- * when p->renorm is set. */
+ * when p->renorm is set.  In FP32 mode the normalised vectors are factorised
+ * in FP64 into the frame Q and triangle R described at chs_ensemble. */
 chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemble* e,
                              const double* ics, const int32_t* ic_status, const void* w_in,
                              void* stream);
@@ -166,7 +176,9 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
  * the fixed-step integrator of Sec. Functionalities (RK4 in place of DOP8).
  * After each step: vectors are renormalised when p->renorm is set ("DOP 8 ODE
  * solver with fixed step size that includes the normalization of the
- * deviation vectors"); an orbit with sum_i q_i^2 > escape_r2 freezes as
+ * deviation vectors"); in FP32 mode the frame Q is advanced by the exact
+ * one-step RK4 propagator of the variational equations and re-orthonormalised
+ * (Phi Q = Q' S, R <- S R with unit columns), the orbit and LD staying FP64; an orbit with sum_i q_i^2 > escape_r2 freezes as
  * ESCAPED.  At absolute steps divisible by sample_every: non-finite -> frozen
  * NONFINITE; dh_max <- max(dh_max, |H - h0|); |H - h0| > dh_limit -> frozen
  * ENERGY_DRIFT.  Splitting a run into calls with consecutive step0 gives
@@ -180,7 +192,9 @@ chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ense
  *                       vectors (refs Skokos2001/03/04); needs k >= 2.
  *   gali_out [k-1][n]   GALI_m, m = 2..k: the product of the singular values
  *                       of the d x m matrix of the first m unit vectors (ref
- *                       Skokos2008), computed as prod |R_ii| of its QR.
+ *                       Skokos2008), computed as prod |R_ii| of its QR (FP32
+ *                       mode: of the stored triangle R, and SALI as
+ *                       R_11 sqrt(2 / (1 + |R_01|))).
  *   label_out [n]       1 chaotic (SALI < sali_threshold), 0 regular,
  *                       2 ESCAPED, -1 any other non-OK status.
  *   ld_ind_out [2][n]   when grid_ny * grid_npy == n and the ensemble has an

@@ -193,6 +193,27 @@ class System:
             pass
 
 
+def vector_rows(k: int, d: int, vec_fp32: bool) -> int:
+    """Rows of the ensemble's vector buffer: k*d (FP64), k*d + k(k+1)/2 (FP32 frame)."""
+    if k <= 0:
+        return 1
+    return k * d + (k * (k + 1) // 2 if vec_fp32 else 0)
+
+
+def frame_to_vectors(w, k: int, d: int):
+    """Unit vectors w_j / |w_j| = sum_i R_ij q_i from an FP32-mode vector buffer
+    (host-side inspection helper; works on numpy arrays [rows, n])."""
+    import numpy as np
+    w = np.asarray(w, dtype=np.float64)
+    n = w.shape[1]
+    Q = w[: k * d].reshape(k, d, n)
+    out = np.zeros((k, d, n))
+    for j in range(k):
+        for i in range(j + 1):
+            out[j] += w[k * d + j * (j + 1) // 2 + i] * Q[i]
+    return out.reshape(k * d, n)
+
+
 @dataclass
 class DeviceEnsemble:
     """Caller-owned device buffers of a resumable ensemble (see chs_ensemble)."""
@@ -209,7 +230,7 @@ class DeviceEnsemble:
         f64 = dict(dtype=torch.float64, device=device)
         wdt = torch.float32 if vec_fp32 else torch.float64
         return cls(x=torch.empty((d, n), **f64),
-                   w=torch.empty((max(k, 1) * d, n), dtype=wdt, device=device),
+                   w=torch.empty((vector_rows(k, d, vec_fp32), n), dtype=wdt, device=device),
                    ld=torch.zeros(n, **f64), h0=torch.empty(n, **f64), dh_max=torch.empty(n, **f64),
                    n_exec=torch.empty(n, dtype=torch.int64, device=device),
                    status=torch.empty(n, dtype=torch.int32, device=device))

@@ -69,6 +69,8 @@ chs_status check_params(const chs_params* p, const chs::SysPar& sp)
     if (p->vec_precision != CHS_VEC_FP64 && p->vec_precision != CHS_VEC_FP32)
         return fail(CHS_E_INVALID, "vec_precision must be CHS_VEC_FP64 or CHS_VEC_FP32");
     if (p->reserved != 0) return fail(CHS_E_INVALID, "reserved must be 0");
+    if (p->vec_precision == CHS_VEC_FP32 && p->n_dev > 0 && p->renorm != 1)
+        return fail(CHS_E_INVALID, "FP32 vectors are re-orthonormalised every step: renorm must be 1");
     if (!(p->ld_p >= 0.0) || !isfinite(p->ld_p)) return fail(CHS_E_INVALID, "ld_p must be finite and >= 0");
     if (!(p->escape_r2 >= 0.0)) return fail(CHS_E_INVALID, "escape_r2 must be >= 0");
     if (!(p->dh_limit >= 0.0)) return fail(CHS_E_INVALID, "dh_limit must be >= 0");

@@ -57,6 +57,14 @@ cudaError_t launch_integrate(const SysPar& sp, int k, int vec_fp32, bool ld, con
 cudaError_t launch_indicators(const SysPar& sp, int k, int vec_fp32, double sali_threshold,
                               const EnsPtrs& e, double* sali, double* gali, int8_t* label,
                               cudaStream_t st);
+// FP32 deviation vectors held as an orthonormal frame plus a triangular factor
+cudaError_t launch_init_f32(const SysPar& sp, int k, uint64_t seed, const double* ics,
+                            const int32_t* ic_status, const void* w_in, const EnsPtrs& e,
+                            cudaStream_t st);
+cudaError_t launch_integrate_f32(const SysPar& sp, int k, bool ld, const StepArgs& a,
+                                 const EnsPtrs& e, cudaStream_t st);
+cudaError_t launch_indicators_f32(const SysPar& sp, int k, double sali_threshold, const EnsPtrs& e,
+                                  double* sali, double* gali, int8_t* label, cudaStream_t st);
 cudaError_t launch_ld_stencil(int ny, int npy, const double* ld, const int32_t* status,
                               double* out, cudaStream_t st);
 cudaError_t launch_lyap_small(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,

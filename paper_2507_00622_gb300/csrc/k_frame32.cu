@@ -1,0 +1,429 @@
+// k_frame32.cu -- FP32 deviation vectors with an FP64 orbit (one orbit per thread).
+//
+// FP32 vectors renormalised one by one cannot resolve small SALI or GALI
+// values: every step injects rounding of relative size eps32 ~ 6e-8 into each
+// vector while the flow aligns them only by a factor exp(-(l1 - l2) h) per
+// step, so the computed angle between two vectors stalls near
+// eps32 / ((l1 - l2) h) ~ 1e-4 for chaotic Henon-Heiles orbits at h = 0.01.
+//
+// This mode therefore stores the k vectors as W = Q R D: an orthonormal frame
+// Q (d x k, FP32) and an upper-triangular R with unit columns (FP32), D an
+// irrelevant positive diagonal.  Each step applies the exact one-step RK4
+// propagator Phi to Q, re-orthonormalises it by modified Gram-Schmidt,
+// Phi Q = Q' S, and updates R <- colnorm(S R).  Every diagonal entry of R only
+// ever gets multiplied by S_jj and divided by a column norm, so it keeps its
+// relative precision however small it becomes:
+//   GALI_m = prod_{j < m} R_jj,   SALI = R_11 sqrt(2 / (1 + |R_01|)),
+// which are the GALI and SALI of the unit vectors w_j / |w_j| (the re-
+// orthonormalisation of every step is the per-step renormalisation).  The
+// orbit, its energy check and the LD stay in FP64.
+//
+// Ensemble vector buffer in this mode: FP32, [k*d + k(k+1)/2][n]: rows j*d + c
+// hold Q (vector j, component c), rows k*d + j(j+1)/2 + i hold R_ij (i <= j).
+#include <math.h>
+
+#include "rk4_common.cuh"
+
+namespace chs {
+
+__host__ __device__ constexpr int tri(int i, int j) { return j * (j + 1) / 2 + i; }
+
+// Round-to-nearest FP64 -> FP32 on the integer pipe (no FP64-pipe conversion):
+// values below FLT_MIN flush to zero, values beyond FLT_MAX become infinity.
+__device__ __forceinline__ float f32_from_f64(double a)
+{
+    const long long r = __double_as_longlong(a) + (1LL << 28);
+    const int hi = (int)(r >> 32);
+    const unsigned lo = (unsigned)r;
+    const int sgn = hi & (int)0x80000000;
+    const int ah = hi & 0x7fffffff;
+    int fb = ((ah - kBiasShift) << 3) | (int)(lo >> 29);
+    fb = ah < ((1023 - 126) << 20) ? 0 : fb;
+    fb = ah >= ((1023 + 128) << 20) ? 0x7f800000 : fb;
+    return __int_as_float(fb | sgn);
+}
+
+__device__ __forceinline__ uint64_t splitmix64_at32(uint64_t seed, uint64_t m)
+{
+    uint64_t z = seed + m * 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+template <class Sys, int K>
+__global__ void __launch_bounds__(kSmallBlock)
+k_init_f32(const SysPar sp, const uint64_t seed, const double* __restrict__ ics,
+           const int32_t* __restrict__ ic_status, const float* __restrict__ w_in, const EnsPtrs e)
+{
+    constexpr int D = 2 * Sys::N;
+    const int64_t n = e.n;
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    double x[D];
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        x[c] = ics[c * n + o];
+        e.x[c * n + o] = x[c];
+        finite = finite && isfinite(x[c]);
+    }
+    int32_t st = ic_status ? ic_status[o] : CHS_ORBIT_OK;
+    if (st == CHS_ORBIT_OK && !finite) st = CHS_ORBIT_NONFINITE;
+    e.status[o] = st;
+    e.h0[o] = (st == CHS_ORBIT_OK) ? Sys::energy(x, sp) : __longlong_as_double(0x7ff8000000000000LL);
+    e.dh_max[o] = 0.0;
+    e.n_exec[o] = 0;
+    if (e.ld) e.ld[o] = 0.0;
+    // unit vectors (FP64), then Q R by modified Gram-Schmidt
+    double V[K][D];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            if (w_in) {
+                V[j][c] = (double)w_in[(j * D + c) * n + o];
+            } else {
+                const uint64_t m = ((uint64_t)o * K + j) * D + c + 1;
+                const uint64_t z = splitmix64_at32(seed, m);
+                V[j][c] = __dsub_rn(__dmul_rn(2.0, __dmul_rn((double)(z >> 11), 0x1.0p-53)), 1.0);
+            }
+        }
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) acc = __dadd_rn(acc, __dmul_rn(V[j][c], V[j][c]));
+        const double nr = __dsqrt_rn(acc);
+#pragma unroll
+        for (int c = 0; c < D; ++c) V[j][c] = __ddiv_rn(V[j][c], nr);
+    }
+    double R[K * (K + 1) / 2];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+#pragma unroll
+        for (int i = 0; i < j; ++i) {
+            double r = 0.0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) r = fma(V[i][c], V[j][c], r);
+#pragma unroll
+            for (int c = 0; c < D; ++c) V[j][c] = fma(-r, V[i][c], V[j][c]);
+            R[tri(i, j)] = r;
+        }
+        double n2 = 0.0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) n2 = fma(V[j][c], V[j][c], n2);
+        const double rjj = sqrt(n2);
+        R[tri(j, j)] = rjj;
+#pragma unroll
+        for (int c = 0; c < D; ++c) V[j][c] /= rjj;
+    }
+    float* wg = static_cast<float*>(e.w);
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = (float)V[j][c];
+#pragma unroll
+    for (int p = 0; p < K * (K + 1) / 2; ++p) wg[(K * D + p) * n + o] = (float)R[p];
+}
+
+template <class Sys, int K, bool LD>
+__global__ void __launch_bounds__(kSmallBlock)
+k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e)
+{
+    constexpr int N = Sys::N, D = 2 * N, NH = Sys::NH, NR = K * (K + 1) / 2;
+    const int64_t n = e.n;
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    if (e.status[o] != CHS_ORBIT_OK) return;
+
+    float* wg = static_cast<float*>(e.w);
+    double x[D];
+    float Q[K][D], R[NR];
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int c = 0; c < D; ++c) Q[j][c] = wg[(j * D + c) * n + o];
+#pragma unroll
+    for (int p = 0; p < NR; ++p) R[p] = wg[(K * D + p) * n + o];
+    double L = LD ? e.ld[o] : 0.0;
+    const double h0 = e.h0[o];
+    double dhm = e.dh_max[o];
+
+    int32_t st = CHS_ORBIT_OK;
+    int64_t until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
+    int64_t s = 0;
+    while (s < a.n_steps) {
+        ++s;
+        double H[4][NH];
+        rk4_state_capture<Sys, LD>(x, L, a.dt, a.ld_sqrt, a.ld_p, sp, H);
+        float Hf[4][NH];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int i = 0; i < NH; ++i) Hf[q][i] = f32_from_f64(H[q][i]);
+        PhiBlocks<N, float> P;
+        phi_build<N, NH, float>(Hf, a.dt, P);
+#pragma unroll
+        for (int j = 0; j < K; ++j) phi_apply<N, float>(P, Q[j]);
+        // Phi Q = Q' S (modified Gram-Schmidt), then R <- colnorm(S R)
+        float S[NR];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+#pragma unroll
+            for (int i = 0; i < j; ++i) {
+                float r = Q[i][0] * Q[j][0];
+#pragma unroll
+                for (int c = 1; c < D; ++c) r = fmaf(Q[i][c], Q[j][c], r);
+#pragma unroll
+                for (int c = 0; c < D; ++c) Q[j][c] = fmaf(-r, Q[i][c], Q[j][c]);
+                S[tri(i, j)] = r;
+            }
+            float n2 = Q[j][0] * Q[j][0];
+#pragma unroll
+            for (int c = 1; c < D; ++c) n2 = fmaf(Q[j][c], Q[j][c], n2);
+            const float inv = rsqrtf(n2);
+            S[tri(j, j)] = n2 * inv;
+#pragma unroll
+            for (int c = 0; c < D; ++c) Q[j][c] *= inv;
+        }
+#pragma unroll
+        for (int j = K - 1; j >= 0; --j) {
+            float col[K];
+            float nn = 0.0f;
+#pragma unroll
+            for (int i = 0; i <= j; ++i) {
+                float t = 0.0f;
+#pragma unroll
+                for (int m = i; m <= j; ++m) t = fmaf(S[tri(i, m)], R[tri(m, j)], t);
+                col[i] = t;
+                nn = fmaf(t, t, nn);
+            }
+            const float inv = rsqrtf(nn);
+#pragma unroll
+            for (int i = 0; i <= j; ++i) R[tri(i, j)] = col[i] * inv;
+        }
+        if (a.escape_r2 > 0.0) {
+            double r2 = x[0] * x[0];
+#pragma unroll
+            for (int i = 1; i < N; ++i) r2 = fma(x[i], x[i], r2);
+            if (r2 > a.escape_r2) {
+                st = CHS_ORBIT_ESCAPED;
+                break;
+            }
+        }
+        if (--until == 0) {
+            until = a.sample_every;
+            bool fin = isfinite(L);
+#pragma unroll
+            for (int c = 0; c < D; ++c) fin = fin && isfinite(x[c]);
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int c = 0; c < D; ++c) fin = fin && isfinite(Q[j][c]);
+            if (!fin) {
+                st = CHS_ORBIT_NONFINITE;
+                break;
+            }
+            const double dH = fabs(Sys::energy(x, sp) - h0);
+            dhm = fmax(dhm, dH);
+            if (a.dh_limit > 0.0 && dH > a.dh_limit) {
+                st = CHS_ORBIT_ENERGY_DRIFT;
+                break;
+            }
+        }
+    }
+
+#pragma unroll
+    for (int c = 0; c < D; ++c) e.x[c * n + o] = x[c];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = Q[j][c];
+#pragma unroll
+    for (int p = 0; p < NR; ++p) wg[(K * D + p) * n + o] = R[p];
+    if (LD) e.ld[o] = L;
+    e.dh_max[o] = dhm;
+    e.n_exec[o] += s;
+    e.status[o] = st;
+}
+
+// SALI, GALI_m and labels from the triangular factor (see the file comment).
+template <int D, int K>
+__global__ void __launch_bounds__(kSmallBlock)
+k_indicators_f32(const int64_t n, const float* __restrict__ wg, const int32_t* __restrict__ status,
+                 const double thr, double* __restrict__ sali, double* __restrict__ gali,
+                 int8_t* __restrict__ label)
+{
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int32_t st = status[o];
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    const bool forb = st == CHS_ORBIT_FORBIDDEN;
+    double sv = qnan;
+    if (K >= 2 && !forb) {
+        const double a01 = fabs((double)wg[(K * D + tri(0, 1 % K)) * n + o]);
+        const double b11 = fabs((double)wg[(K * D + tri(1 % K, 1 % K)) * n + o]);
+        sv = b11 * sqrt(2.0 / (1.0 + fmin(a01, 1.0)));
+    }
+    if (sali) sali[o] = sv;
+    if (gali) {
+        double prod = 1.0;
+#pragma unroll
+        for (int j = 1; j < K; ++j) {
+            prod *= fabs((double)wg[(K * D + tri(j, j)) * n + o]);
+            gali[(int64_t)(j - 1) * n + o] = forb ? qnan : prod;
+        }
+    }
+    if (label) {
+        int8_t lb;
+        if (st == CHS_ORBIT_OK)
+            lb = (sv < thr) ? 1 : 0;
+        else if (st == CHS_ORBIT_ESCAPED)
+            lb = 2;
+        else
+            lb = -1;
+        label[o] = lb;
+    }
+}
+
+// --------------------------------------------------------------------------
+// dispatch
+// --------------------------------------------------------------------------
+
+template <class Sys, int K>
+static void init_one(const unsigned g, const SysPar& sp, uint64_t seed, const double* ics,
+                     const int32_t* ics_st, const float* wi, const EnsPtrs& e, cudaStream_t st)
+{
+    k_init_f32<Sys, K><<<g, kSmallBlock, 0, st>>>(sp, seed, ics, ics_st, wi, e);
+}
+
+template <class Sys>
+static cudaError_t init_sys(int k, const SysPar& sp, uint64_t seed, const double* ics,
+                            const int32_t* ics_st, const void* w_in, const EnsPtrs& e, cudaStream_t st)
+{
+    const unsigned g = blocks_for(e.n, kSmallBlock);
+    const float* wi = static_cast<const float*>(w_in);
+    switch (k) {
+    case 1: init_one<Sys, 1>(g, sp, seed, ics, ics_st, wi, e, st); break;
+    case 2: init_one<Sys, 2>(g, sp, seed, ics, ics_st, wi, e, st); break;
+    case 3: init_one<Sys, 3>(g, sp, seed, ics, ics_st, wi, e, st); break;
+    case 4: init_one<Sys, 4>(g, sp, seed, ics, ics_st, wi, e, st); break;
+    case 5:
+        if constexpr (Sys::N >= 3) {
+            init_one<Sys, 5>(g, sp, seed, ics, ics_st, wi, e, st);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    case 6:
+        if constexpr (Sys::N >= 3) {
+            init_one<Sys, 6>(g, sp, seed, ics, ics_st, wi, e, st);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_f32(const SysPar& sp, int k, uint64_t seed, const double* ics,
+                            const int32_t* ic_status, const void* w_in, const EnsPtrs& e,
+                            cudaStream_t st)
+{
+    if (e.n == 0) return cudaSuccess;
+    switch (sp.model) {
+    case CHS_HENON_HEILES: return init_sys<SysHenonHeiles>(k, sp, seed, ics, ic_status, w_in, e, st);
+    case CHS_HARMONIC: return init_sys<SysHarmonic>(k, sp, seed, ics, ic_status, w_in, e, st);
+    case CHS_INVERTED: return init_sys<SysInverted>(k, sp, seed, ics, ic_status, w_in, e, st);
+    case CHS_QUARTIC3: return init_sys<SysQuartic3>(k, sp, seed, ics, ic_status, w_in, e, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <class Sys, int K, bool LD>
+static void integ_one(const unsigned g, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
+                      cudaStream_t st)
+{
+    k_integrate_f32<Sys, K, LD><<<g, kSmallBlock, 0, st>>>(a, sp, e);
+}
+
+template <class Sys, bool LD>
+static cudaError_t integ_sys(int k, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
+                             cudaStream_t st)
+{
+    const unsigned g = blocks_for(e.n, kSmallBlock);
+    switch (k) {
+    case 1: integ_one<Sys, 1, LD>(g, a, sp, e, st); break;
+    case 2: integ_one<Sys, 2, LD>(g, a, sp, e, st); break;
+    case 3: integ_one<Sys, 3, LD>(g, a, sp, e, st); break;
+    case 4: integ_one<Sys, 4, LD>(g, a, sp, e, st); break;
+    case 5:
+        if constexpr (Sys::N >= 3) {
+            integ_one<Sys, 5, LD>(g, a, sp, e, st);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    case 6:
+        if constexpr (Sys::N >= 3) {
+            integ_one<Sys, 6, LD>(g, a, sp, e, st);
+            break;
+        }
+        return cudaErrorInvalidValue;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrate_f32(const SysPar& sp, int k, bool ld, const StepArgs& a,
+                                 const EnsPtrs& e, cudaStream_t st)
+{
+    if (e.n == 0 || a.n_steps == 0) return cudaSuccess;
+    switch (sp.model) {
+    case CHS_HENON_HEILES:
+        return ld ? integ_sys<SysHenonHeiles, true>(k, a, sp, e, st)
+                  : integ_sys<SysHenonHeiles, false>(k, a, sp, e, st);
+    case CHS_HARMONIC:
+        return ld ? integ_sys<SysHarmonic, true>(k, a, sp, e, st)
+                  : integ_sys<SysHarmonic, false>(k, a, sp, e, st);
+    case CHS_INVERTED:
+        return ld ? integ_sys<SysInverted, true>(k, a, sp, e, st)
+                  : integ_sys<SysInverted, false>(k, a, sp, e, st);
+    case CHS_QUARTIC3:
+        return ld ? integ_sys<SysQuartic3, true>(k, a, sp, e, st)
+                  : integ_sys<SysQuartic3, false>(k, a, sp, e, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int D>
+static cudaError_t ind_f32(int k, double thr, const EnsPtrs& e, double* sali, double* gali,
+                           int8_t* label, cudaStream_t st)
+{
+    const unsigned g = blocks_for(e.n, kSmallBlock);
+    const float* w = static_cast<const float*>(e.w);
+    switch (k) {
+#define CHS_CASE(KV)                                                                                \
+    case KV:                                                                                        \
+        k_indicators_f32<D, KV><<<g, kSmallBlock, 0, st>>>(e.n, w, e.status, thr, sali, gali, label); \
+        break;
+        CHS_CASE(1) CHS_CASE(2) CHS_CASE(3) CHS_CASE(4) CHS_CASE(5) CHS_CASE(6)
+#undef CHS_CASE
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_indicators_f32(const SysPar& sp, int k, double sali_threshold, const EnsPtrs& e,
+                                  double* sali, double* gali, int8_t* label, cudaStream_t st)
+{
+    if (e.n == 0) return cudaSuccess;
+    const int D = 2 * sp.n_dof;
+    if (D == 4) return ind_f32<4>(k, sali_threshold, e, sali, gali, label, st);
+    if (D == 6) return ind_f32<6>(k, sali_threshold, e, sali, gali, label, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace chs

@@ -8,9 +8,7 @@
 // FP64 pipe (GB300: 2 DFMA/clk/SM), not by HBM.
 #include <math.h>
 
-#include "chs_internal.cuh"
-#include "fastmath.cuh"
-#include "systems.cuh"
+#include "rk4_common.cuh"
 
 namespace chs {
 
@@ -100,24 +98,6 @@ __device__ __forceinline__ void var_rhs(const VT* Hc, const VT* w, VT* dw)
     }
 }
 
-// LD integrand sum_i |f_i|^p (p = 1/2: Newton-refined square roots).
-template <int D>
-__device__ __forceinline__ double ld_integrand(const double* f, int ld_sqrt, double p)
-{
-    double acc = 0.0;
-    if (ld_sqrt) {
-#pragma unroll
-        for (int i = 0; i < D; ++i) acc += sqrt_nr(fabs(f[i]));
-    } else {
-#pragma unroll
-        for (int i = 0; i < D; ++i) acc += pow(fabs(f[i]), p);
-    }
-    return acc;
-}
-
-__device__ __forceinline__ float rsqrt_vt(float v) { return rsqrtf(v); }
-__device__ __forceinline__ double rsqrt_vt(double v) { return rsqrt_nr(v); }
-
 // One classic RK4 step of (x, w_1..w_K, L):
 //   k1 = F(z), k2 = F(z + h/2 k1), k3 = F(z + h/2 k2), k4 = F(z + h k3),
 //   z <- z + h/6 (k1 + 2 k2 + 2 k3 + k4),
@@ -197,113 +177,34 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
 }
 
 // The same RK4 step with the vectors advanced by the exact one-step propagator
-// of RK4 on the linear variational equation w' = J_s w, J_s = [[0, I], [-H_s, 0]]
-// (H_s = Hess V at stage s):
-//   Phi = I + h/6 (J1 + 2J2 + 2J3 + J4) + h^2/6 (J2J1 + J3J2 + J4J3)
-//           + h^3/12 (J3J2J1 + J4J3J2) + h^4/24 J4J3J2J1
-//       = [[I - h^2/6 (H1+H2+H3) + h^4/24 H3H1,   h I - h^3/12 (H2+H3)],
-//          [-h/6 (H1+2H2+2H3+H4) + h^3/12 (H3H1 + H4H2),
-//                                 I - h^2/6 (H2+H3+H4) + h^4/24 H4H2]].
-// Identical to the direct form in exact arithmetic; for k >= 3 vectors it needs
-// fewer operations (Phi is built once and applied to each vector).
-template <class Sys, int K, bool LD, typename VT>
-__device__ __forceinline__ void rk4_step_phi(double* x, VT (*w)[2 * Sys::N], double& L,
+// Phi of RK4 on the variational equations (rk4_common.cuh); identical to the
+// direct form in exact arithmetic and cheaper for k >= 3 vectors (Phi is built
+// once per step and applied to each vector).
+template <class Sys, int K, bool LD>
+__device__ __forceinline__ void rk4_step_phi(double* x, double (*w)[2 * Sys::N], double& L,
                                              const double h, const int ld_sqrt, const double ld_p,
                                              const SysPar& sp)
 {
-    constexpr int N = Sys::N, D = 2 * N, NH = Sys::NH;
-    const double hh = 0.5 * h, h6 = h / 6.0;
-    double ax[D], xs[D], f[D], H[4][NH];
-    double aL = 0.0;
-
-    Sys::eval(x, f, H[0], sp);
+    double H[4][Sys::NH];
+    rk4_state_capture<Sys, LD>(x, L, h, ld_sqrt, ld_p, sp, H);
+    PhiBlocks<Sys::N, double> P;
+    phi_build<Sys::N, Sys::NH, double>(H, h, P);
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-        ax[c] = f[c];
-        xs[c] = fma(hh, f[c], x[c]);
-    }
-    if (LD) aL = ld_integrand<D>(f, ld_sqrt, ld_p);
-#pragma unroll
-    for (int s = 1; s < 3; ++s) {
-        const double cs = (s == 1) ? hh : h;
-        Sys::eval(xs, f, H[s], sp);
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            ax[c] = fma(2.0, f[c], ax[c]);
-            xs[c] = fma(cs, f[c], x[c]);
-        }
-        if (LD) aL = fma(2.0, ld_integrand<D>(f, ld_sqrt, ld_p), aL);
-    }
-    Sys::eval(xs, f, H[3], sp);
-#pragma unroll
-    for (int c = 0; c < D; ++c) x[c] = fma(h6, ax[c] + f[c], x[c]);
-    if (LD) L = fma(h6, aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
-
-    // Phi blocks in the vector precision
-    VT Hs[4][NH];
-#pragma unroll
-    for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int i = 0; i < NH; ++i) Hs[s][i] = (VT)H[s][i];
-    const VT hv = (VT)h, c1 = (VT)(h / 6.0), c2 = (VT)(h * h / 6.0), c3 = (VT)(h * h * h / 12.0),
-             c4 = (VT)(h * h * h * h / 24.0);
-    VT A[N][N], B[N][N], C[N][N], Dm[N][N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) {
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const VT s1 = Hs[0][hidx<N>(i, j)], s2 = Hs[1][hidx<N>(i, j)];
-            const VT s3 = Hs[2][hidx<N>(i, j)], s4 = Hs[3][hidx<N>(i, j)];
-            VT p31 = Hs[2][hidx<N>(i, 0)] * Hs[0][hidx<N>(0, j)];
-            VT p42 = Hs[3][hidx<N>(i, 0)] * Hs[1][hidx<N>(0, j)];
-#pragma unroll
-            for (int m = 1; m < N; ++m) {
-                p31 = fma(Hs[2][hidx<N>(i, m)], Hs[0][hidx<N>(m, j)], p31);
-                p42 = fma(Hs[3][hidx<N>(i, m)], Hs[1][hidx<N>(m, j)], p42);
-            }
-            const VT s23 = s2 + s3;
-            const VT id = (i == j) ? (VT)1 : (VT)0;
-            A[i][j] = fma(c4, p31, fma(-c2, s1 + s23, id));
-            B[i][j] = (i == j) ? fma(-c3, s23, hv) : -c3 * s23;
-            C[i][j] = fma(c3, p31 + p42, -c1 * (fma((VT)2, s23, s1) + s4));
-            Dm[i][j] = fma(c4, p42, fma(-c2, s23 + s4, id));
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        VT nw[D];
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            VT u = A[i][0] * w[j][0], v = C[i][0] * w[j][0];
-#pragma unroll
-            for (int m = 1; m < N; ++m) {
-                u = fma(A[i][m], w[j][m], u);
-                v = fma(C[i][m], w[j][m], v);
-            }
-#pragma unroll
-            for (int m = 0; m < N; ++m) {
-                u = fma(B[i][m], w[j][N + m], u);
-                v = fma(Dm[i][m], w[j][N + m], v);
-            }
-            nw[i] = u;
-            nw[N + i] = v;
-        }
-#pragma unroll
-        for (int c = 0; c < D; ++c) w[j][c] = nw[c];
-    }
+    for (int j = 0; j < K; ++j) phi_apply<Sys::N, double>(P, w[j]);
 }
 
-template <class Sys, int K, bool LD, typename VT>
-__device__ __forceinline__ void rk4_step(double* x, VT (*w)[2 * Sys::N], double& L, const double h,
-                                         const int ld_sqrt, const double ld_p, const SysPar& sp)
+template <class Sys, int K, bool LD>
+__device__ __forceinline__ void rk4_step(double* x, double (*w)[2 * Sys::N], double& L,
+                                         const double h, const int ld_sqrt, const double ld_p,
+                                         const SysPar& sp)
 {
     if constexpr (K >= 3)
-        rk4_step_phi<Sys, K, LD, VT>(x, w, L, h, ld_sqrt, ld_p, sp);
+        rk4_step_phi<Sys, K, LD>(x, w, L, h, ld_sqrt, ld_p, sp);
     else
-        rk4_step_direct<Sys, K, LD, VT>(x, w, L, h, ld_sqrt, ld_p, sp);
+        rk4_step_direct<Sys, K, LD, double>(x, w, L, h, ld_sqrt, ld_p, sp);
 }
 
-template <class Sys, int K, bool LD, typename VT>
+template <class Sys, int K, bool LD>
 __global__ void __launch_bounds__(kSmallBlock)
 k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e)
 {
@@ -314,9 +215,9 @@ k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e)
     if (o >= n) return;
     if (e.status[o] != CHS_ORBIT_OK) return;
 
-    VT* wg = static_cast<VT*>(e.w);
+    double* wg = static_cast<double*>(e.w);
     double x[D];
-    VT w[KK][D];
+    double w[KK][D];
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
 #pragma unroll
@@ -332,14 +233,14 @@ k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e)
     int64_t s = 0;
     while (s < a.n_steps) {
         ++s;
-        rk4_step<Sys, K, LD, VT>(x, w, L, a.dt, a.ld_sqrt, a.ld_p, sp);
+        rk4_step<Sys, K, LD>(x, w, L, a.dt, a.ld_sqrt, a.ld_p, sp);
         if (a.renorm) {
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                VT n2 = w[j][0] * w[j][0];
+                double n2 = w[j][0] * w[j][0];
 #pragma unroll
                 for (int c = 1; c < D; ++c) n2 = fma(w[j][c], w[j][c], n2);
-                const VT inv = rsqrt_vt(n2);
+                const double inv = rsqrt_nr(n2);
 #pragma unroll
                 for (int c = 0; c < D; ++c) w[j][c] *= inv;
             }
@@ -361,7 +262,7 @@ k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e)
 #pragma unroll
             for (int j = 0; j < K; ++j)
 #pragma unroll
-                for (int c = 0; c < D; ++c) fin = fin && isfinite((double)w[j][c]);
+                for (int c = 0; c < D; ++c) fin = fin && isfinite(w[j][c]);
             if (!fin) {
                 st = CHS_ORBIT_NONFINITE;
                 break;
@@ -496,7 +397,7 @@ k_lyap_small(const StepArgs a, const SysPar sp, const int64_t n, const double* _
         int64_t until_qr = a.qr_every;
         int64_t until = a.sample_every > 0 ? a.sample_every : -1;
         for (int64_t s = 1; s <= a.n_steps; ++s) {
-            rk4_step<Sys, D, false, double>(x, W, L, a.dt, 0, 0.0, sp);
+            rk4_step<Sys, D, false>(x, W, L, a.dt, 0, 0.0, sp);
             if (--until_qr == 0 || s == a.n_steps) {
                 until_qr = a.qr_every;
 #pragma unroll
@@ -546,28 +447,28 @@ bool small_model(int model)
            model == CHS_QUARTIC3;
 }
 
-template <class Sys, typename VT>
+template <class Sys>
 static cudaError_t init_k(int k, const SysPar& sp, int renorm, uint64_t seed, const double* ics,
                           const int32_t* ics_st, const void* w_in, const EnsPtrs& e, cudaStream_t st)
 {
     const unsigned g = blocks_for(e.n, kSmallBlock);
-    const VT* wi = static_cast<const VT*>(w_in);
+    const double* wi = static_cast<const double*>(w_in);
     switch (k) {
-#define CHS_CASE(KV)                                                                           \
-    case KV:                                                                                   \
-        k_init<Sys, KV, VT><<<g, kSmallBlock, 0, st>>>(sp, renorm, seed, ics, ics_st, wi, e); \
+#define CHS_CASE(KV)                                                                               \
+    case KV:                                                                                       \
+        k_init<Sys, KV, double><<<g, kSmallBlock, 0, st>>>(sp, renorm, seed, ics, ics_st, wi, e); \
         break;
         CHS_CASE(0) CHS_CASE(1) CHS_CASE(2) CHS_CASE(3) CHS_CASE(4)
 #undef CHS_CASE
     case 5:
         if constexpr (Sys::N >= 3) {
-            k_init<Sys, 5, VT><<<g, kSmallBlock, 0, st>>>(sp, renorm, seed, ics, ics_st, wi, e);
+            k_init<Sys, 5, double><<<g, kSmallBlock, 0, st>>>(sp, renorm, seed, ics, ics_st, wi, e);
             break;
         }
         return cudaErrorInvalidValue;
     case 6:
         if constexpr (Sys::N >= 3) {
-            k_init<Sys, 6, VT><<<g, kSmallBlock, 0, st>>>(sp, renorm, seed, ics, ics_st, wi, e);
+            k_init<Sys, 6, double><<<g, kSmallBlock, 0, st>>>(sp, renorm, seed, ics, ics_st, wi, e);
             break;
         }
         return cudaErrorInvalidValue;
@@ -575,15 +476,6 @@ static cudaError_t init_k(int k, const SysPar& sp, int renorm, uint64_t seed, co
         return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
-}
-
-template <class Sys>
-static cudaError_t init_sys(int k, int fp32, const SysPar& sp, int renorm, uint64_t seed,
-                            const double* ics, const int32_t* ics_st, const void* w_in,
-                            const EnsPtrs& e, cudaStream_t st)
-{
-    return fp32 ? init_k<Sys, float>(k, sp, renorm, seed, ics, ics_st, w_in, e, st)
-                : init_k<Sys, double>(k, sp, renorm, seed, ics, ics_st, w_in, e, st);
 }
 
 cudaError_t launch_init(const SysPar& sp, int k, int vec_fp32, int renorm, uint64_t seed,
@@ -591,40 +483,37 @@ cudaError_t launch_init(const SysPar& sp, int k, int vec_fp32, int renorm, uint6
                         const EnsPtrs& e, cudaStream_t st)
 {
     if (e.n == 0) return cudaSuccess;
+    if (vec_fp32 && k > 0) return launch_init_f32(sp, k, seed, ics, ic_status, w_in, e, st);
     switch (sp.model) {
-    case CHS_HENON_HEILES:
-        return init_sys<SysHenonHeiles>(k, vec_fp32, sp, renorm, seed, ics, ic_status, w_in, e, st);
-    case CHS_HARMONIC:
-        return init_sys<SysHarmonic>(k, vec_fp32, sp, renorm, seed, ics, ic_status, w_in, e, st);
-    case CHS_INVERTED:
-        return init_sys<SysInverted>(k, vec_fp32, sp, renorm, seed, ics, ic_status, w_in, e, st);
-    case CHS_QUARTIC3:
-        return init_sys<SysQuartic3>(k, vec_fp32, sp, renorm, seed, ics, ic_status, w_in, e, st);
+    case CHS_HENON_HEILES: return init_k<SysHenonHeiles>(k, sp, renorm, seed, ics, ic_status, w_in, e, st);
+    case CHS_HARMONIC: return init_k<SysHarmonic>(k, sp, renorm, seed, ics, ic_status, w_in, e, st);
+    case CHS_INVERTED: return init_k<SysInverted>(k, sp, renorm, seed, ics, ic_status, w_in, e, st);
+    case CHS_QUARTIC3: return init_k<SysQuartic3>(k, sp, renorm, seed, ics, ic_status, w_in, e, st);
     }
     return cudaErrorInvalidValue;
 }
 
-template <class Sys, typename VT, bool LD>
+template <class Sys, bool LD>
 static cudaError_t integ_k(int k, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
                            cudaStream_t st)
 {
     const unsigned g = blocks_for(e.n, kSmallBlock);
     switch (k) {
-#define CHS_CASE(KV)                                                          \
-    case KV:                                                                  \
-        k_integrate<Sys, KV, LD, VT><<<g, kSmallBlock, 0, st>>>(a, sp, e); \
+#define CHS_CASE(KV)                                                      \
+    case KV:                                                              \
+        k_integrate<Sys, KV, LD><<<g, kSmallBlock, 0, st>>>(a, sp, e); \
         break;
         CHS_CASE(0) CHS_CASE(1) CHS_CASE(2) CHS_CASE(3) CHS_CASE(4)
 #undef CHS_CASE
     case 5:
         if constexpr (Sys::N >= 3) {
-            k_integrate<Sys, 5, LD, VT><<<g, kSmallBlock, 0, st>>>(a, sp, e);
+            k_integrate<Sys, 5, LD><<<g, kSmallBlock, 0, st>>>(a, sp, e);
             break;
         }
         return cudaErrorInvalidValue;
     case 6:
         if constexpr (Sys::N >= 3) {
-            k_integrate<Sys, 6, LD, VT><<<g, kSmallBlock, 0, st>>>(a, sp, e);
+            k_integrate<Sys, 6, LD><<<g, kSmallBlock, 0, st>>>(a, sp, e);
             break;
         }
         return cudaErrorInvalidValue;
@@ -635,40 +524,37 @@ static cudaError_t integ_k(int k, const StepArgs& a, const SysPar& sp, const Ens
 }
 
 template <class Sys>
-static cudaError_t integ_sys(int k, int fp32, bool ld, const StepArgs& a, const SysPar& sp,
-                             const EnsPtrs& e, cudaStream_t st)
+static cudaError_t integ_sys(int k, bool ld, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
+                             cudaStream_t st)
 {
-    if (fp32)
-        return ld ? integ_k<Sys, float, true>(k, a, sp, e, st)
-                  : integ_k<Sys, float, false>(k, a, sp, e, st);
-    return ld ? integ_k<Sys, double, true>(k, a, sp, e, st)
-              : integ_k<Sys, double, false>(k, a, sp, e, st);
+    return ld ? integ_k<Sys, true>(k, a, sp, e, st) : integ_k<Sys, false>(k, a, sp, e, st);
 }
 
 cudaError_t launch_integrate(const SysPar& sp, int k, int vec_fp32, bool ld, const StepArgs& a,
                              const EnsPtrs& e, cudaStream_t st)
 {
     if (e.n == 0 || a.n_steps == 0) return cudaSuccess;
+    if (vec_fp32 && k > 0) return launch_integrate_f32(sp, k, ld, a, e, st);
     switch (sp.model) {
-    case CHS_HENON_HEILES: return integ_sys<SysHenonHeiles>(k, vec_fp32, ld, a, sp, e, st);
-    case CHS_HARMONIC: return integ_sys<SysHarmonic>(k, vec_fp32, ld, a, sp, e, st);
-    case CHS_INVERTED: return integ_sys<SysInverted>(k, vec_fp32, ld, a, sp, e, st);
-    case CHS_QUARTIC3: return integ_sys<SysQuartic3>(k, vec_fp32, ld, a, sp, e, st);
+    case CHS_HENON_HEILES: return integ_sys<SysHenonHeiles>(k, ld, a, sp, e, st);
+    case CHS_HARMONIC: return integ_sys<SysHarmonic>(k, ld, a, sp, e, st);
+    case CHS_INVERTED: return integ_sys<SysInverted>(k, ld, a, sp, e, st);
+    case CHS_QUARTIC3: return integ_sys<SysQuartic3>(k, ld, a, sp, e, st);
     }
     return cudaErrorInvalidValue;
 }
 
-template <int D, typename VT>
+template <int D>
 static cudaError_t ind_k(int k, double thr, const EnsPtrs& e, double* sali, double* gali,
                          int8_t* label, cudaStream_t st)
 {
     const unsigned g = blocks_for(e.n, kSmallBlock);
-    const VT* w = static_cast<const VT*>(e.w);
+    const double* w = static_cast<const double*>(e.w);
     switch (k) {
-#define CHS_CASE(KV)                                                                          \
-    case KV:                                                                                  \
-        k_indicators<D, KV, VT><<<g, kSmallBlock, 0, st>>>(e.n, w, e.status, thr, sali, gali, \
-                                                           label);                            \
+#define CHS_CASE(KV)                                                                              \
+    case KV:                                                                                      \
+        k_indicators<D, KV, double><<<g, kSmallBlock, 0, st>>>(e.n, w, e.status, thr, sali, gali, \
+                                                               label);                            \
         break;
         CHS_CASE(1) CHS_CASE(2) CHS_CASE(3) CHS_CASE(4) CHS_CASE(5) CHS_CASE(6)
 #undef CHS_CASE
@@ -683,13 +569,10 @@ cudaError_t launch_indicators(const SysPar& sp, int k, int vec_fp32, double sali
                               cudaStream_t st)
 {
     if (e.n == 0) return cudaSuccess;
+    if (vec_fp32 && k > 0) return launch_indicators_f32(sp, k, sali_threshold, e, sali, gali, label, st);
     const int D = 2 * sp.n_dof;
-    if (D == 4)
-        return vec_fp32 ? ind_k<4, float>(k, sali_threshold, e, sali, gali, label, st)
-                        : ind_k<4, double>(k, sali_threshold, e, sali, gali, label, st);
-    if (D == 6)
-        return vec_fp32 ? ind_k<6, float>(k, sali_threshold, e, sali, gali, label, st)
-                        : ind_k<6, double>(k, sali_threshold, e, sali, gali, label, st);
+    if (D == 4) return ind_k<4>(k, sali_threshold, e, sali, gali, label, st);
+    if (D == 6) return ind_k<6>(k, sali_threshold, e, sali, gali, label, st);
     return cudaErrorInvalidValue;
 }
 

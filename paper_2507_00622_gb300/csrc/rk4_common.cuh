@@ -1,0 +1,132 @@
+// rk4_common.cuh -- pieces of the classic RK4 step shared by the one-orbit-per-
+// thread kernels: the orbit's four stages (with the LD quadrature and the stage
+// Hessians recorded) and the exact one-step propagator of the variational
+// equations.
+#pragma once
+
+#include "chs_internal.cuh"
+#include "fastmath.cuh"
+#include "systems.cuh"
+
+namespace chs {
+
+// LD integrand sum_i |f_i|^p (p = 1/2: Newton-refined square roots).
+template <int D>
+__device__ __forceinline__ double ld_integrand(const double* f, int ld_sqrt, double p)
+{
+    double acc = 0.0;
+    if (ld_sqrt) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc += sqrt_nr(fabs(f[i]));
+    } else {
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc += pow(fabs(f[i]), p);
+    }
+    return acc;
+}
+
+// One classic RK4 step of the orbit x and its LD accumulator L,
+//   k1 = f(x), k2 = f(x + h/2 k1), k3 = f(x + h/2 k2), k4 = f(x + h k3),
+//   x <- x + h/6 (k1 + 2 k2 + 2 k3 + k4),
+// recording Hess V at the four stage states in H[s] (packed upper triangle).
+template <class Sys, bool LD>
+__device__ __forceinline__ void rk4_state_capture(double* x, double& L, const double h,
+                                                  const int ld_sqrt, const double ld_p,
+                                                  const SysPar& sp, double (*H)[Sys::NH])
+{
+    constexpr int D = 2 * Sys::N;
+    const double hh = 0.5 * h, h6 = h / 6.0;
+    double ax[D], xs[D], f[D];
+    double aL = 0.0;
+    Sys::eval(x, f, H[0], sp);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        ax[c] = f[c];
+        xs[c] = fma(hh, f[c], x[c]);
+    }
+    if (LD) aL = ld_integrand<D>(f, ld_sqrt, ld_p);
+#pragma unroll
+    for (int s = 1; s < 3; ++s) {
+        const double cs = (s == 1) ? hh : h;
+        Sys::eval(xs, f, H[s], sp);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            ax[c] = fma(2.0, f[c], ax[c]);
+            xs[c] = fma(cs, f[c], x[c]);
+        }
+        if (LD) aL = fma(2.0, ld_integrand<D>(f, ld_sqrt, ld_p), aL);
+    }
+    Sys::eval(xs, f, H[3], sp);
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = fma(h6, ax[c] + f[c], x[c]);
+    if (LD) L = fma(h6, aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
+}
+
+// Exact one-step propagator of RK4 on the linear variational equation
+// w' = J_s w, J_s = [[0, I], [-H_s, 0]] (H_s = Hess V at stage s):
+//   Phi = I + h/6 (J1 + 2J2 + 2J3 + J4) + h^2/6 (J2J1 + J3J2 + J4J3)
+//           + h^3/12 (J3J2J1 + J4J3J2) + h^4/24 J4J3J2J1
+//       = [[A, B], [C, D]] with
+//   A = I - h^2/6 (H1+H2+H3) + h^4/24 H3H1,   B = h I - h^3/12 (H2+H3),
+//   C = -h/6 (H1+2H2+2H3+H4) + h^3/12 (H3H1 + H4H2),
+//   D = I - h^2/6 (H2+H3+H4) + h^4/24 H4H2.
+// Applying Phi equals RK4 on the joint system in exact arithmetic.
+template <int N, typename T>
+struct PhiBlocks {
+    T A[N][N], B[N][N], C[N][N], D[N][N];
+};
+
+template <int N, int NH, typename T>
+__device__ __forceinline__ void phi_build(const T (*Hs)[NH], const double h, PhiBlocks<N, T>& P)
+{
+    const T hv = (T)h, c1 = (T)(h / 6.0), c2 = (T)(h * h / 6.0), c3 = (T)(h * h * h / 12.0),
+            c4 = (T)(h * h * h * h / 24.0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const T s1 = Hs[0][hidx<N>(i, j)], s2 = Hs[1][hidx<N>(i, j)];
+            const T s3 = Hs[2][hidx<N>(i, j)], s4 = Hs[3][hidx<N>(i, j)];
+            T p31 = Hs[2][hidx<N>(i, 0)] * Hs[0][hidx<N>(0, j)];
+            T p42 = Hs[3][hidx<N>(i, 0)] * Hs[1][hidx<N>(0, j)];
+#pragma unroll
+            for (int m = 1; m < N; ++m) {
+                p31 = fma(Hs[2][hidx<N>(i, m)], Hs[0][hidx<N>(m, j)], p31);
+                p42 = fma(Hs[3][hidx<N>(i, m)], Hs[1][hidx<N>(m, j)], p42);
+            }
+            const T s23 = s2 + s3;
+            const T id = (i == j) ? (T)1 : (T)0;
+            P.A[i][j] = fma(c4, p31, fma(-c2, s1 + s23, id));
+            P.B[i][j] = (i == j) ? fma(-c3, s23, hv) : -c3 * s23;
+            P.C[i][j] = fma(c3, p31 + p42, -c1 * (fma((T)2, s23, s1) + s4));
+            P.D[i][j] = fma(c4, p42, fma(-c2, s23 + s4, id));
+        }
+    }
+}
+
+// w <- Phi w for one vector w = (u, v).
+template <int N, typename T>
+__device__ __forceinline__ void phi_apply(const PhiBlocks<N, T>& P, T* w)
+{
+    T nw[2 * N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T u = P.A[i][0] * w[0], v = P.C[i][0] * w[0];
+#pragma unroll
+        for (int m = 1; m < N; ++m) {
+            u = fma(P.A[i][m], w[m], u);
+            v = fma(P.C[i][m], w[m], v);
+        }
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            u = fma(P.B[i][m], w[N + m], u);
+            v = fma(P.D[i][m], w[N + m], v);
+        }
+        nw[i] = u;
+        nw[N + i] = v;
+    }
+#pragma unroll
+    for (int c = 0; c < 2 * N; ++c) w[c] = nw[c];
+}
+
+}  // namespace chs

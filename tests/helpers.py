@@ -95,7 +95,11 @@ def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=Tr
         if ldi is not None:
             out.update(dl=ldi[0].cpu().numpy(), sl=ldi[1].cpu().numpy())
     torch.cuda.synchronize()
-    out.update(x=ens.x.cpu().numpy(), w=ens.w[: k * S.d].double().cpu().numpy(),
+    if vec_fp32 and k > 0:
+        w_out = chs.frame_to_vectors(ens.w.double().cpu().numpy(), k, S.d)
+    else:
+        w_out = ens.w[: k * S.d].double().cpu().numpy()
+    out.update(x=ens.x.cpu().numpy(), w=w_out,
                ld=ens.ld.cpu().numpy(), dh_max=ens.dh_max.cpu().numpy(),
                n_exec=ens.n_exec.cpu().numpy(), status=ens.status.cpu().numpy(),
                h0=ens.h0.cpu().numpy())

@@ -245,27 +245,34 @@ def test_invalid_arguments_are_rejected():
 # --------------------------------------------------------------------------
 
 def test_fp32_vectors_error_against_fp64_oracle():
+    """FP32 deviation vectors held as an orthonormal frame plus a unit-column
+    triangle (FP64 orbit and LD): indicator errors against the FP64 oracle."""
     g0 = _grid(1 / 8, 32, 32)
     ics, st = O.grid_ics(*g0)
     v = st == 0
-    kw = dict(dt=0.01, n_steps=20000, k=2, ld_p=0.5, escape_r2=4.0, sali_threshold=1e-6)
+    kw = dict(dt=0.01, n_steps=20000, k=3, ld_p=0.5, escape_r2=4.0)
     g = gpu_run(HH, 2, ics, st, vec_fp32=True, **kw)
     r = oracle_run(HH, 2, ics, st, **kw)
-    # the state and LD do not depend on the vectors: FP64 parity holds for them
+    # the orbit and LD do not depend on the vectors: FP64 parity holds for them
     lam, _ = O.lyapunov(O.henon_heiles(), O.params(0.01, 20000, qr_every=10), np.nan_to_num(ics), st)
     reg = v & (lam[0] < 0.02)
     assert state_rel_err(g["x"][:, reg], r["x"][:, reg]).max() < STATE_RTOL
     assert ind_err(g["ld"][reg], r["ld"][reg]).max() < IND_TOL
-    # SALI of regular orbits carries the FP32 rounding of the vectors, grown
-    # linearly along the torus over 20000 steps
-    err = np.abs(g["sali"][reg] - r["sali"][reg])
-    assert np.median(err) < 1e-4 and err.max() < 5e-3
-    # labels (threshold 1e-6 on both sides, FP32 SALI saturates near 1e-7) once the
-    # SALI distribution has separated, at t = 2000
+    # regular orbits: the FP32 rounding of the frame, grown along the torus
+    rel = np.abs(g["sali"][reg] - r["sali"][reg]) / r["sali"][reg]
+    assert np.median(rel) < 1e-3 and rel.max() < 5e-2
+    relg = np.abs(g["gali"][:, reg] - r["gali"][:, reg]) / r["gali"][:, reg]
+    assert np.median(relg) < 1e-3
+    assert np.abs(g["w"][:, reg] - r["w"][:, reg]).max() < 5e-2
+    assert (g["label"][v] == r["label"][v]).mean() >= LABEL_AGREE
+    # at t = 2000 the SALI distribution has separated; the frame keeps resolving
+    # SALI far below the FP32 rounding level, so the FP64 threshold 1e-8 applies
     kw["n_steps"] = 200000
     g = gpu_run(HH, 2, ics, st, vec_fp32=True, **kw)
     r = oracle_run(HH, 2, ics, st, **kw)
-    assert (g["label"][v] == r["label"][v]).mean() >= 0.99
+    assert (g["label"][v] == r["label"][v]).mean() >= LABEL_AGREE
+    chaotic = v & (r["sali"] < 1e-12)
+    assert chaotic.sum() > 100 and np.all(g["sali"][chaotic] < 1e-8)
 
 
 def test_ld_newton_sqrt_precision():
