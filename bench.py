@@ -78,6 +78,13 @@ def shard_rows(ny: int, rank: int, world: int) -> tuple[int, int, int, int]:
     return lo - halo_lo, ny + halo_lo + halo_hi, halo_lo, halo_hi
 
 
+def slab_bounds(y0: float, y1: float, ny: int, rank: int, world: int):
+    """y-range, row count and owned-row slice of rank's slab of the (world*ny)-row grid."""
+    dyg = (y1 - y0) / (ny * world)
+    first, rows, hlo, hhi = shard_rows(ny, rank, world)
+    return y0 + first * dyg, y0 + (first + rows) * dyg, rows, hlo
+
+
 class ClockSampler:
     """nvidia-smi clock and throttle-reason samples during the timed region."""
 
@@ -213,9 +220,7 @@ def run_gpu(args):
 
     ny = npy = args.n_side
     y0, y1, p0, p1 = grid_box(E_GRID)
-    dyg = (y1 - y0) / (ny * world)
-    first, rows, hlo, hhi = shard_rows(ny, rank, world)
-    sy0, sy1 = y0 + first * dyg, y0 + (first + rows) * dyg
+    sy0, sy1, rows, hlo = slab_bounds(y0, y1, ny, rank, world)
     n = rows * npy
     own = slice(hlo * npy, (hlo + ny) * npy)
     vec_fp32 = args.vec == "fp32"
