@@ -29,6 +29,7 @@
 #ifndef CHS_H
 #define CHS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -68,7 +69,9 @@ enum {
     CHS_ORBIT_FORBIDDEN = 1,    /* no initial condition exists in this cell */
     CHS_ORBIT_ESCAPED = 2,      /* sum_i q_i^2 exceeded escape_r2; frozen */
     CHS_ORBIT_NONFINITE = 3,    /* a non-finite value at a health check; frozen */
-    CHS_ORBIT_ENERGY_DRIFT = 4  /* |H - H0| exceeded dh_limit at a health check; frozen */
+    CHS_ORBIT_ENERGY_DRIFT = 4, /* |H - H0| exceeded dh_limit at a health check; frozen */
+    CHS_ORBIT_EARLY_CHAOTIC = 5 /* SALI fell below sali_threshold at a health check with
+                                   early_exit set; frozen, labelled chaotic */
 };
 
 /* Deviation-vector storage precision. */
@@ -84,7 +87,8 @@ typedef struct {
     int32_t sample_every;    /* health checks at absolute steps divisible by this (0 = never) */
     int32_t qr_every;        /* Lyapunov: QR of the vectors every qr_every steps and at the end */
     int32_t vec_precision;   /* CHS_VEC_FP64 or CHS_VEC_FP32 (FP32 requires renorm = 1) */
-    int32_t reserved;        /* must be 0 */
+    int32_t early_exit;      /* 1: freeze as EARLY_CHAOTIC once SALI < sali_threshold at a
+                                health check (needs n_dev >= 2); 0: integrate to the end */
     double ld_p;             /* LD exponent p (LD integrand sum_i |dx_i/dt|^p); 0 = no LD */
     double escape_r2;        /* ESCAPED when sum_i q_i^2 > escape_r2; 0 = off */
     double dh_limit;         /* ENERGY_DRIFT when |H - H0| > dh_limit; 0 = off */
@@ -107,7 +111,9 @@ typedef struct {
  *   h0      [n]       energy at t = 0
  *   dh_max  [n]       largest |H - H0| seen at health checks
  *   n_exec  [n]       integration steps executed so far (frozen orbits stop counting)
- *   status  [n]       CHS_ORBIT_* */
+ *   status  [n]       CHS_ORBIT_*
+ *   t_end   [n]       optional (NULL = none): orbit o stops once n_exec reaches
+ *                     t_end[o] steps (uneven integration lengths); read only */
 typedef struct {
     int64_t n_orbits;
     double* x;
@@ -117,6 +123,7 @@ typedef struct {
     double* dh_max;
     int64_t* n_exec;
     int32_t* status;
+    const int64_t* t_end;
 } chs_ensemble;
 
 typedef struct chs_system_s* chs_system;
@@ -154,6 +161,14 @@ chs_status chs_section_grid_ics(chs_system s, double E, double y0, double y1, in
 chs_status chs_fput_mode_ics(chs_system s, int64_t n, const double* Qm, const double* Pm,
                              const double* E, double* ics_out, void* stream);
 
+/* Quartic-3 initial conditions on energy shells (a0 for the coupled quartic
+ * oscillator): the direction u = dir / |dir| of each 6-component draw is scaled
+ * by s > 0 so that H(s u) = E_o; with H2 = |u|^2/2 and H4 = eps (u1^2 u2^2 +
+ * u2^2 u3^2 + u1^2 u3^2), s^2 = 2E / (H2 + sqrt(H2^2 + 4 H4 E)).
+ * dirs [6][n], E [n], ics_out [6][n].  CHS_E_UNSUPPORTED for other models. */
+chs_status chs_shell_ics(chs_system s, int64_t n, const double* dirs, const double* E,
+                         double* ics_out, void* stream);
+
 /* Initialises an ensemble from initial conditions `ics` [d][n]:
  * x <- ics; status <- ic_status (or OK when NULL), NONFINITE for a non-finite
  * OK state; h0 <- H(x); dh_max, n_exec, ld <- 0; the k = p->n_dev deviation
@@ -181,11 +196,29 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
  * (Phi Q = Q' S, R <- S R with unit columns), the orbit and LD staying FP64; an orbit with sum_i q_i^2 > escape_r2 freezes as
  * ESCAPED.  At absolute steps divisible by sample_every: non-finite -> frozen
  * NONFINITE; dh_max <- max(dh_max, |H - h0|); |H - h0| > dh_limit -> frozen
- * ENERGY_DRIFT.  Splitting a run into calls with consecutive step0 gives
- * bit-identical results.  Supported: HENON_HEILES, HARMONIC, INVERTED
+ * ENERGY_DRIFT; with early_exit, SALI < sali_threshold -> frozen EARLY_CHAOTIC.
+ * An orbit with t_end stops after t_end[o] total steps.  Splitting a run into
+ * calls with consecutive step0 gives bit-identical results.  Supported: HENON_HEILES, HARMONIC, INVERTED
  * (k <= 4) and QUARTIC3 (k <= 6). */
 chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ensemble* e,
                                void* stream);
+
+/* Bytes of device scratch that chs_integrate_compacted needs for n orbits. */
+size_t chs_compact_work_size(int64_t n_orbits);
+
+/* The same integration as chs_integrate_batch (p->n_steps steps from step
+ * p->step0, identical results bit for bit), run in chunks of chunk_steps steps
+ * over a list of the orbits still running: after every chunk the orbits that
+ * froze (early exit, escape, ...) or reached their t_end are dropped from the
+ * list, so later chunks launch only over live orbits.  The chunk sequence is
+ * recorded once as a CUDA graph and replayed; the recorded graph is cached in
+ * the handle and reused while the ensemble pointers, sizes and parameters are
+ * unchanged.  `work` is caller-owned device scratch of at least
+ * chs_compact_work_size(n) bytes, 256-byte aligned; its contents are
+ * overwritten.  Calls that share a work buffer and overlap on the GPU race. */
+chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_ensemble* e,
+                                   int32_t chunk_steps, void* work, size_t work_bytes,
+                                   void* stream);
 
 /* Indicators of the current ensemble state (Sec. Functionalities):
  *   sali_out [n]        SALI = min(|w1 + w2|, |w1 - w2|) of the first two unit
@@ -195,8 +228,8 @@ chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ense
  *                       Skokos2008), computed as prod |R_ii| of its QR (FP32
  *                       mode: of the stored triangle R, and SALI as
  *                       R_11 sqrt(2 / (1 + |R_01|))).
- *   label_out [n]       1 chaotic (SALI < sali_threshold), 0 regular,
- *                       2 ESCAPED, -1 any other non-OK status.
+ *   label_out [n]       1 chaotic (SALI < sali_threshold, or EARLY_CHAOTIC),
+ *                       0 regular, 2 ESCAPED, -1 any other non-OK status.
  *   ld_ind_out [2][n]   when grid_ny * grid_npy == n and the ensemble has an
  *                       LD: D_L and S_L from the four grid neighbours (LD-based
  *                       indicators and neighbouring trajectories):

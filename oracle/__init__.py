@@ -37,7 +37,7 @@ _lock = threading.Lock()
 _lib = None
 
 HENON_HEILES, FPUT, QUARTIC3, HARMONIC, INVERTED = 1, 2, 3, 100, 101
-OK, FORBIDDEN, ESCAPED, NONFINITE, ENERGY_DRIFT = 0, 1, 2, 3, 4
+OK, FORBIDDEN, ESCAPED, NONFINITE, ENERGY_DRIFT, EARLY_CHAOTIC = 0, 1, 2, 3, 4, 5
 RK4, YOSHIDA4 = 0, 1
 
 
@@ -50,7 +50,8 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_steps", C.c_int64), ("step0", C.c_int64),
                 ("n_dev", C.c_int), ("renorm", C.c_int), ("sample_every", C.c_int),
                 ("qr_every", C.c_int), ("integrator", C.c_int), ("ld_p", C.c_double),
-                ("escape_r2", C.c_double), ("dh_limit", C.c_double)]
+                ("escape_r2", C.c_double), ("dh_limit", C.c_double), ("early_exit", C.c_int),
+                ("sali_threshold", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -88,7 +89,9 @@ def lib():
         L.o_ensemble_init.argtypes = [C.POINTER(System), C.POINTER(Params), C.c_int64, P, P, P,
                                       C.c_uint64, P, P, P, P, P, P, P]
         L.o_integrate.argtypes = [C.POINTER(System), C.POINTER(Params), C.c_int64, P, P, P, P,
-                                  P, P, P, C.c_int]
+                                  P, P, P, P, C.c_int]
+        L.o_shell_ics.restype = C.c_int
+        L.o_shell_ics.argtypes = [C.POINTER(System), C.c_int64, P, P, P]
         L.o_jacobi_sv.argtypes = [C.c_int, C.c_int, P, P]
         L.o_indicators.argtypes = [C.POINTER(System), C.c_int64, C.c_int, P, P, C.c_double, P,
                                    P, P]
@@ -123,9 +126,10 @@ def fput(N: int, beta: float = 1.0, alpha: float = 0.0, kk: float = 1.0) -> Syst
 
 def params(dt: float, n_steps: int, *, step0: int = 0, n_dev: int = 0, renorm: bool = True,
            sample_every: int = 100, qr_every: int = 10, integrator: int = RK4,
-           ld_p: float = 0.0, escape_r2: float = 0.0, dh_limit: float = 0.0) -> Params:
+           ld_p: float = 0.0, escape_r2: float = 0.0, dh_limit: float = 0.0,
+           early_exit: bool = False, sali_threshold: float = 1e-8) -> Params:
     return Params(dt, n_steps, step0, n_dev, int(renorm), sample_every, qr_every, integrator,
-                  ld_p, escape_r2, dh_limit)
+                  ld_p, escape_r2, dh_limit, int(early_exit), sali_threshold)
 
 
 def max_threads() -> int:
@@ -203,10 +207,12 @@ class Ensemble:
                               seed, _p(self.x), _p(self.w), _p(self.ld), _p(self.h0),
                               _p(self.dh_max), _p(self.n_exec), _p(self.status))
 
-    def integrate(self, prm: Params, nthreads: int = 0) -> "Ensemble":
+    def integrate(self, prm: Params, nthreads: int = 0, t_end=None) -> "Ensemble":
+        """Advance by prm.n_steps steps (each orbit at most up to its own t_end[o])."""
+        te = None if t_end is None else np.ascontiguousarray(t_end, dtype=np.int64)
         lib().o_integrate(C.byref(self.sysd), C.byref(prm), self.n, _p(self.x), _p(self.w),
                           _p(self.ld), _p(self.h0), _p(self.dh_max), _p(self.n_exec),
-                          _p(self.status), nthreads)
+                          _p(self.status), _p(te), nthreads)
         return self
 
     def indicators(self, sali_threshold: float = 1e-8):
@@ -217,6 +223,16 @@ class Ensemble:
         lib().o_indicators(C.byref(self.sysd), n, k, _p(self.w), _p(self.status), sali_threshold,
                            _p(sali), _p(gali), _p(label))
         return sali, gali[: max(k - 1, 0)], label
+
+
+def shell_ics(sysd: System, dirs, E):
+    """Quartic-3 states on the energy shells E[o] along the directions dirs [6, n]."""
+    dirs, E = _f64(dirs), _f64(E)
+    n = E.shape[0]
+    ics = np.empty((6, n))
+    if lib().o_shell_ics(C.byref(sysd), n, _p(dirs), _p(E), _p(ics)) != 0:
+        raise ValueError("shell initial conditions are defined for QUARTIC3")
+    return ics
 
 
 def jacobi_sv(A) -> np.ndarray:

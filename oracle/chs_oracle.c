@@ -63,7 +63,8 @@
 #endif
 
 enum { O_HENON_HEILES = 1, O_FPUT = 2, O_QUARTIC3 = 3, O_HARMONIC = 100, O_INVERTED = 101 };
-enum { OS_OK = 0, OS_FORBIDDEN = 1, OS_ESCAPED = 2, OS_NONFINITE = 3, OS_ENERGY_DRIFT = 4 };
+enum { OS_OK = 0, OS_FORBIDDEN = 1, OS_ESCAPED = 2, OS_NONFINITE = 3, OS_ENERGY_DRIFT = 4,
+       OS_EARLY_CHAOTIC = 5 };
 enum { OI_RK4 = 0, OI_YOSHIDA4 = 1 };
 
 typedef struct {
@@ -87,6 +88,8 @@ typedef struct {
     double ld_p;          /* exponent p of the LD; 0 switches the LD off */
     double escape_r2;     /* escape when sum_i q_i^2 exceeds this; 0 = off */
     double dh_limit;      /* ENERGY_DRIFT when |H - H0| exceeds this; 0 = off */
+    int early_exit;       /* 1: stop as EARLY_CHAOTIC once SALI < sali_threshold at a health check */
+    double sali_threshold;
 } o_params;
 
 /* ------------------------------------------------------------------------ */
@@ -447,6 +450,31 @@ int o_fput_mode_ics(const o_system* s, int64_t n, const double* Qm, const double
     return 0;
 }
 
+/* Quartic-3 initial conditions on an energy shell: the direction u = dir/|dir|
+ * of a 6-component draw is scaled by s > 0 with H(s u) = E_o.  H(s u) =
+ * s^2 H2 + s^4 H4 with H2 = |u|^2 / 2 = 1/2 and H4 = eps (u1^2 u2^2 + u2^2 u3^2 +
+ * u1^2 u3^2) over the coordinate part, so s^2 = 2E / (H2 + sqrt(H2^2 + 4 H4 E)). */
+int o_shell_ics(const o_system* s, int64_t n, const double* dirs, const double* E, double* ics)
+{
+    if (s->model != O_QUARTIC3) return -1;
+    for (int64_t o = 0; o < n; ++o) {
+        double u[6], nr = 0.0;
+        for (int c = 0; c < 6; ++c) {
+            u[c] = dirs[(int64_t)c * n + o];
+            nr += u[c] * u[c];
+        }
+        nr = sqrt(nr);
+        for (int c = 0; c < 6; ++c) u[c] = u[c] / nr;
+        double H2 = 0.0;
+        for (int c = 0; c < 6; ++c) H2 += u[c] * u[c] / 2.0;
+        double H4 = s->eps * (u[0] * u[0] * u[1] * u[1] + u[1] * u[1] * u[2] * u[2] + u[0] * u[0] * u[2] * u[2]);
+        double s2 = 2.0 * E[o] / (H2 + sqrt(H2 * H2 + 4.0 * H4 * E[o]));
+        double sc = sqrt(s2);
+        for (int c = 0; c < 6; ++c) ics[(int64_t)c * n + o] = sc * u[c];
+    }
+    return 0;
+}
+
 /* Initial ensemble: x <- ics, w <- w_in (or seeded), normalised when renorm
  * is set, L <- 0, H0 <- H(x), dH_max <- 0, n_exec <- 0.  A cell whose
  * ic_status is not OK keeps that status; a non-finite state becomes NONFINITE. */
@@ -490,15 +518,32 @@ void o_ensemble_init(const o_system* s, const o_params* prm, int64_t n, const do
 /* Integration                                                               */
 /* ------------------------------------------------------------------------ */
 
-/* Advance every orbit by prm->n_steps steps.  After each step: renormalise
- * the vectors (if prm->renorm), then freeze the orbit as ESCAPED if
+/* Advance every orbit by prm->n_steps steps, or fewer when its own end step
+ * t_end[o] (total steps, when t_end is given) comes first.  After each step:
+ * renormalise the vectors (if prm->renorm), then freeze the orbit as ESCAPED if
  * sum_i q_i^2 > escape_r2.  At absolute steps divisible by sample_every:
  * freeze as NONFINITE on any non-finite value, update dH_max = max |H - H0|,
- * and freeze as ENERGY_DRIFT when it exceeds dh_limit.  A frozen orbit keeps
- * the state of the step at which it froze; n_exec counts executed steps. */
+ * freeze as ENERGY_DRIFT when it exceeds dh_limit, and (early_exit, k >= 2)
+ * freeze as EARLY_CHAOTIC once SALI < sali_threshold.  A frozen orbit keeps the
+ * state of the step at which it froze; n_exec counts executed steps. */
+/* SALI of the first two vectors of the joint state z (each normalised first). */
+static double o_sali_of(const double* a, const double* b, int d)
+{
+    double na = o_norm(a, d), nb = o_norm(b, d);
+    double sp = 0.0, sm = 0.0;
+    for (int c = 0; c < d; ++c) {
+        double u = a[c] / na, v = b[c] / nb;
+        sp += (u + v) * (u + v);
+        sm += (u - v) * (u - v);
+    }
+    sp = sqrt(sp);
+    sm = sqrt(sm);
+    return sp < sm ? sp : sm;
+}
+
 void o_integrate(const o_system* s, const o_params* prm, int64_t n, double* x, double* w,
                  double* ld, const double* h0, double* dh_max, int64_t* n_exec, int32_t* status,
-                 int nthreads)
+                 const int64_t* t_end, int nthreads)
 {
     int d = 2 * s->n_dof, k = prm->n_dev, N = s->n_dof;
     int use_ld = (prm->ld_p != 0.0) && ld != NULL;
@@ -519,7 +564,9 @@ void o_integrate(const o_system* s, const o_params* prm, int64_t n, double* x, d
         double dhm = dh_max[o];
         int32_t st = OS_OK;
         int64_t done = 0;
-        for (int64_t sidx = 1; sidx <= prm->n_steps; ++sidx) {
+        int64_t todo = prm->n_steps;
+        if (t_end && t_end[o] - n_exec[o] < todo) todo = t_end[o] - n_exec[o] > 0 ? t_end[o] - n_exec[o] : 0;
+        for (int64_t sidx = 1; sidx <= todo; ++sidx) {
             if (prm->integrator == OI_YOSHIDA4)
                 o_yoshida_step(&J, z, prm->dt);
             else
@@ -550,6 +597,10 @@ void o_integrate(const o_system* s, const o_params* prm, int64_t n, double* x, d
                 if (dH > dhm) dhm = dH;
                 if (prm->dh_limit > 0.0 && dH > prm->dh_limit) {
                     st = OS_ENERGY_DRIFT;
+                    break;
+                }
+                if (prm->early_exit && k >= 2 && o_sali_of(z + d, z + 2 * d, d) < prm->sali_threshold) {
+                    st = OS_EARLY_CHAOTIC;
                     break;
                 }
             }
@@ -615,7 +666,7 @@ void o_jacobi_sv(int d, int k, const double* A, double* sv)
  *   SALI = min(|w1 + w2|, |w1 - w2|)                      (needs k >= 2)
  *   GALI_m = product of the singular values of [w1..wm]   for m = 2..k
  *   label: status OK -> 1 (chaotic) if SALI < sali_threshold else 0 (regular);
- *          ESCAPED -> 2; any other status -> -1.
+ *          EARLY_CHAOTIC -> 1; ESCAPED -> 2; any other status -> -1.
  * FORBIDDEN orbits get NaN indicators. */
 void o_indicators(const o_system* s, int64_t n, int k, const double* w, const int32_t* status,
                   double sali_threshold, double* sali, double* gali, int8_t* label)
@@ -656,6 +707,8 @@ void o_indicators(const o_system* s, int64_t n, int k, const double* w, const in
             int8_t lb;
             if (status[o] == OS_OK)
                 lb = (sv < sali_threshold) ? 1 : 0;
+            else if (status[o] == OS_EARLY_CHAOTIC)
+                lb = 1;
             else if (status[o] == OS_ESCAPED)
                 lb = 2;
             else

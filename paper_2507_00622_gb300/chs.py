@@ -19,11 +19,13 @@ LIB_PATH = os.path.join(_HERE, "libchs.so")
 
 CHS_OK, CHS_E_INVALID, CHS_E_UNSUPPORTED, CHS_E_CUDA, CHS_E_NOMEM, CHS_E_SIZE = range(6)
 HENON_HEILES, FPUT, QUARTIC3, HARMONIC, INVERTED = 1, 2, 3, 100, 101
-ORBIT_OK, ORBIT_FORBIDDEN, ORBIT_ESCAPED, ORBIT_NONFINITE, ORBIT_ENERGY_DRIFT = range(5)
+(ORBIT_OK, ORBIT_FORBIDDEN, ORBIT_ESCAPED, ORBIT_NONFINITE, ORBIT_ENERGY_DRIFT,
+ ORBIT_EARLY_CHAOTIC) = range(6)
 VEC_FP64, VEC_FP32 = 0, 1
 
 EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_section_grid_ics",
-           "chs_fput_mode_ics", "chs_ensemble_init", "chs_integrate_batch", "chs_indicators",
+           "chs_fput_mode_ics", "chs_shell_ics", "chs_ensemble_init", "chs_integrate_batch",
+           "chs_compact_work_size", "chs_integrate_compacted", "chs_indicators",
            "chs_lyapunov_spectrum", "chs_last_error", "chs_version")
 
 
@@ -36,7 +38,7 @@ class ChsError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("n_steps", C.c_int64), ("step0", C.c_int64),
                 ("n_dev", C.c_int32), ("renorm", C.c_int32), ("sample_every", C.c_int32),
-                ("qr_every", C.c_int32), ("vec_precision", C.c_int32), ("reserved", C.c_int32),
+                ("qr_every", C.c_int32), ("vec_precision", C.c_int32), ("early_exit", C.c_int32),
                 ("ld_p", C.c_double), ("escape_r2", C.c_double), ("dh_limit", C.c_double),
                 ("sali_threshold", C.c_double), ("seed", C.c_uint64)]
 
@@ -44,7 +46,7 @@ class Params(C.Structure):
 class Ensemble(C.Structure):
     _fields_ = [("n_orbits", C.c_int64), ("x", C.c_void_p), ("w", C.c_void_p), ("ld", C.c_void_p),
                 ("h0", C.c_void_p), ("dh_max", C.c_void_p), ("n_exec", C.c_void_p),
-                ("status", C.c_void_p)]
+                ("status", C.c_void_p), ("t_end", C.c_void_p)]
 
 
 _lib = None
@@ -66,6 +68,10 @@ def load(path: str | None = None):
         "chs_system_dim": (I32, [P]),
         "chs_section_grid_ics": (C.c_int, [P, D, D, D, I32, D, D, I32, P, P, P]),
         "chs_fput_mode_ics": (C.c_int, [P, I64, P, P, P, P, P]),
+        "chs_shell_ics": (C.c_int, [P, I64, P, P, P, P]),
+        "chs_compact_work_size": (C.c_size_t, [I64]),
+        "chs_integrate_compacted": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), I32, P,
+                                              C.c_size_t, P]),
         "chs_ensemble_init": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), P, P, P, P]),
         "chs_integrate_batch": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), P]),
         "chs_indicators": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), I32, I32, P, P,
@@ -107,9 +113,9 @@ def _stream(stream):
 def params(dt: float, n_steps: int, *, step0: int = 0, n_dev: int = 0, renorm: bool = True,
            sample_every: int = 100, qr_every: int = 10, vec_precision: int = VEC_FP64,
            ld_p: float = 0.0, escape_r2: float = 0.0, dh_limit: float = 0.0,
-           sali_threshold: float = 1e-8, seed: int = 1) -> Params:
-    return Params(dt, n_steps, step0, n_dev, int(renorm), sample_every, qr_every, vec_precision, 0,
-                  ld_p, escape_r2, dh_limit, sali_threshold, seed)
+           sali_threshold: float = 1e-8, seed: int = 1, early_exit: bool = False) -> Params:
+    return Params(dt, n_steps, step0, n_dev, int(renorm), sample_every, qr_every, vec_precision,
+                  int(early_exit), ld_p, escape_r2, dh_limit, sali_threshold, seed)
 
 
 # ----------------------------------------------------------------------------
@@ -139,6 +145,19 @@ def chs_section_grid_ics(h, E, y0, y1, ny, py0, py1, npy, ics, status, stream=No
 
 def chs_fput_mode_ics(h, n, Qm, Pm, E, ics, stream=None):
     _check(load().chs_fput_mode_ics(h, n, _ptr(Qm), _ptr(Pm), _ptr(E), _ptr(ics), _stream(stream)))
+
+
+def chs_shell_ics(h, n, dirs, E, ics, stream=None):
+    _check(load().chs_shell_ics(h, n, _ptr(dirs), _ptr(E), _ptr(ics), _stream(stream)))
+
+
+def chs_compact_work_size(n: int) -> int:
+    return int(load().chs_compact_work_size(n))
+
+
+def chs_integrate_compacted(h, prm: Params, ens: Ensemble, chunk_steps: int, work, stream=None):
+    _check(load().chs_integrate_compacted(h, C.byref(prm), C.byref(ens), chunk_steps, _ptr(work),
+                                          work.numel() * work.element_size(), _stream(stream)))
 
 
 def chs_ensemble_init(h, prm: Params, ens: Ensemble, ics, ic_status=None, w_in=None, stream=None):
@@ -239,7 +258,13 @@ class DeviceEnsemble:
     def n(self) -> int:
         return self.x.shape[1]
 
-    def abi(self, with_ld: bool = True) -> Ensemble:
+    def abi(self, with_ld: bool = True, t_end=None) -> Ensemble:
         p = lambda t: t.data_ptr()  # noqa: E731
         return Ensemble(self.n, p(self.x), p(self.w), p(self.ld) if with_ld else None, p(self.h0),
-                        p(self.dh_max), p(self.n_exec), p(self.status))
+                        p(self.dh_max), p(self.n_exec), p(self.status),
+                        None if t_end is None else p(t_end))
+
+
+def compact_work(n: int, device="cuda") -> torch.Tensor:
+    """A 256-byte aligned device scratch buffer for chs_integrate_compacted."""
+    return torch.empty(chs_compact_work_size(n), dtype=torch.uint8, device=device)

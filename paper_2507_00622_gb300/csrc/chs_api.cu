@@ -5,14 +5,29 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
+#include <utility>
 
 #include "chs_internal.cuh"
+
+// Recorded chunk sequence of chs_integrate_compacted and the inputs it was
+// recorded for.
+struct CompactGraph {
+    bool valid = false;
+    chs_params p{};
+    chs_ensemble e{};
+    int32_t chunk = 0;
+    void* work = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
 
 struct chs_system_s {
     chs::SysPar sp;
     int device;
+    cudaStream_t capture = nullptr;  // private stream used only to record graphs
+    CompactGraph graph;
 };
 
 namespace {
@@ -47,7 +62,8 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
 chs::EnsPtrs ens_ptrs(const chs_ensemble* e)
 {
-    return chs::EnsPtrs{e->n_orbits, e->x, e->w, e->ld, e->h0, e->dh_max, e->n_exec, e->status};
+    return chs::EnsPtrs{e->n_orbits, e->x, e->w, e->ld, e->h0, e->dh_max, e->n_exec, e->status,
+                        e->t_end};
 }
 
 // Largest number of deviation vectors an ensemble of the system may carry.
@@ -68,7 +84,9 @@ chs_status check_params(const chs_params* p, const chs::SysPar& sp)
     if (p->renorm != 0 && p->renorm != 1) return fail(CHS_E_INVALID, "renorm must be 0 or 1");
     if (p->vec_precision != CHS_VEC_FP64 && p->vec_precision != CHS_VEC_FP32)
         return fail(CHS_E_INVALID, "vec_precision must be CHS_VEC_FP64 or CHS_VEC_FP32");
-    if (p->reserved != 0) return fail(CHS_E_INVALID, "reserved must be 0");
+    if (p->early_exit != 0 && p->early_exit != 1) return fail(CHS_E_INVALID, "early_exit must be 0 or 1");
+    if (p->early_exit && p->n_dev < 2) return fail(CHS_E_INVALID, "early_exit needs n_dev >= 2");
+    if (!(p->sali_threshold >= 0.0)) return fail(CHS_E_INVALID, "sali_threshold must be >= 0");
     if (p->vec_precision == CHS_VEC_FP32 && p->n_dev > 0 && p->renorm != 1)
         return fail(CHS_E_INVALID, "FP32 vectors are re-orthonormalised every step: renorm must be 1");
     if (!(p->ld_p >= 0.0) || !isfinite(p->ld_p)) return fail(CHS_E_INVALID, "ld_p must be finite and >= 0");
@@ -103,6 +121,8 @@ chs::StepArgs step_args(const chs_params* p)
     a.ld_p = p->ld_p;
     a.escape_r2 = p->escape_r2;
     a.dh_limit = p->dh_limit;
+    a.early_exit = p->early_exit;
+    a.sali_threshold = p->sali_threshold;
     return a;
 }
 
@@ -171,6 +191,9 @@ chs_status chs_create_system(chs_system* out, chs_model model, int32_t n_dof, co
 
 chs_status chs_destroy_system(chs_system s)
 {
+    if (!s) return ok();
+    if (s->graph.exec) cudaGraphExecDestroy(s->graph.exec);
+    if (s->capture) cudaStreamDestroy(s->capture);
     delete s;
     return ok();
 }
@@ -209,6 +232,19 @@ chs_status chs_fput_mode_ics(chs_system s, int64_t n, const double* Qm, const do
                        "normal-mode launch");
 }
 
+chs_status chs_shell_ics(chs_system s, int64_t n, const double* dirs, const double* E,
+                         double* ics_out, void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (s->sp.model != CHS_QUARTIC3) return fail(CHS_E_UNSUPPORTED, "shell ICs are for QUARTIC3");
+    if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
+    if (n == 0) return ok();
+    if (!dirs || !E || !ics_out) return fail(CHS_E_INVALID, "pointers must be non-NULL");
+    return cuda_status(chs::launch_shell_ics(s->sp, n, dirs, E, ics_out, as_stream(stream)),
+                       "shell ICs launch");
+}
+
 chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemble* e,
                              const double* ics, const int32_t* ic_status, const void* w_in,
                              void* stream)
@@ -236,8 +272,91 @@ chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ense
     if ((r = check_ensemble(e, p)) != CHS_OK) return r;
     if (e->n_orbits == 0 || p->n_steps == 0) return ok();
     return cuda_status(chs::launch_integrate(s->sp, p->n_dev, p->vec_precision, p->ld_p > 0.0,
-                                             step_args(p), ens_ptrs(e), as_stream(stream)),
+                                             step_args(p), ens_ptrs(e), nullptr, as_stream(stream)),
                        "integrate launch");
+}
+
+size_t chs_compact_work_size(int64_t n_orbits)
+{
+    if (n_orbits < 0) return 0;
+    const size_t list = (((size_t)n_orbits * sizeof(int32_t)) + 255) / 256 * 256;
+    return 2 * list + 256;
+}
+
+chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_ensemble* e,
+                                   int32_t chunk_steps, void* work, size_t work_bytes, void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (!chs::small_model(s->sp.model))
+        return fail(CHS_E_UNSUPPORTED, "integration is implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
+    if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ensemble(e, p)) != CHS_OK) return r;
+    if (chunk_steps < 1) return fail(CHS_E_INVALID, "chunk_steps must be >= 1");
+    if (e->n_orbits > INT32_MAX) return fail(CHS_E_SIZE, "compacted runs support at most 2^31 - 1 orbits");
+    if (e->n_orbits == 0 || p->n_steps == 0) return ok();
+    const int64_t n_chunks = (p->n_steps + chunk_steps - 1) / chunk_steps;
+    if (n_chunks > 100000) return fail(CHS_E_SIZE, "more than 100000 chunks: raise chunk_steps");
+    if (!work || ((uintptr_t)work & 255u)) return fail(CHS_E_INVALID, "work must be a 256-byte aligned device buffer");
+    if (work_bytes < chs_compact_work_size(e->n_orbits))
+        return fail(CHS_E_SIZE, "work buffer smaller than chs_compact_work_size(n)");
+
+    CompactGraph& G = s->graph;
+    const bool same = G.valid && G.chunk == chunk_steps && G.work == work &&
+                      memcmp(&G.p, p, sizeof(chs_params)) == 0 &&
+                      memcmp(&G.e, e, sizeof(chs_ensemble)) == 0;
+    if (!same) {
+        if (G.exec) {
+            cudaGraphExecDestroy(G.exec);
+            G.exec = nullptr;
+        }
+        G.valid = false;
+        cudaError_t ce;
+        if (!s->capture && (ce = cudaStreamCreateWithFlags(&s->capture, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_status(ce, "capture stream");
+        const size_t list_bytes = (((size_t)e->n_orbits * sizeof(int32_t)) + 255) / 256 * 256;
+        int32_t* la = static_cast<int32_t*>(work);
+        int32_t* lb = reinterpret_cast<int32_t*>(static_cast<char*>(work) + list_bytes);
+        int32_t* ca = reinterpret_cast<int32_t*>(static_cast<char*>(work) + 2 * list_bytes);
+        int32_t* cb = ca + 1;
+        const chs::EnsPtrs ep = ens_ptrs(e);
+        cudaStream_t cs = s->capture;
+        if ((ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return cuda_status(ce, "begin capture");
+        cudaError_t le = cudaMemsetAsync(ca, 0, sizeof(int32_t), cs);
+        if (le == cudaSuccess) le = chs::launch_list_init(ep, la, ca, cs);
+        for (int64_t c = 0; c < n_chunks && le == cudaSuccess; ++c) {
+            chs::StepArgs a = step_args(p);
+            a.step0 = p->step0 + c * chunk_steps;
+            a.n_steps = std::min<int64_t>(chunk_steps, p->n_steps - c * chunk_steps);
+            le = cudaMemsetAsync(cb, 0, sizeof(int32_t), cs);
+            const chs::OrbitList ol{la, ca, lb, cb};
+            if (le == cudaSuccess)
+                le = chs::launch_integrate(s->sp, p->n_dev, p->vec_precision, p->ld_p > 0.0, a, ep,
+                                           &ol, cs);
+            std::swap(la, lb);
+            std::swap(ca, cb);
+        }
+        cudaGraph_t graph = nullptr;
+        ce = cudaStreamEndCapture(cs, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_status(le, "recording the chunk sequence");
+        }
+        if (ce != cudaSuccess) return cuda_status(ce, "end capture");
+        ce = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            G.exec = nullptr;
+            return cuda_status(ce, "graph instantiate");
+        }
+        G.p = *p;
+        G.e = *e;
+        G.chunk = chunk_steps;
+        G.work = work;
+        G.valid = true;
+    }
+    return cuda_status(cudaGraphLaunch(G.exec, as_stream(stream)), "graph launch");
 }
 
 chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble* e, int32_t grid_ny,

@@ -28,6 +28,16 @@ struct EnsPtrs {
     double* dh_max;
     int64_t* n_exec;
     int32_t* status;
+    const int64_t* t_end;  // optional per-orbit end step
+};
+
+// Optional orbit list for compacted runs: thread t integrates orbit list[t] for
+// t < *count and appends the orbits still running to next / *next_count.
+struct OrbitList {
+    const int32_t* list;
+    const int32_t* count;
+    int32_t* next;
+    int32_t* next_count;
 };
 
 // Integration controls, validated on the host.
@@ -42,6 +52,8 @@ struct StepArgs {
     double ld_p;
     double escape_r2;      // 0: off
     double dh_limit;       // 0: off
+    int32_t early_exit;    // freeze as EARLY_CHAOTIC once SALI < sali_threshold
+    double sali_threshold;
 };
 
 // Launchers (host side, one per kernel family).  Each returns the launch error.
@@ -53,7 +65,10 @@ cudaError_t launch_init(const SysPar& sp, int k, int vec_fp32, int renorm, uint6
                         const double* ics, const int32_t* ic_status, const void* w_in,
                         const EnsPtrs& e, cudaStream_t st);
 cudaError_t launch_integrate(const SysPar& sp, int k, int vec_fp32, bool ld, const StepArgs& a,
-                             const EnsPtrs& e, cudaStream_t st);
+                             const EnsPtrs& e, const OrbitList* ol, cudaStream_t st);
+cudaError_t launch_list_init(const EnsPtrs& e, int32_t* list, int32_t* count, cudaStream_t st);
+cudaError_t launch_shell_ics(const SysPar& sp, int64_t n, const double* dirs, const double* E,
+                             double* ics, cudaStream_t st);
 cudaError_t launch_indicators(const SysPar& sp, int k, int vec_fp32, double sali_threshold,
                               const EnsPtrs& e, double* sali, double* gali, int8_t* label,
                               cudaStream_t st);
@@ -62,7 +77,7 @@ cudaError_t launch_init_f32(const SysPar& sp, int k, uint64_t seed, const double
                             const int32_t* ic_status, const void* w_in, const EnsPtrs& e,
                             cudaStream_t st);
 cudaError_t launch_integrate_f32(const SysPar& sp, int k, bool ld, const StepArgs& a,
-                                 const EnsPtrs& e, cudaStream_t st);
+                                 const EnsPtrs& e, const OrbitList* ol, cudaStream_t st);
 cudaError_t launch_indicators_f32(const SysPar& sp, int k, double sali_threshold, const EnsPtrs& e,
                                   double* sali, double* gali, int8_t* label, cudaStream_t st);
 cudaError_t launch_ld_stencil(int ny, int npy, const double* ld, const int32_t* status,
@@ -77,6 +92,20 @@ cudaError_t launch_fput_lyap(const SysPar& sp, const StepArgs& a, int64_t n, con
 // Which systems each kernel family supports.
 bool small_model(int model);
 bool fput_lyap_supported(int n_dof);
+
+// Appends orbit o to ol.next when keep is set, one atomic per converged group of
+// lanes.
+__device__ __forceinline__ void list_append(const OrbitList& ol, bool keep, int32_t o)
+{
+    const unsigned act = __activemask();
+    const unsigned ballot = __ballot_sync(act, keep);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if (lane == leader && ballot) base = atomicAdd(ol.next_count, __popc(ballot));
+    base = __shfl_sync(act, base, leader);
+    if (keep) ol.next[base + __popc(ballot & ((1u << lane) - 1u))] = o;
+}
 
 inline unsigned blocks_for(int64_t n, int per_block)
 {

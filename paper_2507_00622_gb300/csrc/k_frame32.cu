@@ -125,13 +125,18 @@ k_init_f32(const SysPar sp, const uint64_t seed, const double* __restrict__ ics,
     for (int p = 0; p < K * (K + 1) / 2; ++p) wg[(K * D + p) * n + o] = (float)R[p];
 }
 
-template <class Sys, int K, bool LD>
+template <class Sys, int K, bool LD, bool LIST>
 __global__ void __launch_bounds__(kSmallBlock)
-k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e)
+k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
 {
     constexpr int N = Sys::N, D = 2 * N, NH = Sys::NH, NR = K * (K + 1) / 2;
     const int64_t n = e.n;
-    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t o = t;
+    if (LIST) {
+        if (t >= *ol.count) return;
+        o = ol.list[t];
+    }
     if (o >= n) return;
     if (e.status[o] != CHS_ORBIT_OK) return;
 
@@ -149,11 +154,14 @@ k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e)
     double L = LD ? e.ld[o] : 0.0;
     const double h0 = e.h0[o];
     double dhm = e.dh_max[o];
+    const int64_t exec0 = e.n_exec[o];
+    int64_t todo = a.n_steps;
+    if (e.t_end) todo = min(todo, max(e.t_end[o] - exec0, (int64_t)0));
 
     int32_t st = CHS_ORBIT_OK;
     int64_t until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
     int64_t s = 0;
-    while (s < a.n_steps) {
+    while (s < todo) {
         ++s;
         double H[4][NH];
         rk4_state_capture<Sys, LD>(x, L, a.dt, a.ld_sqrt, a.ld_p, sp, H);
@@ -231,6 +239,14 @@ k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e)
                 st = CHS_ORBIT_ENERGY_DRIFT;
                 break;
             }
+            if constexpr (K >= 2) {
+                const double sv = fabs((double)R[tri(1, 1)]) *
+                                  sqrt(2.0 / (1.0 + fmin(fabs((double)R[tri(0, 1)]), 1.0)));
+                if (a.early_exit && sv < a.sali_threshold) {
+                    st = CHS_ORBIT_EARLY_CHAOTIC;
+                    break;
+                }
+            }
         }
     }
 
@@ -244,8 +260,9 @@ k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e)
     for (int p = 0; p < NR; ++p) wg[(K * D + p) * n + o] = R[p];
     if (LD) e.ld[o] = L;
     e.dh_max[o] = dhm;
-    e.n_exec[o] += s;
+    e.n_exec[o] = exec0 + s;
     e.status[o] = st;
+    if (LIST) list_append(ol, st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]), (int32_t)o);
 }
 
 // SALI, GALI_m and labels from the triangular factor (see the file comment).
@@ -279,6 +296,8 @@ k_indicators_f32(const int64_t n, const float* __restrict__ wg, const int32_t* _
         int8_t lb;
         if (st == CHS_ORBIT_OK)
             lb = (sv < thr) ? 1 : 0;
+        else if (st == CHS_ORBIT_EARLY_CHAOTIC)
+            lb = 1;
         else if (st == CHS_ORBIT_ESCAPED)
             lb = 2;
         else
@@ -343,30 +362,33 @@ cudaError_t launch_init_f32(const SysPar& sp, int k, uint64_t seed, const double
 
 template <class Sys, int K, bool LD>
 static void integ_one(const unsigned g, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
-                      cudaStream_t st)
+                      const OrbitList* ol, cudaStream_t st)
 {
-    k_integrate_f32<Sys, K, LD><<<g, kSmallBlock, 0, st>>>(a, sp, e);
+    if (ol)
+        k_integrate_f32<Sys, K, LD, true><<<g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+    else
+        k_integrate_f32<Sys, K, LD, false><<<g, kSmallBlock, 0, st>>>(a, sp, e, OrbitList{});
 }
 
 template <class Sys, bool LD>
 static cudaError_t integ_sys(int k, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
-                             cudaStream_t st)
+                             const OrbitList* ol, cudaStream_t st)
 {
     const unsigned g = blocks_for(e.n, kSmallBlock);
     switch (k) {
-    case 1: integ_one<Sys, 1, LD>(g, a, sp, e, st); break;
-    case 2: integ_one<Sys, 2, LD>(g, a, sp, e, st); break;
-    case 3: integ_one<Sys, 3, LD>(g, a, sp, e, st); break;
-    case 4: integ_one<Sys, 4, LD>(g, a, sp, e, st); break;
+    case 1: integ_one<Sys, 1, LD>(g, a, sp, e, ol, st); break;
+    case 2: integ_one<Sys, 2, LD>(g, a, sp, e, ol, st); break;
+    case 3: integ_one<Sys, 3, LD>(g, a, sp, e, ol, st); break;
+    case 4: integ_one<Sys, 4, LD>(g, a, sp, e, ol, st); break;
     case 5:
         if constexpr (Sys::N >= 3) {
-            integ_one<Sys, 5, LD>(g, a, sp, e, st);
+            integ_one<Sys, 5, LD>(g, a, sp, e, ol, st);
             break;
         }
         return cudaErrorInvalidValue;
     case 6:
         if constexpr (Sys::N >= 3) {
-            integ_one<Sys, 6, LD>(g, a, sp, e, st);
+            integ_one<Sys, 6, LD>(g, a, sp, e, ol, st);
             break;
         }
         return cudaErrorInvalidValue;
@@ -377,22 +399,22 @@ static cudaError_t integ_sys(int k, const StepArgs& a, const SysPar& sp, const E
 }
 
 cudaError_t launch_integrate_f32(const SysPar& sp, int k, bool ld, const StepArgs& a,
-                                 const EnsPtrs& e, cudaStream_t st)
+                                 const EnsPtrs& e, const OrbitList* ol, cudaStream_t st)
 {
     if (e.n == 0 || a.n_steps == 0) return cudaSuccess;
     switch (sp.model) {
     case CHS_HENON_HEILES:
-        return ld ? integ_sys<SysHenonHeiles, true>(k, a, sp, e, st)
-                  : integ_sys<SysHenonHeiles, false>(k, a, sp, e, st);
+        return ld ? integ_sys<SysHenonHeiles, true>(k, a, sp, e, ol, st)
+                  : integ_sys<SysHenonHeiles, false>(k, a, sp, e, ol, st);
     case CHS_HARMONIC:
-        return ld ? integ_sys<SysHarmonic, true>(k, a, sp, e, st)
-                  : integ_sys<SysHarmonic, false>(k, a, sp, e, st);
+        return ld ? integ_sys<SysHarmonic, true>(k, a, sp, e, ol, st)
+                  : integ_sys<SysHarmonic, false>(k, a, sp, e, ol, st);
     case CHS_INVERTED:
-        return ld ? integ_sys<SysInverted, true>(k, a, sp, e, st)
-                  : integ_sys<SysInverted, false>(k, a, sp, e, st);
+        return ld ? integ_sys<SysInverted, true>(k, a, sp, e, ol, st)
+                  : integ_sys<SysInverted, false>(k, a, sp, e, ol, st);
     case CHS_QUARTIC3:
-        return ld ? integ_sys<SysQuartic3, true>(k, a, sp, e, st)
-                  : integ_sys<SysQuartic3, false>(k, a, sp, e, st);
+        return ld ? integ_sys<SysQuartic3, true>(k, a, sp, e, ol, st)
+                  : integ_sys<SysQuartic3, false>(k, a, sp, e, ol, st);
     }
     return cudaErrorInvalidValue;
 }

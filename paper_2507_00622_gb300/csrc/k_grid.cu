@@ -139,4 +139,41 @@ cudaError_t launch_fput_mode_ics(const SysPar& sp, int64_t n, const double* Qm, 
     return cudaGetLastError();
 }
 
+// Quartic-3 initial conditions on energy shells: u = dir / |dir|, scaled by s
+// with H(s u) = E, s^2 = 2E / (H2 + sqrt(H2^2 + 4 H4 E)), H2 = |u|^2 / 2,
+// H4 = eps (u1^2 u2^2 + u2^2 u3^2 + u1^2 u3^2).
+__global__ void k_shell_ics(const SysPar sp, const int64_t n, const double* __restrict__ dirs,
+                            const double* __restrict__ E, double* __restrict__ ics)
+{
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    double u[6], nr = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        u[c] = dirs[c * n + o];
+        nr = fma(u[c], u[c], nr);
+    }
+    const double inv = 1.0 / sqrt(nr);
+    double H2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        u[c] *= inv;
+        H2 = fma(0.5 * u[c], u[c], H2);
+    }
+    const double a = u[0] * u[0], b = u[1] * u[1], c2 = u[2] * u[2];
+    const double H4 = sp.eps * (a * b + b * c2 + a * c2);
+    const double Eo = E[o];
+    const double sc = sqrt(2.0 * Eo / (H2 + sqrt(H2 * H2 + 4.0 * H4 * Eo)));
+#pragma unroll
+    for (int c = 0; c < 6; ++c) ics[c * n + o] = sc * u[c];
+}
+
+cudaError_t launch_shell_ics(const SysPar& sp, int64_t n, const double* dirs, const double* E,
+                             double* ics, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    k_shell_ics<<<blocks_for(n, 128), 128, 0, st>>>(sp, n, dirs, E, ics);
+    return cudaGetLastError();
+}
+
 }  // namespace chs

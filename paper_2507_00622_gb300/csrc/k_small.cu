@@ -204,14 +204,42 @@ __device__ __forceinline__ void rk4_step(double* x, double (*w)[2 * Sys::N], dou
         rk4_step_direct<Sys, K, LD, double>(x, w, L, h, ld_sqrt, ld_p, sp);
 }
 
-template <class Sys, int K, bool LD>
+// SALI of two vectors (each normalised first): min(|u + v|, |u - v|).
+template <int D>
+__device__ __forceinline__ double sali_of(const double* a, const double* b)
+{
+    double na = a[0] * a[0], nb = b[0] * b[0];
+#pragma unroll
+    for (int c = 1; c < D; ++c) {
+        na = fma(a[c], a[c], na);
+        nb = fma(b[c], b[c], nb);
+    }
+    const double ia = rsqrt_nr(na), ib = rsqrt_nr(nb);
+    double sp = 0.0, sm = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const double u = a[c] * ia, v = b[c] * ib;
+        sp = fma(u + v, u + v, sp);
+        sm = fma(u - v, u - v, sm);
+    }
+    return sqrt(fmin(sp, sm));
+}
+
+// One thread per orbit.  LIST: thread t takes orbit list[t] (t < *count) and
+// appends the orbit to the next list when it is still running after the call.
+template <class Sys, int K, bool LD, bool LIST>
 __global__ void __launch_bounds__(kSmallBlock)
-k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e)
+k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
 {
     constexpr int N = Sys::N, D = 2 * N;
     constexpr int KK = K > 0 ? K : 1;
     const int64_t n = e.n;
-    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t o = t;
+    if (LIST) {
+        if (t >= *ol.count) return;
+        o = ol.list[t];
+    }
     if (o >= n) return;
     if (e.status[o] != CHS_ORBIT_OK) return;
 
@@ -227,11 +255,14 @@ k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e)
     double L = LD ? e.ld[o] : 0.0;
     const double h0 = e.h0[o];
     double dhm = e.dh_max[o];
+    const int64_t exec0 = e.n_exec[o];
+    int64_t todo = a.n_steps;
+    if (e.t_end) todo = min(todo, max(e.t_end[o] - exec0, (int64_t)0));
 
     int32_t st = CHS_ORBIT_OK;
     int64_t until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
     int64_t s = 0;
-    while (s < a.n_steps) {
+    while (s < todo) {
         ++s;
         rk4_step<Sys, K, LD>(x, w, L, a.dt, a.ld_sqrt, a.ld_p, sp);
         if (a.renorm) {
@@ -273,6 +304,12 @@ k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e)
                 st = CHS_ORBIT_ENERGY_DRIFT;
                 break;
             }
+            if constexpr (K >= 2) {
+                if (a.early_exit && sali_of<D>(w[0], w[1]) < a.sali_threshold) {
+                    st = CHS_ORBIT_EARLY_CHAOTIC;
+                    break;
+                }
+            }
         }
     }
 
@@ -284,8 +321,27 @@ k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e)
         for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = w[j][c];
     if (LD) e.ld[o] = L;
     e.dh_max[o] = dhm;
-    e.n_exec[o] += s;
+    e.n_exec[o] = exec0 + s;
     e.status[o] = st;
+    if (LIST) list_append(ol, st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]), (int32_t)o);
+}
+
+// Orbits that can still advance: status OK and below their end step.
+__global__ void k_list_init(const EnsPtrs e, int32_t* __restrict__ list, int32_t* __restrict__ count)
+{
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= e.n) return;
+    bool keep = e.status[o] == CHS_ORBIT_OK;
+    if (keep && e.t_end) keep = e.n_exec[o] < e.t_end[o];
+    OrbitList ol{nullptr, nullptr, list, count};
+    list_append(ol, keep, (int32_t)o);
+}
+
+cudaError_t launch_list_init(const EnsPtrs& e, int32_t* list, int32_t* count, cudaStream_t st)
+{
+    if (e.n == 0) return cudaSuccess;
+    k_list_init<<<blocks_for(e.n, 256), 256, 0, st>>>(e, list, count);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------
@@ -358,6 +414,8 @@ k_indicators(const int64_t n, const VT* __restrict__ wg, const int32_t* __restri
         int8_t lb;
         if (st == CHS_ORBIT_OK)
             lb = (sv < thr) ? 1 : 0;
+        else if (st == CHS_ORBIT_EARLY_CHAOTIC)
+            lb = 1;
         else if (st == CHS_ORBIT_ESCAPED)
             lb = 2;
         else
@@ -493,27 +551,36 @@ cudaError_t launch_init(const SysPar& sp, int k, int vec_fp32, int renorm, uint6
     return cudaErrorInvalidValue;
 }
 
+template <class Sys, int K, bool LD>
+static void integ_one(const unsigned g, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
+                      const OrbitList* ol, cudaStream_t st)
+{
+    if (ol)
+        k_integrate<Sys, K, LD, true><<<g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+    else
+        k_integrate<Sys, K, LD, false><<<g, kSmallBlock, 0, st>>>(a, sp, e, OrbitList{});
+}
+
 template <class Sys, bool LD>
 static cudaError_t integ_k(int k, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
-                           cudaStream_t st)
+                           const OrbitList* ol, cudaStream_t st)
 {
     const unsigned g = blocks_for(e.n, kSmallBlock);
     switch (k) {
-#define CHS_CASE(KV)                                                      \
-    case KV:                                                              \
-        k_integrate<Sys, KV, LD><<<g, kSmallBlock, 0, st>>>(a, sp, e); \
-        break;
-        CHS_CASE(0) CHS_CASE(1) CHS_CASE(2) CHS_CASE(3) CHS_CASE(4)
-#undef CHS_CASE
+    case 0: integ_one<Sys, 0, LD>(g, a, sp, e, ol, st); break;
+    case 1: integ_one<Sys, 1, LD>(g, a, sp, e, ol, st); break;
+    case 2: integ_one<Sys, 2, LD>(g, a, sp, e, ol, st); break;
+    case 3: integ_one<Sys, 3, LD>(g, a, sp, e, ol, st); break;
+    case 4: integ_one<Sys, 4, LD>(g, a, sp, e, ol, st); break;
     case 5:
         if constexpr (Sys::N >= 3) {
-            k_integrate<Sys, 5, LD><<<g, kSmallBlock, 0, st>>>(a, sp, e);
+            integ_one<Sys, 5, LD>(g, a, sp, e, ol, st);
             break;
         }
         return cudaErrorInvalidValue;
     case 6:
         if constexpr (Sys::N >= 3) {
-            k_integrate<Sys, 6, LD><<<g, kSmallBlock, 0, st>>>(a, sp, e);
+            integ_one<Sys, 6, LD>(g, a, sp, e, ol, st);
             break;
         }
         return cudaErrorInvalidValue;
@@ -525,21 +592,21 @@ static cudaError_t integ_k(int k, const StepArgs& a, const SysPar& sp, const Ens
 
 template <class Sys>
 static cudaError_t integ_sys(int k, bool ld, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
-                             cudaStream_t st)
+                             const OrbitList* ol, cudaStream_t st)
 {
-    return ld ? integ_k<Sys, true>(k, a, sp, e, st) : integ_k<Sys, false>(k, a, sp, e, st);
+    return ld ? integ_k<Sys, true>(k, a, sp, e, ol, st) : integ_k<Sys, false>(k, a, sp, e, ol, st);
 }
 
 cudaError_t launch_integrate(const SysPar& sp, int k, int vec_fp32, bool ld, const StepArgs& a,
-                             const EnsPtrs& e, cudaStream_t st)
+                             const EnsPtrs& e, const OrbitList* ol, cudaStream_t st)
 {
     if (e.n == 0 || a.n_steps == 0) return cudaSuccess;
-    if (vec_fp32 && k > 0) return launch_integrate_f32(sp, k, ld, a, e, st);
+    if (vec_fp32 && k > 0) return launch_integrate_f32(sp, k, ld, a, e, ol, st);
     switch (sp.model) {
-    case CHS_HENON_HEILES: return integ_sys<SysHenonHeiles>(k, ld, a, sp, e, st);
-    case CHS_HARMONIC: return integ_sys<SysHarmonic>(k, ld, a, sp, e, st);
-    case CHS_INVERTED: return integ_sys<SysInverted>(k, ld, a, sp, e, st);
-    case CHS_QUARTIC3: return integ_sys<SysQuartic3>(k, ld, a, sp, e, st);
+    case CHS_HENON_HEILES: return integ_sys<SysHenonHeiles>(k, ld, a, sp, e, ol, st);
+    case CHS_HARMONIC: return integ_sys<SysHarmonic>(k, ld, a, sp, e, ol, st);
+    case CHS_INVERTED: return integ_sys<SysInverted>(k, ld, a, sp, e, ol, st);
+    case CHS_QUARTIC3: return integ_sys<SysQuartic3>(k, ld, a, sp, e, ol, st);
     }
     return cudaErrorInvalidValue;
 }

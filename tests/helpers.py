@@ -34,14 +34,15 @@ def oracle_system(model: int, n_dof: int, sys_params=()):
 
 def oracle_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=True,
                sample_every=100, escape_r2=0.0, dh_limit=0.0, seed=1, w_in=None,
-               sali_threshold=1e-8, chunks=None, grid=None, sys_params=()):
+               sali_threshold=1e-8, chunks=None, grid=None, sys_params=(), early_exit=False,
+               t_end=None):
     S = oracle_system(model, n_dof, sys_params)
     kw = dict(n_dev=k, ld_p=ld_p, renorm=renorm, sample_every=sample_every, escape_r2=escape_r2,
-              dh_limit=dh_limit)
+              dh_limit=dh_limit, early_exit=early_exit, sali_threshold=sali_threshold)
     e = O.Ensemble(S, O.params(dt, 1, **kw), ics, ic_status, w_in=w_in, seed=seed)
     step = 0
     for c in (chunks or [n_steps]):
-        e.integrate(O.params(dt, c, step0=step, **kw))
+        e.integrate(O.params(dt, c, step0=step, **kw), t_end=t_end)
         step += c
     out = dict(x=e.x, w=e.w, ld=e.ld, dh_max=e.dh_max, n_exec=e.n_exec, status=e.status)
     if k >= 2:
@@ -56,7 +57,7 @@ def oracle_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm
 def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=True,
             sample_every=100, escape_r2=0.0, dh_limit=0.0, seed=1, w_in=None,
             sali_threshold=1e-8, chunks=None, grid=None, vec_fp32=False, sys_params=(),
-            device_seed=True):
+            early_exit=False, t_end=None, compact_chunk=None):
     import torch
 
     from paper_2507_00622_gb300 import chs
@@ -66,7 +67,8 @@ def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=Tr
     ens = chs.DeviceEnsemble.empty(n, S.d, k, vec_fp32)
     vp = chs.VEC_FP32 if vec_fp32 else chs.VEC_FP64
     kw = dict(n_dev=k, ld_p=ld_p, renorm=renorm, sample_every=sample_every, escape_r2=escape_r2,
-              dh_limit=dh_limit, sali_threshold=sali_threshold, seed=seed, vec_precision=vp)
+              dh_limit=dh_limit, sali_threshold=sali_threshold, seed=seed, vec_precision=vp,
+              early_exit=early_exit)
     ics_t = torch.from_numpy(np.ascontiguousarray(ics)).cuda()
     st_t = None if ic_status is None else torch.from_numpy(
         np.ascontiguousarray(ic_status, dtype=np.int32)).cuda()
@@ -74,11 +76,16 @@ def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=Tr
     if w_in is not None:
         w_t = torch.from_numpy(np.ascontiguousarray(w_in)).to(
             torch.float32 if vec_fp32 else torch.float64).cuda()
-    abi = ens.abi(with_ld=ld_p > 0)
+    te_t = None if t_end is None else torch.from_numpy(np.ascontiguousarray(t_end, dtype=np.int64)).cuda()
+    abi = ens.abi(with_ld=ld_p > 0, t_end=te_t)
     chs.chs_ensemble_init(S.h, chs.params(dt, 1, **kw), abi, ics_t, st_t, w_t)
     step = 0
+    work = chs.compact_work(n) if compact_chunk else None
     for c in (chunks or [n_steps]):
-        chs.chs_integrate_batch(S.h, chs.params(dt, c, step0=step, **kw), abi)
+        if compact_chunk:
+            chs.chs_integrate_compacted(S.h, chs.params(dt, c, step0=step, **kw), abi, compact_chunk, work)
+        else:
+            chs.chs_integrate_batch(S.h, chs.params(dt, c, step0=step, **kw), abi)
         step += c
     out = {}
     prm = chs.params(dt, 0, **kw)

@@ -62,7 +62,7 @@ def test_struct_layouts_match_header(lib):
     from paper_2507_00622_gb300 import chs
     # chs_params: 1 double, 2 int64, 6 int32, 4 double, 1 uint64 = 88 bytes
     assert C.sizeof(chs.Params) == 88
-    assert C.sizeof(chs.Ensemble) == 64
+    assert C.sizeof(chs.Ensemble) == 72
 
 
 def test_binding_refuses_host_tensors(lib):

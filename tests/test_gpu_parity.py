@@ -368,3 +368,75 @@ def test_full_size_grid_sampled_against_oracle():
     m = ~np.isnan(dl)
     np.testing.assert_array_equal(dl[m], g["dl"][m])
     np.testing.assert_array_equal(sl[m], g["sl"][m])
+
+
+# --------------------------------------------------------------------------
+# early exit, uneven end steps, compacted graph runs, quartic shell ICs
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("vec_fp32", [False, True])
+def test_early_exit_matches_oracle(vec_fp32):
+    g0 = _grid(1 / 8, 32, 32)
+    ics, st = O.grid_ics(*g0)
+    kw = dict(dt=0.01, n_steps=100000, k=2, ld_p=0.5, escape_r2=4.0, early_exit=True)
+    g = gpu_run(HH, 2, ics, st, vec_fp32=vec_fp32, **kw)
+    r = oracle_run(HH, 2, ics, st, **kw)
+    v = st == 0
+    early = r["status"] == chs.ORBIT_EARLY_CHAOTIC
+    assert early.sum() > 100
+    # the stop is a floating-point decision taken at health checks: stop steps agree
+    # exactly on nearly all orbits, labels on >= 99.5 %
+    assert (g["status"][v] == r["status"][v]).mean() >= LABEL_AGREE
+    assert (g["n_exec"][v] == r["n_exec"][v]).mean() >= 0.99
+    assert (g["label"][v] == r["label"][v]).mean() >= LABEL_AGREE
+    assert np.all(g["label"][g["status"] == chs.ORBIT_EARLY_CHAOTIC] == 1)
+
+
+@pytest.mark.parametrize("vec_fp32", [False, True])
+def test_compacted_graph_run_is_bit_identical_to_plain(vec_fp32):
+    g0 = _grid(1 / 6, 40, 40)
+    ics, st = O.grid_ics(*g0)
+    rng = np.random.default_rng(3)
+    t_end = rng.integers(0, 6000, ics.shape[1]).astype(np.int64)
+    kw = dict(dt=0.01, k=3, ld_p=0.5, escape_r2=4.0, early_exit=True, t_end=t_end,
+              vec_fp32=vec_fp32, seed=5)
+    a = gpu_run(HH, 2, ics, st, n_steps=5000, **kw)
+    b = gpu_run(HH, 2, ics, st, n_steps=5000, chunks=[2300, 2700], compact_chunk=300, **kw)
+    for key in ("x", "w", "ld", "dh_max", "n_exec", "status", "sali", "gali", "label"):
+        np.testing.assert_array_equal(a[key], b[key])
+    ok = st == 0
+    np.testing.assert_array_equal(a["n_exec"][ok & (a["status"] == 0)],
+                                  np.minimum(t_end, 5000)[ok & (a["status"] == 0)])
+
+
+def test_uneven_end_steps_match_oracle():
+    g0 = _grid(1 / 8, 20, 20)
+    ics, st = O.grid_ics(*g0)
+    t_end = np.random.default_rng(8).integers(100, 3000, ics.shape[1]).astype(np.int64)
+    kw = dict(dt=0.01, n_steps=3000, k=2, ld_p=0.5, escape_r2=4.0, t_end=t_end)
+    g = gpu_run(HH, 2, ics, st, compact_chunk=500, **kw)
+    r = oracle_run(HH, 2, ics, st, **kw)
+    np.testing.assert_array_equal(g["n_exec"], r["n_exec"])
+    ok = st == 0
+    assert state_rel_err(g["x"][:, ok], r["x"][:, ok]).max() < STATE_RTOL
+    assert ind_err(g["ld"][ok], r["ld"][ok]).max() < IND_TOL
+
+
+def test_quartic_shell_ics_and_fp32_gali6():
+    n = 500
+    rng = np.random.default_rng(17)
+    dirs = rng.standard_normal((6, n))
+    E = rng.uniform(1.0, 10.0, n)
+    S = chs.System(chs.QUARTIC3, 3, (0.1,))
+    ics = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    chs.chs_shell_ics(S.h, n, torch.from_numpy(dirs).cuda(), torch.from_numpy(E).cuda(), ics)
+    ref = O.shell_ics(O.system(O.QUARTIC3, 3, eps=0.1), dirs, E)
+    gi = ics.cpu().numpy()
+    assert state_rel_err(gi, ref).max() < 1e-13
+    kw = dict(dt=0.01, n_steps=2000, k=6, ld_p=0.5, sys_params=(0.1,), seed=4)
+    g = gpu_run(chs.QUARTIC3, 3, ref, None, vec_fp32=True, **kw)
+    r = oracle_run(chs.QUARTIC3, 3, ref, None, **kw)
+    assert state_rel_err(g["x"], r["x"]).max() < STATE_RTOL
+    big = np.abs(r["gali"]) > 1e-6
+    rel = np.abs(g["gali"][big] - r["gali"][big]) / r["gali"][big]
+    assert np.median(rel) < 1e-3

@@ -509,3 +509,57 @@ def test_ld_indicators_on_synthetic_fields():
     for o in (3 * npy + 4, 2 * npy + 4, 4 * npy + 4, 3 * npy + 3, 3 * npy + 5):
         assert np.isnan(dl[o]) and np.isnan(sl[o])
     assert np.isfinite(dl[2 * npy + 2])
+
+
+# --------------------------------------------------------------------------
+# early exit, per-orbit end steps, quartic shell initial conditions
+# --------------------------------------------------------------------------
+
+def test_early_exit_stops_at_first_health_check_below_threshold(hh_reference_orbits):
+    S = O.henon_heiles()
+    c, r = hh_reference_orbits["chaotic"], hh_reference_orbits["regular"]
+    ics = np.concatenate([_hh_ic(c["y"], c["py"], c["E"]), _hh_ic(r["y"], r["py"], r["E"])], axis=1)
+    kw = dict(n_dev=2, sample_every=100, sali_threshold=1e-8)
+    e = O.Ensemble(S, O.params(0.01, 1, **kw), ics, seed=4)
+    e.integrate(O.params(0.01, 100000, early_exit=True, **kw))
+    assert list(e.status) == [O.EARLY_CHAOTIC, O.OK]
+    m = int(e.n_exec[0])
+    assert m % 100 == 0 and 0 < m < 100000 and e.n_exec[1] == 100000
+    sali, _, lab = e.indicators(1e-8)
+    assert sali[0] < 1e-8 and list(lab) == [1, 0]
+    # the same orbit without early exit is above the threshold one check earlier
+    f = O.Ensemble(S, O.params(0.01, 1, **kw), ics[:, :1], seed=4)
+    f.integrate(O.params(0.01, m - 100, **kw))
+    assert f.indicators(1e-8)[0][0] >= 1e-8
+    f.integrate(O.params(0.01, 100, step0=m - 100, **kw))
+    np.testing.assert_array_equal(f.x[:, 0], e.x[:, 0])
+
+
+def test_per_orbit_end_steps():
+    S = O.henon_heiles()
+    y0, y1, p0, p1 = hh_section_box(1 / 8)
+    ics, st = O.grid_ics(1 / 8, y0, y1, 3, p0, p1, 3)
+    t_end = np.array([0, 150, 300, 450, 600, 750, 900, 1050, 1200], dtype=np.int64)
+    kw = dict(n_dev=2, ld_p=0.5)
+    e = O.Ensemble(S, O.params(0.01, 1, **kw), ics, st, seed=2)
+    for s0 in (0, 500):
+        e.integrate(O.params(0.01, 500, step0=s0, **kw), t_end=t_end)
+    ok = st == 0
+    np.testing.assert_array_equal(e.n_exec[ok], np.minimum(t_end, 1000)[ok])
+    for o in np.where(ok)[0]:
+        f = O.Ensemble(S, O.params(0.01, 1, **kw), ics[:, o:o + 1], seed=2,
+                       w_in=O.seed_vectors(2, ics.shape[1], 2, 4)[:, o:o + 1])
+        f.integrate(O.params(0.01, int(min(t_end[o], 1000)), **kw))
+        np.testing.assert_array_equal(f.x[:, 0], e.x[:, o])
+
+
+def test_quartic_shell_ics():
+    S = O.system(O.QUARTIC3, 3, eps=0.1)
+    rng = np.random.default_rng(12)
+    dirs = rng.standard_normal((6, 50))
+    E = rng.uniform(1.0, 10.0, 50)
+    ics = O.shell_ics(S, dirs, E)
+    for o in range(50):
+        assert abs(O.energy(S, ics[:, o]) - E[o]) < 1e-12 * E[o]
+        u = dirs[:, o] / np.linalg.norm(dirs[:, o])
+        np.testing.assert_allclose(ics[:, o] / np.linalg.norm(ics[:, o]), u, atol=1e-14)
