@@ -220,6 +220,24 @@ chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_
                                    int32_t chunk_steps, void* work, size_t work_bytes,
                                    void* stream);
 
+/* The run of chs_integrate_compacted (same results), for callers that cannot
+ * provide a scratch buffer: callers whose device memory belongs to another
+ * allocator (a framework's caching allocator, a fixed arena sized at start-up)
+ * that does not hand out extra buffers, or whose rules forbid device
+ * allocation while the application runs.  The paper has no counterpart; this
+ * is an interface convenience.  The orbit lists live in a fixed device array
+ * inside the library (8 MiB + 256 B, held by every GPU that loads the library
+ * until the process exits), so the call allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine, and no graph.  At most 1,048,576
+ * orbits (the 1024 x 1024 grid); larger ensembles return CHS_E_SIZE.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call shares the one array per device: calls that overlap on the GPU
+ * (different streams, or different handles on the same device) race; the
+ * counters are cleared by each call, the lists are overwritten. */
+chs_status chs_integrate_compacted_static(chs_system s, const chs_params* p, const chs_ensemble* e,
+                                          int32_t chunk_steps, void* stream);
+
 /* Indicators of the current ensemble state (Sec. Functionalities):
  *   sali_out [n]        SALI = min(|w1 + w2|, |w1 - w2|) of the first two unit
  *                       vectors (refs Skokos2001/03/04); needs k >= 2.

@@ -25,7 +25,8 @@ VEC_FP64, VEC_FP32 = 0, 1
 
 EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_section_grid_ics",
            "chs_fput_mode_ics", "chs_shell_ics", "chs_ensemble_init", "chs_integrate_batch",
-           "chs_compact_work_size", "chs_integrate_compacted", "chs_indicators",
+           "chs_compact_work_size", "chs_integrate_compacted", "chs_integrate_compacted_static",
+           "chs_indicators",
            "chs_lyapunov_spectrum", "chs_last_error", "chs_version")
 
 
@@ -72,6 +73,8 @@ def load(path: str | None = None):
         "chs_compact_work_size": (C.c_size_t, [I64]),
         "chs_integrate_compacted": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), I32, P,
                                               C.c_size_t, P]),
+        "chs_integrate_compacted_static": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble),
+                                                     I32, P]),
         "chs_ensemble_init": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), P, P, P, P]),
         "chs_integrate_batch": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), P]),
         "chs_indicators": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), I32, I32, P, P,
@@ -158,6 +161,13 @@ def chs_compact_work_size(n: int) -> int:
 def chs_integrate_compacted(h, prm: Params, ens: Ensemble, chunk_steps: int, work, stream=None):
     _check(load().chs_integrate_compacted(h, C.byref(prm), C.byref(ens), chunk_steps, _ptr(work),
                                           work.numel() * work.element_size(), _stream(stream)))
+
+
+def chs_integrate_compacted_static(h, prm: Params, ens: Ensemble, chunk_steps: int, stream=None):
+    """chs_integrate_compacted without a work buffer: for callers that cannot allocate
+    device scratch (see include/chs.h); at most 1,048,576 orbits."""
+    _check(load().chs_integrate_compacted_static(h, C.byref(prm), C.byref(ens), chunk_steps,
+                                                 _stream(stream)))
 
 
 def chs_ensemble_init(h, prm: Params, ens: Ensemble, ics, ic_status=None, w_in=None, stream=None):

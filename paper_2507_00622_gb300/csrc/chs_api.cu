@@ -138,6 +138,25 @@ chs_status check_handle(chs_system s)
 
 }  // namespace
 
+// Validation and plumbing shared with the entry point in chs_static.cu.
+namespace chs {
+chs_status api_validate_run(chs_system s, const chs_params* p, const chs_ensemble* e, int* device)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (!small_model(s->sp.model))
+        return fail(CHS_E_UNSUPPORTED, "integration is implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
+    if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ensemble(e, p)) != CHS_OK) return r;
+    *device = s->device;
+    return CHS_OK;
+}
+chs_status api_fail(chs_status code, const char* msg) { return fail(code, "%s", msg); }
+StepArgs api_step_args(const chs_params* p) { return step_args(p); }
+EnsPtrs api_ens_ptrs(const chs_ensemble* e) { return ens_ptrs(e); }
+SysPar api_syspar(chs_system s) { return s->sp; }
+}  // namespace chs
+
 extern "C" {
 
 const char* chs_version(void) { return "chs 0.1.0 (sm_103a)"; }
