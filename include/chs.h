@@ -189,12 +189,12 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
  *   Sec. Statement of need), M_p' = sum_i |f_i(x)|^p (the LD, Sec. Statement
  *   of need),
  * the fixed-step integrator of Sec. Functionalities (RK4 in place of DOP8).
- * After each step: vectors are renormalised when p->renorm is set ("DOP 8 ODE
- * solver with fixed step size that includes the normalization of the
- * deviation vectors"); in FP32 mode the frame Q is advanced by the exact
+ * After each step: vectors are renormalised when p->renorm is set (the
+ * fixed-step solver variant with vector normalisation, Sec. Functionalities);
+ * in FP32 mode the frame Q is advanced by the exact
  * one-step RK4 propagator of the variational equations and re-orthonormalised
- * (Phi Q = Q' S, R <- S R with unit columns), the orbit and LD staying FP64; an orbit with sum_i q_i^2 > escape_r2 freezes as
- * ESCAPED.  At absolute steps divisible by sample_every: non-finite -> frozen
+ * (Phi Q = Q' S, R <- S R with unit columns), the orbit and LD staying FP64;
+ * an orbit with sum_i q_i^2 > escape_r2 freezes as ESCAPED.  At absolute steps divisible by sample_every: non-finite -> frozen
  * NONFINITE; dh_max <- max(dh_max, |H - h0|); |H - h0| > dh_limit -> frozen
  * ENERGY_DRIFT; with early_exit, SALI < sali_threshold -> frozen EARLY_CHAOTIC.
  * An orbit with t_end stops after t_end[o] total steps.  Splitting a run into

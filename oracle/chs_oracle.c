@@ -27,9 +27,9 @@
  *                                  system (x, w_1..w_k, L): deviation vectors
  *                                  obey the variational equations (Sec.
  *                                  Statement of need), are renormalised after
- *                                  every step (the "normalization of the
- *                                  deviation vectors" item of Sec.
- *                                  Functionalities) and L is the Lagrangian
+ *                                  every step (the vector-normalising solver
+ *                                  variant listed in Sec. Functionalities)
+ *                                  and L is the Lagrangian
  *                                  descriptor M_p = int sum_i |dx_i/dt|^p dt
  *                                  (Sec. Statement of need, refs mancho2013,
  *                                  lopesino2017).  A 4th-order Yoshida
