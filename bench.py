@@ -36,6 +36,26 @@ SM_COUNT = 152
 FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA lanes per SM per clock (measured 1.20 TFLOP/s at ~1.99 GHz)
 
 
+# DRAM traffic of one k_integrate<HenonHeiles,4,LD> launch over the 1024 x 1024 grid
+# (dram__bytes_read.sum + dram__bytes_write.sum from one ncu capture; a launch reads
+# and writes the ensemble state once whatever its step count), valid while the
+# kernel sources hash to the recorded value.
+TRAFFIC_SOURCES = ("k_small.cu", "rk4_common.cuh", "fastmath.cuh", "systems.cuh", "chs_internal.cuh")
+TRAFFIC_RECORD = {"sha256_16": "7155e81161345a09", "bytes_per_launch": 147.314176e6 + 80.468992e6,
+                  "n_side": 1024}
+
+
+def recorded_traffic(n_side: int, vec_fp32: bool):
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2507_00622_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if vec_fp32 or n_side != TRAFFIC_RECORD["n_side"] or h.hexdigest()[:16] != TRAFFIC_RECORD["sha256_16"]:
+        return None
+    return TRAFFIC_RECORD["bytes_per_launch"]
+
+
 def grid_box(E: float):
     """Energy-allowed (y, p_y) box of the x = 0 section at E = 1/6."""
     return -0.5, 1.0, -float(np.sqrt(2 * E)), float(np.sqrt(2 * E))
@@ -341,7 +361,7 @@ def run_gpu(args):
                              (h2d / 1e6),
                        "parallelism": f"orbit-range shards x{world}, no data-path collective"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": recorded_traffic(ny, vec_fp32),
                          "kernel": "k_integrate<HenonHeiles,4,LD>",
                          "flops_per_orbit_step": {"fp64": f64, "fp32": f32},
                          "peak_basis": f"152 SMs x 2 DFMA/clk x 2 flop x {peak_mhz:.0f} MHz",
@@ -360,6 +380,80 @@ def run_gpu(args):
     return 0
 
 
+def fput_flops_per_orbit_step(N: int, qr_every: int = 10) -> int:
+    """Algorithmic FP64 flops of one step of the FPUT Lyapunov run (FMA = 2):
+    propagation of the 2N vectors by the banded one-step RK4 propagator, 36 N^2
+    FMA; its rows, ~60 N; the orbit's RK4, ~50 N; modified Gram-Schmidt of the
+    2N x 2N matrix, (2N)^2 (2N + 1) FMA every qr_every steps."""
+    d = 2 * N
+    return 72 * N * N + 60 * N + 50 * N + (2 * d * d * (d + 1)) // qr_every
+
+
+def run_fput(args):
+    """FPUT-beta Lyapunov spectra (k = 1, beta = 1, h = 0.05, QR every 10 steps):
+    4096 normal-mode orbits at energy density 0.1 per chain length; one bench
+    step integrates every chain length for --chunk steps."""
+    import torch
+
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+
+    cuda_build.build()
+    chs.load()
+    Ns = [int(v) for v in args.fput_n.split(",")]
+    n = args.fput_orbits
+    runs = []
+    for N in Ns:
+        S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
+        Q, P = normal_mode_draws(1000 + N, N, n)
+        ics = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+        chs.chs_fput_mode_ics(S.h, n, torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(),
+                              torch.full((n,), 0.1 * N, dtype=torch.float64, device="cuda"), ics)
+        lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        runs.append((N, S, ics, lam, st))
+    prm = chs.params(0.05, args.chunk, qr_every=10, sample_every=100)
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        for i, (N, S, ics, lam, st) in enumerate(runs):
+            if evs is not None:
+                evs[i][0].record(stream)
+            chs.chs_lyapunov_spectrum(S.h, prm, n, ics, None, lam, st)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in runs] for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    per_n = {}
+    for j, (N, *_rest) in enumerate(runs):
+        ms = float(np.mean([evs[i][j][0].elapsed_time(evs[i][j][1]) for i in range(args.steps)]))
+        os_ = n * args.chunk / (ms / 1e3)
+        tf = fput_flops_per_orbit_step(N) * os_ / 1e12
+        per_n[str(N)] = {"orbit_steps_per_s": os_, "kernel_ms": ms, "fp64_tflops": tf,
+                         "frac_of_fp64_peak": tf / fp64_peak_tflops(2070.0)}
+    value = len(runs) * n * args.chunk * args.steps / (total_ms / 1e3)
+    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": "fput_beta_lyapunov_qr10_h0.05", "N": Ns,
+                                 "orbits_per_N": n, "rk4_steps_per_bench_step": args.chunk},
+                      "per_N": per_n}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -373,7 +467,12 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--workload", choices=["grid", "fput"], default="grid")
+    ap.add_argument("--fput-n", default="4,8,16,32,64")
+    ap.add_argument("--fput-orbits", type=int, default=4096)
     args = ap.parse_args()
+    if args.workload == "fput":
+        return run_fput(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
