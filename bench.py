@@ -454,6 +454,55 @@ def run_fput(args):
     return 0
 
 
+def run_classify(args):
+    """Time to classify a Henon-Heiles section grid (E = 1/8, final t = steps * 0.01)
+    by the plain form (FP64 vectors, every orbit to the end) and by the fast form
+    (FP32 vector frame, early exit, compacted CUDA-graph chunks, and the trained
+    surrogate when its weights are present), with the label agreement; a 2 %
+    random sample of the orbits the surrogate stopped is judged against the plain
+    labels as well."""
+    import torch
+
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+    from paper_2507_00622_gb300 import classify as CL
+    from paper_2507_00622_gb300 import surrogate as SG
+
+    cuda_build.build()
+    chs.load()
+    g = CL.GridSpec(E=1.0 / 8.0, n_side=args.n_side, n_steps=args.final_steps)
+    plain = CL.run_plain(g)
+    fast = CL.run_fast(g)
+    valid = plain.status != chs.ORBIT_FORBIDDEN
+    out = {"metric": "time-to-classified-grid vs plain at >=99.5% agreement", "unit": "s",
+           "config": {"workload": f"henon_heiles_E1/8_grid{args.n_side}x{args.n_side}_k2_ld",
+                      "final_t": args.final_steps * 0.01, "valid_cells": int(valid.sum())},
+           "plain": {"seconds": plain.seconds, "orbit_steps": plain.orbit_steps, "dtype": "f64"},
+           "fast": {"seconds": fast.seconds, "orbit_steps": fast.orbit_steps, "dtype": "f64 orbit + f32 frame",
+                    "speedup": plain.seconds / fast.seconds,
+                    "agreement": CL.agreement(plain, fast, plain.status)}}
+    if os.path.exists(SG.WEIGHTS):
+        import json as _json
+        with np.load(SG.WEIGHTS) as z:
+            meta = _json.loads(str(z["meta"]))
+        sur = SG.Surrogate.load()
+        conf = float(args.confidence or meta.get("confidence", 0.999))
+        fs = CL.run_fast(g, surrogate=sur, confidence=conf)
+        stopped = np.where((fs.n_exec == SG.DECIDE_STEP) & ((fs.status == chs.ORBIT_PREDICTED_REGULAR) |
+                                                            (fs.status == chs.ORBIT_EARLY_CHAOTIC)))[0]
+        rng = np.random.default_rng(0)
+        judge = rng.choice(stopped, max(1, int(0.02 * stopped.size)), replace=False) if stopped.size else stopped
+        out["fast_surrogate"] = {
+            "seconds": fs.seconds, "orbit_steps": fs.orbit_steps, "confidence": conf,
+            "speedup": plain.seconds / fs.seconds, "agreement": CL.agreement(plain, fs, plain.status),
+            "stopped_by_surrogate": int(stopped.size),
+            "judge_sample": int(judge.size),
+            "judge_agreement": float(np.mean(fs.label[judge] == plain.label[judge])) if judge.size else None,
+            "training": meta}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -467,12 +516,16 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
-    ap.add_argument("--workload", choices=["grid", "fput"], default="grid")
+    ap.add_argument("--workload", choices=["grid", "fput", "classify"], default="grid")
+    ap.add_argument("--final-steps", type=int, default=1_000_000)
+    ap.add_argument("--confidence", type=float, default=None)
     ap.add_argument("--fput-n", default="4,8,16,32,64")
     ap.add_argument("--fput-orbits", type=int, default=4096)
     args = ap.parse_args()
     if args.workload == "fput":
         return run_fput(args)
+    if args.workload == "classify":
+        return run_classify(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

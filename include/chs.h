@@ -70,8 +70,11 @@ enum {
     CHS_ORBIT_ESCAPED = 2,      /* sum_i q_i^2 exceeded escape_r2; frozen */
     CHS_ORBIT_NONFINITE = 3,    /* a non-finite value at a health check; frozen */
     CHS_ORBIT_ENERGY_DRIFT = 4, /* |H - H0| exceeded dh_limit at a health check; frozen */
-    CHS_ORBIT_EARLY_CHAOTIC = 5 /* SALI fell below sali_threshold at a health check with
-                                   early_exit set; frozen, labelled chaotic */
+    CHS_ORBIT_EARLY_CHAOTIC = 5, /* SALI fell below sali_threshold at a health check with
+                                    early_exit set, or the surrogate predicted "chaotic" with
+                                    confidence; frozen, labelled chaotic */
+    CHS_ORBIT_PREDICTED_REGULAR = 6 /* the surrogate predicted "regular" with confidence;
+                                       frozen, labelled regular */
 };
 
 /* Deviation-vector storage precision. */
@@ -247,7 +250,8 @@ chs_status chs_integrate_compacted_static(chs_system s, const chs_params* p, con
  *                       mode: of the stored triangle R, and SALI as
  *                       R_11 sqrt(2 / (1 + |R_01|))).
  *   label_out [n]       1 chaotic (SALI < sali_threshold, or EARLY_CHAOTIC),
- *                       0 regular, 2 ESCAPED, -1 any other non-OK status.
+ *                       0 regular (or PREDICTED_REGULAR), 2 ESCAPED, -1 any
+ *                       other non-OK status.
  *   ld_ind_out [2][n]   when grid_ny * grid_npy == n and the ensemble has an
  *                       LD: D_L and S_L from the four grid neighbours (LD-based
  *                       indicators and neighbouring trajectories):
@@ -273,6 +277,59 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
 chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n,
                                  const double* ics, const int32_t* ic_status,
                                  double* lambda_out, int32_t* status_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Early-stop surrogate (a learned classifier of the final label; the method's
+ * indicators stay the judge).  A 12 -> 128 -> 128 -> 128 -> 2 ReLU perceptron
+ * with BF16 weights and activations and FP32 accumulation.  Features of an
+ * orbit at the decision time t, from S <= 10 SALI samples taken at
+ * t_i = (i + 1) t / S and the LD M_p(t):
+ *   f_i = log10(max(SALI(t_i), 1e-20)) / 8 (i < 10; missing samples count as
+ *   1e-20), f_10 = M_p(t) / t - 1, f_11 = (E_o - 0.133) / 0.033 (E_o the
+ *   orbit's energy).
+ * Outputs: y_0 = logit of "chaotic at the final time", y_1 = final
+ * log10(SALI) / 8.  Parameters: one flat BF16 array (row-major out x in)
+ * W1[128][12] b1[128] W2[128][128] b2[128] W3[128][128] b3[128] W4[2][128]
+ * b4[2], chs_mlp_param_count() values.  Training keeps an FP32 master copy.
+ * ------------------------------------------------------------------------ */
+
+/* Number of parameters (34,946). */
+size_t chs_mlp_param_count(void);
+
+/* Features X [12][n] (FP32) from sali_series [S][n], ld [n], t and the
+ * orbits' energies E [n]. */
+chs_status chs_mlp_features(const double* sali_series, int32_t n_samples, const double* ld,
+                            double t_decide, const double* E, int64_t n, float* X, void* stream);
+
+/* Forward pass: Y [2][n] (FP32); act [3][128][n] (BF16, nullable) keeps the
+ * hidden activations for chs_mlp_backward. */
+chs_status chs_mlp_forward(const void* params_bf16, const float* X, int64_t n, float* Y, void* act,
+                           void* stream);
+
+/* Loss L = mean over n of BCE(sigmoid(y0), label) + w_reg (y1 - target)^2, and
+ * dY [2][n] = dL/dY; loss_out (one float) receives L. */
+chs_status chs_mlp_loss_grad(const float* Y, const float* label, const float* target, int64_t n,
+                             float w_reg, float* dY, float* loss_out, void* stream);
+
+/* Backward pass: parameter gradients grad_out [P] (FP32, overwritten) of the
+ * loss whose output gradient is dY, from X and the activations of the forward
+ * pass; delta_work is caller scratch of 3*128*n floats. */
+chs_status chs_mlp_backward(const void* params_bf16, const float* X, const void* act, const float* dY,
+                            int64_t n, float* delta_work, float* grad_out, void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on the FP32 master weights with
+ * moments m, v (all [P]); writes the BF16 copy params_bf16_out. */
+chs_status chs_mlp_adam(float* master, float* m, float* v, const float* grad, float lr, float beta1,
+                        float beta2, float eps, int32_t step, void* params_bf16_out, void* stream);
+
+/* Decision at time t for every orbit whose status is OK: features from
+ * sali_series [S][n], ld [n] and E [n], forward pass, then status <-
+ * EARLY_CHAOTIC when sigmoid(y0) >= confidence, PREDICTED_REGULAR when
+ * sigmoid(y0) <= 1 - confidence; other orbits are untouched.  prob_out [n]
+ * (nullable) receives sigmoid(y0). */
+chs_status chs_surrogate_decide(const void* params_bf16, const double* sali_series, int32_t n_samples,
+                                const double* ld, double t_decide, const double* E, double confidence,
+                                int64_t n, int32_t* status_inout, float* prob_out, void* stream);
 
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char* chs_last_error(void);

@@ -20,14 +20,16 @@ LIB_PATH = os.path.join(_HERE, "libchs.so")
 CHS_OK, CHS_E_INVALID, CHS_E_UNSUPPORTED, CHS_E_CUDA, CHS_E_NOMEM, CHS_E_SIZE = range(6)
 HENON_HEILES, FPUT, QUARTIC3, HARMONIC, INVERTED = 1, 2, 3, 100, 101
 (ORBIT_OK, ORBIT_FORBIDDEN, ORBIT_ESCAPED, ORBIT_NONFINITE, ORBIT_ENERGY_DRIFT,
- ORBIT_EARLY_CHAOTIC) = range(6)
+ ORBIT_EARLY_CHAOTIC, ORBIT_PREDICTED_REGULAR) = range(7)
 VEC_FP64, VEC_FP32 = 0, 1
 
 EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_section_grid_ics",
            "chs_fput_mode_ics", "chs_shell_ics", "chs_ensemble_init", "chs_integrate_batch",
            "chs_compact_work_size", "chs_integrate_compacted", "chs_integrate_compacted_static",
            "chs_indicators",
-           "chs_lyapunov_spectrum", "chs_last_error", "chs_version")
+           "chs_lyapunov_spectrum", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
+           "chs_mlp_loss_grad", "chs_mlp_backward", "chs_mlp_adam", "chs_surrogate_decide",
+           "chs_last_error", "chs_version")
 
 
 class ChsError(RuntimeError):
@@ -80,6 +82,13 @@ def load(path: str | None = None):
         "chs_indicators": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), I32, I32, P, P,
                                      P, P, P]),
         "chs_lyapunov_spectrum": (C.c_int, [P, C.POINTER(Params), I64, P, P, P, P, P]),
+        "chs_mlp_param_count": (C.c_size_t, []),
+        "chs_mlp_features": (C.c_int, [P, I32, P, D, P, I64, P, P]),
+        "chs_mlp_forward": (C.c_int, [P, P, I64, P, P, P]),
+        "chs_mlp_loss_grad": (C.c_int, [P, P, P, I64, C.c_float, P, P, P]),
+        "chs_mlp_backward": (C.c_int, [P, P, P, P, I64, P, P, P]),
+        "chs_mlp_adam": (C.c_int, [P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, P, P]),
+        "chs_surrogate_decide": (C.c_int, [P, P, I32, P, D, P, D, I64, P, P, P]),
         "chs_last_error": (C.c_char_p, []),
         "chs_version": (C.c_char_p, []),
     }
@@ -188,6 +197,40 @@ def chs_indicators(h, prm: Params, ens: Ensemble, grid_ny=0, grid_npy=0, sali=No
 def chs_lyapunov_spectrum(h, prm: Params, n, ics, ic_status, lam, status, stream=None):
     _check(load().chs_lyapunov_spectrum(h, C.byref(prm), n, _ptr(ics), _ptr(ic_status), _ptr(lam),
                                         _ptr(status), _stream(stream)))
+
+
+def chs_mlp_param_count() -> int:
+    return int(load().chs_mlp_param_count())
+
+
+def chs_mlp_features(series, n_samples, ld, t_decide, E, n, X, stream=None):
+    _check(load().chs_mlp_features(_ptr(series), n_samples, _ptr(ld), t_decide, _ptr(E), n, _ptr(X),
+                                   _stream(stream)))
+
+
+def chs_mlp_forward(params, X, n, Y, act=None, stream=None):
+    _check(load().chs_mlp_forward(_ptr(params), _ptr(X), n, _ptr(Y), _ptr(act), _stream(stream)))
+
+
+def chs_mlp_loss_grad(Y, label, target, n, w_reg, dY, loss, stream=None):
+    _check(load().chs_mlp_loss_grad(_ptr(Y), _ptr(label), _ptr(target), n, w_reg, _ptr(dY),
+                                    _ptr(loss), _stream(stream)))
+
+
+def chs_mlp_backward(params, X, act, dY, n, delta_work, grad, stream=None):
+    _check(load().chs_mlp_backward(_ptr(params), _ptr(X), _ptr(act), _ptr(dY), n, _ptr(delta_work),
+                                   _ptr(grad), _stream(stream)))
+
+
+def chs_mlp_adam(master, m, v, grad, lr, beta1, beta2, eps, step, params_out, stream=None):
+    _check(load().chs_mlp_adam(_ptr(master), _ptr(m), _ptr(v), _ptr(grad), lr, beta1, beta2, eps,
+                               step, _ptr(params_out), _stream(stream)))
+
+
+def chs_surrogate_decide(params, series, n_samples, ld, t_decide, E, confidence, n, status, prob=None,
+                         stream=None):
+    _check(load().chs_surrogate_decide(_ptr(params), _ptr(series), n_samples, _ptr(ld), t_decide, _ptr(E),
+                                       confidence, n, _ptr(status), _ptr(prob), _stream(stream)))
 
 
 def chs_last_error() -> str:

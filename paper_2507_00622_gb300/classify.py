@@ -1,0 +1,108 @@
+"""Classifying a Henon-Heiles section grid as regular or chaotic (labels from SALI
+at a final time), in two forms that call only the C ABI:
+
+- plain: FP64 deviation vectors renormalised every step, every orbit integrated to
+  the final step, labels from the final SALI;
+- fast: FP32 vector frame (FP64 orbit), early exit once SALI < threshold, the run
+  compacted over live orbits every chunk (CUDA graph), and optionally a surrogate
+  that, at a decision time, stops the orbits whose final label it predicts with
+  confidence.
+
+Both forms use the same grid, seeds and threshold, so their labels can be
+compared orbit by orbit.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import chs
+
+
+@dataclass
+class GridSpec:
+    E: float = 1.0 / 8.0
+    n_side: int = 1024
+    box: tuple[float, float, float, float] | None = None  # (y0, y1, py0, py1)
+    dt: float = 0.01
+    n_steps: int = 1_000_000          # final time 1e4
+    k: int = 2
+    seed: int = 1
+    sali_threshold: float = 1e-8
+
+    def bounds(self):
+        if self.box is not None:
+            return self.box
+        from .inputs import hh_section_box
+        return hh_section_box(self.E)
+
+
+@dataclass
+class RunResult:
+    label: np.ndarray
+    status: np.ndarray
+    n_exec: np.ndarray
+    seconds: float
+    orbit_steps: int
+    extra: dict = field(default_factory=dict)
+
+
+def _grid(S, g: GridSpec):
+    y0, y1, p0, p1 = g.bounds()
+    n = g.n_side * g.n_side
+    ics = torch.empty((4, n), dtype=torch.float64, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    chs.chs_section_grid_ics(S.h, g.E, y0, y1, g.n_side, p0, p1, g.n_side, ics, st)
+    return ics, st
+
+
+def run_plain(g: GridSpec, chunk: int = 100_000) -> RunResult:
+    """FP64 vectors, every orbit to the final step, labels from the final SALI."""
+    S = chs.System(chs.HENON_HEILES, 2)
+    ics, st = _grid(S, g)
+    n = ics.shape[1]
+    kw = dict(n_dev=g.k, ld_p=0.5, escape_r2=4.0, seed=g.seed, sali_threshold=g.sali_threshold)
+    ens = chs.DeviceEnsemble.empty(n, 4, g.k)
+    abi = ens.abi()
+    chs.chs_ensemble_init(S.h, chs.params(g.dt, 1, **kw), abi, ics, st)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step = 0
+    while step < g.n_steps:
+        c = min(chunk, g.n_steps - step)
+        chs.chs_integrate_batch(S.h, chs.params(g.dt, c, step0=step, **kw), abi)
+        step += c
+    label = torch.empty(n, dtype=torch.int8, device="cuda")
+    chs.chs_indicators(S.h, chs.params(g.dt, 0, **kw), abi, label=label,
+                       sali=torch.empty(n, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    n_exec = ens.n_exec.cpu().numpy()
+    return RunResult(label.cpu().numpy(), ens.status.cpu().numpy(), n_exec, sec, int(n_exec.sum()))
+
+
+def run_fast(g: GridSpec, chunk: int = 2000, surrogate=None, confidence: float = 0.999) -> RunResult:
+    """FP32 frame, early exit, compacted graph chunks; with a surrogate, the orbits
+    still running at the decision time (t = 500) whose final label it predicts
+    with probability >= confidence stop there and keep that label."""
+    from . import surrogate as sg
+    S = chs.System(chs.HENON_HEILES, 2)
+    ics, st = _grid(S, g)
+    n = ics.shape[1]
+    E = torch.full((n,), g.E, dtype=torch.float64, device="cuda")
+    run = sg.run_sampled(ics, st, k=g.k, seed=g.seed, final_step=g.n_steps, chunk=chunk,
+                         surrogate=surrogate, E=E, confidence=confidence)
+    status = run["status"].cpu().numpy()
+    n_exec = run["n_exec"].cpu().numpy()
+    extra = {"surrogate_stopped": int(np.sum(status == chs.ORBIT_PREDICTED_REGULAR))
+             + int(np.sum((status == chs.ORBIT_EARLY_CHAOTIC) & (n_exec == sg.DECIDE_STEP)))}
+    return RunResult(run["label"].cpu().numpy(), status, n_exec, run["seconds"], int(n_exec.sum()), extra)
+
+
+def agreement(a: RunResult, b: RunResult, status_ref: np.ndarray) -> float:
+    """Label agreement over the valid (non-FORBIDDEN) cells."""
+    v = status_ref != chs.ORBIT_FORBIDDEN
+    return float((a.label[v] == b.label[v]).mean())

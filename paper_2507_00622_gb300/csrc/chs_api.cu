@@ -440,4 +440,71 @@ chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n, c
     return fail(CHS_E_UNSUPPORTED, "Lyapunov spectrum not implemented for this model");
 }
 
+size_t chs_mlp_param_count(void) { return chs::mlp_param_count(); }
+
+chs_status chs_mlp_features(const double* sali_series, int32_t n_samples, const double* ld,
+                            double t_decide, const double* E, int64_t n, float* X, void* stream)
+{
+    if (n < 0 || n_samples < 0 || n_samples > 10) return fail(CHS_E_INVALID, "need n >= 0 and 0 <= n_samples <= 10");
+    if (!(t_decide > 0.0)) return fail(CHS_E_INVALID, "t_decide must be > 0");
+    if (n == 0) return ok();
+    if ((n_samples > 0 && !sali_series) || !ld || !E || !X) return fail(CHS_E_INVALID, "pointers must be non-NULL");
+    return cuda_status(chs::launch_mlp_features(sali_series, n_samples, ld, t_decide, E, n, X,
+                                                as_stream(stream)), "features launch");
+}
+
+chs_status chs_mlp_forward(const void* params_bf16, const float* X, int64_t n, float* Y, void* act,
+                           void* stream)
+{
+    if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
+    if (n == 0) return ok();
+    if (!params_bf16 || !X || !Y) return fail(CHS_E_INVALID, "pointers must be non-NULL");
+    return cuda_status(chs::launch_mlp_forward(params_bf16, X, n, Y, act, as_stream(stream)),
+                       "forward launch");
+}
+
+chs_status chs_mlp_loss_grad(const float* Y, const float* label, const float* target, int64_t n,
+                             float w_reg, float* dY, float* loss_out, void* stream)
+{
+    if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
+    if (n == 0) return ok();
+    if (!Y || !label || !target || !dY || !loss_out) return fail(CHS_E_INVALID, "pointers must be non-NULL");
+    return cuda_status(chs::launch_mlp_loss_grad(Y, label, target, n, w_reg, dY, loss_out,
+                                                 as_stream(stream)), "loss launch");
+}
+
+chs_status chs_mlp_backward(const void* params_bf16, const float* X, const void* act, const float* dY,
+                            int64_t n, float* delta_work, float* grad_out, void* stream)
+{
+    if (n < 1) return fail(CHS_E_INVALID, "n must be >= 1");
+    if (!params_bf16 || !X || !act || !dY || !delta_work || !grad_out)
+        return fail(CHS_E_INVALID, "pointers must be non-NULL");
+    return cuda_status(chs::launch_mlp_backward(params_bf16, X, act, dY, n, delta_work, grad_out,
+                                                as_stream(stream)), "backward launch");
+}
+
+chs_status chs_mlp_adam(float* master, float* m, float* v, const float* grad, float lr, float beta1,
+                        float beta2, float eps, int32_t step, void* params_bf16_out, void* stream)
+{
+    if (!master || !m || !v || !grad || !params_bf16_out) return fail(CHS_E_INVALID, "pointers must be non-NULL");
+    if (step < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f))
+        return fail(CHS_E_INVALID, "need step >= 1, lr > 0 and betas in [0, 1)");
+    return cuda_status(chs::launch_mlp_adam(master, m, v, grad, lr, beta1, beta2, eps, step,
+                                            params_bf16_out, as_stream(stream)), "adam launch");
+}
+
+chs_status chs_surrogate_decide(const void* params_bf16, const double* sali_series, int32_t n_samples,
+                                const double* ld, double t_decide, const double* E, double confidence,
+                                int64_t n, int32_t* status_inout, float* prob_out, void* stream)
+{
+    if (n < 0 || n_samples < 1 || n_samples > 10) return fail(CHS_E_INVALID, "need n >= 0 and 1 <= n_samples <= 10");
+    if (!(t_decide > 0.0)) return fail(CHS_E_INVALID, "t_decide must be > 0");
+    if (!(confidence > 0.5 && confidence <= 1.0)) return fail(CHS_E_INVALID, "confidence must be in (0.5, 1]");
+    if (n == 0) return ok();
+    if (!params_bf16 || !sali_series || !ld || !E || !status_inout) return fail(CHS_E_INVALID, "pointers must be non-NULL");
+    return cuda_status(chs::launch_mlp_decide(params_bf16, sali_series, n_samples, ld, t_decide, E, n,
+                                              confidence, status_inout, prob_out, as_stream(stream)),
+                       "decide launch");
+}
+
 }  // extern "C"

@@ -89,6 +89,22 @@ cudaError_t launch_fput_lyap(const SysPar& sp, const StepArgs& a, int64_t n, con
                              const int32_t* ic_status, double* lambda, int32_t* status,
                              cudaStream_t st);
 
+// Surrogate perceptron (k_mlp.cu).
+size_t mlp_param_count();
+cudaError_t launch_mlp_features(const double* series, int S, const double* ld, double t, const double* E,
+                                int64_t n, float* X, cudaStream_t st);
+cudaError_t launch_mlp_forward(const void* P, const float* X, int64_t n, float* Y, void* act,
+                               cudaStream_t st);
+cudaError_t launch_mlp_decide(const void* P, const double* series, int S, const double* ld, double t,
+                              const double* E, int64_t n, double conf, int32_t* status, float* prob,
+                              cudaStream_t st);
+cudaError_t launch_mlp_loss_grad(const float* Y, const float* label, const float* target, int64_t n,
+                                 float w_reg, float* dY, float* loss, cudaStream_t st);
+cudaError_t launch_mlp_backward(const void* P, const float* X, const void* act, const float* dY,
+                                int64_t n, float* delta, float* G, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* W, float* m, float* v, const float* g, float lr, float b1, float b2,
+                            float eps, int step, void* Wb, cudaStream_t st);
+
 // Which systems each kernel family supports.
 bool small_model(int model);
 bool fput_lyap_supported(int n_dof);

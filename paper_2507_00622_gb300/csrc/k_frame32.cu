@@ -298,6 +298,8 @@ k_indicators_f32(const int64_t n, const float* __restrict__ wg, const int32_t* _
             lb = (sv < thr) ? 1 : 0;
         else if (st == CHS_ORBIT_EARLY_CHAOTIC)
             lb = 1;
+        else if (st == CHS_ORBIT_PREDICTED_REGULAR)
+            lb = 0;
         else if (st == CHS_ORBIT_ESCAPED)
             lb = 2;
         else

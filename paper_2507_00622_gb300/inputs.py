@@ -40,3 +40,21 @@ def strided_sample(n: int, count: int) -> np.ndarray:
     """`count` orbit indices spread evenly over range(n)."""
     count = min(count, n)
     return np.unique(np.linspace(0, n - 1, count).round().astype(np.int64))
+
+
+MLP_SHAPES = [((128, 12), True), ((128,), False), ((128, 128), True), ((128,), False),
+              ((128, 128), True), ((128,), False), ((2, 128), True), ((2,), False)]
+
+
+def mlp_init(seed: int) -> np.ndarray:
+    """Initial perceptron parameters (flat, the layout of the surrogate): weights
+    uniform in +-sqrt(6 / fan_in), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for shape, is_w in MLP_SHAPES:
+        if is_w:
+            lim = np.sqrt(6.0 / shape[1])
+            parts.append(rng.uniform(-lim, lim, shape).ravel())
+        else:
+            parts.append(np.zeros(shape))
+    return np.concatenate(parts)
