@@ -374,6 +374,18 @@ def run_gpu(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(args.chunk, args.cpu_budget)
+        if world == 1 and args.classify_side > 0:
+            c = classify_result(args.classify_side, 1_000_000)
+            line["classify"] = {
+                "what": c["metric"], "config": c["config"], "plain_s": c["plain"]["seconds"],
+                "fast_s": c["fast"]["seconds"], "fast_speedup": c["fast"]["speedup"],
+                "fast_agreement": c["fast"]["agreement"]}
+            if "fast_surrogate" in c:
+                fs = c["fast_surrogate"]
+                line["classify"].update(surrogate_s=fs["seconds"], surrogate_speedup=fs["speedup"],
+                                        surrogate_agreement=fs["agreement"],
+                                        surrogate_judge_agreement=fs["judge_agreement"],
+                                        surrogate_confidence=fs["confidence"])
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -413,14 +425,25 @@ def run_fput(args):
         lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
         st = torch.empty(n, dtype=torch.int32, device="cuda")
         runs.append((N, S, ics, lam, st))
-    prm = chs.params(0.05, args.chunk, qr_every=10, sample_every=100)
+    qr = {}
+    for N in Ns:
+        if args.qr_every == "auto":
+            from paper_2507_00622_gb300 import autotune
+            qr[N] = autotune.tune_fput_qr(N)["qr_every"]
+        else:
+            qr[N] = int(args.qr_every)
+    prms = {N: chs.params(0.05, args.chunk, qr_every=qr[N], sample_every=100) for N in Ns}
     stream = torch.cuda.current_stream()
 
     def step(evs=None):
+        if args.fput_batch:
+            # every chain length in one CUDA graph with concurrent branches
+            chs.chs_lyapunov_batch([(S.h, prms[N], n, ics, None, lam, st) for N, S, ics, lam, st in runs])
+            return
         for i, (N, S, ics, lam, st) in enumerate(runs):
             if evs is not None:
                 evs[i][0].record(stream)
-            chs.chs_lyapunov_spectrum(S.h, prm, n, ics, None, lam, st)
+            chs.chs_lyapunov_spectrum(S.h, prms[N], n, ics, None, lam, st)
             if evs is not None:
                 evs[i][1].record(stream)
 
@@ -438,45 +461,46 @@ def run_fput(args):
     total_ms = t0.elapsed_time(t1)
     per_n = {}
     for j, (N, *_rest) in enumerate(runs):
+        if args.fput_batch:
+            per_n[str(N)] = {"qr_every": qr[N]}
+            continue
         ms = float(np.mean([evs[i][j][0].elapsed_time(evs[i][j][1]) for i in range(args.steps)]))
         os_ = n * args.chunk / (ms / 1e3)
-        tf = fput_flops_per_orbit_step(N) * os_ / 1e12
+        tf = fput_flops_per_orbit_step(N, qr[N]) * os_ / 1e12
         per_n[str(N)] = {"orbit_steps_per_s": os_, "kernel_ms": ms, "fp64_tflops": tf,
-                         "frac_of_fp64_peak": tf / fp64_peak_tflops(2070.0)}
+                         "frac_of_fp64_peak": tf / fp64_peak_tflops(2070.0), "qr_every": qr[N]}
     value = len(runs) * n * args.chunk * args.steps / (total_ms / 1e3)
     print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": "fput_beta_lyapunov_qr10_h0.05", "N": Ns,
-                                 "orbits_per_N": n, "rk4_steps_per_bench_step": args.chunk},
+                      "config": {"workload": "fput_beta_lyapunov_h0.05", "N": Ns,
+                                 "orbits_per_N": n, "rk4_steps_per_bench_step": args.chunk,
+                                 "qr_every": args.qr_every,
+                                 "launch": "one CUDA graph, concurrent branches" if args.fput_batch
+                                           else "one launch per N"},
                       "per_N": per_n}))
     return 0
 
 
-def run_classify(args):
+def classify_result(n_side: int, final_steps: int, confidence=None) -> dict:
     """Time to classify a Henon-Heiles section grid (E = 1/8, final t = steps * 0.01)
     by the plain form (FP64 vectors, every orbit to the end) and by the fast form
     (FP32 vector frame, early exit, compacted CUDA-graph chunks, and the trained
     surrogate when its weights are present), with the label agreement; a 2 %
     random sample of the orbits the surrogate stopped is judged against the plain
     labels as well."""
-    import torch
-
-    from paper_2507_00622_gb300 import build as cuda_build
     from paper_2507_00622_gb300 import chs
     from paper_2507_00622_gb300 import classify as CL
     from paper_2507_00622_gb300 import surrogate as SG
 
-    cuda_build.build()
-    chs.load()
-    g = CL.GridSpec(E=1.0 / 8.0, n_side=args.n_side, n_steps=args.final_steps)
+    g = CL.GridSpec(E=1.0 / 8.0, n_side=n_side, n_steps=final_steps)
     plain = CL.run_plain(g)
     fast = CL.run_fast(g)
     valid = plain.status != chs.ORBIT_FORBIDDEN
     out = {"metric": "time-to-classified-grid vs plain at >=99.5% agreement", "unit": "s",
-           "config": {"workload": f"henon_heiles_E1/8_grid{args.n_side}x{args.n_side}_k2_ld",
-                      "final_t": args.final_steps * 0.01, "valid_cells": int(valid.sum())},
+           "config": {"workload": f"henon_heiles_E1/8_grid{n_side}x{n_side}_k2_ld",
+                      "final_t": final_steps * 0.01, "valid_cells": int(valid.sum())},
            "plain": {"seconds": plain.seconds, "orbit_steps": plain.orbit_steps, "dtype": "f64"},
            "fast": {"seconds": fast.seconds, "orbit_steps": fast.orbit_steps, "dtype": "f64 orbit + f32 frame",
                     "speedup": plain.seconds / fast.seconds,
@@ -486,7 +510,7 @@ def run_classify(args):
         with np.load(SG.WEIGHTS) as z:
             meta = _json.loads(str(z["meta"]))
         sur = SG.Surrogate.load()
-        conf = float(args.confidence or meta.get("confidence", 0.999))
+        conf = float(confidence or meta.get("confidence", 0.999))
         fs = CL.run_fast(g, surrogate=sur, confidence=conf)
         stopped = np.where((fs.n_exec == SG.DECIDE_STEP) & ((fs.status == chs.ORBIT_PREDICTED_REGULAR) |
                                                             (fs.status == chs.ORBIT_EARLY_CHAOTIC)))[0]
@@ -499,7 +523,16 @@ def run_classify(args):
             "judge_sample": int(judge.size),
             "judge_agreement": float(np.mean(fs.label[judge] == plain.label[judge])) if judge.size else None,
             "training": meta}
-    print(json.dumps(out))
+    return out
+
+
+def run_classify(args):
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+
+    cuda_build.build()
+    chs.load()
+    print(json.dumps(classify_result(args.n_side, args.final_steps, args.confidence)))
     return 0
 
 
@@ -519,8 +552,14 @@ def main():
     ap.add_argument("--workload", choices=["grid", "fput", "classify"], default="grid")
     ap.add_argument("--final-steps", type=int, default=1_000_000)
     ap.add_argument("--confidence", type=float, default=None)
+    ap.add_argument("--classify-side", type=int, default=256,
+                    help="grid side of the time-to-classified-grid measurement added to the "
+                         "throughput line (0 = skip); the full 1024 x 1024 measurement is "
+                         "--workload classify --n-side 1024")
     ap.add_argument("--fput-n", default="4,8,16,32,64")
     ap.add_argument("--fput-orbits", type=int, default=4096)
+    ap.add_argument("--qr-every", default="10", help="QR interval of the FPUT run, or 'auto' (autotuner)")
+    ap.add_argument("--fput-batch", action="store_true", help="all chain lengths in one CUDA graph")
     args = ap.parse_args()
     if args.workload == "fput":
         return run_fput(args)

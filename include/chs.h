@@ -331,6 +331,25 @@ chs_status chs_surrogate_decide(const void* params_bf16, const double* sali_seri
                                 const double* ld, double t_decide, const double* E, double confidence,
                                 int64_t n, int32_t* status_inout, float* prob_out, void* stream);
 
+/* One Lyapunov-spectrum job of a batch (see chs_lyapunov_spectrum). */
+typedef struct {
+    chs_system sys;
+    chs_params params;
+    int64_t n_orbits;
+    const double* ics;
+    const int32_t* ic_status;  /* nullable */
+    double* lambda_out;
+    int32_t* status_out;
+} chs_lyap_job;
+
+/* Runs several Lyapunov jobs -- typically FPUT chains of different N, each a
+ * differently shaped kernel -- as one CUDA graph whose branches run
+ * concurrently, so that blocks of different chain lengths share the SMs (an
+ * N = 64 block holds 143 KB of shared memory and leaves room for smaller
+ * ones).  Results are identical to separate chs_lyapunov_spectrum calls.  All
+ * jobs must be on the current device; at most 16 jobs. */
+chs_status chs_lyapunov_batch(const chs_lyap_job* jobs, int32_t n_jobs, void* stream);
+
 /* Message for the last non-OK status returned on this thread ("" if none). */
 const char* chs_last_error(void);
 

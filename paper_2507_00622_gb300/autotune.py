@@ -1,0 +1,126 @@
+"""Autotuner for launch-level parameters, with a JSON cache keyed by the GPU and
+the workload.  Every candidate runs through the C ABI on a sample of the workload;
+the choice is cached and reused.
+
+Tuned parameters:
+- qr_every of the FPUT Lyapunov run.  The QR steps only re-orthonormalise the
+  vectors: the accumulated sum of ln R_ii equals the log-diagonal of the R factor
+  of the whole propagator product, whatever the interval, so the spectrum changes
+  only by rounding.  A longer interval lets the columns drift towards the fastest
+  direction (cond(W) ~ exp((lambda_max - lambda_min) q h)), which the
+  Gram-Schmidt step must undo.  The tuner keeps the fastest candidate whose
+  spectrum matches the reference interval's to `tol` on the sample.
+- chunk_steps of compacted runs (chs_integrate_compacted): the fastest candidate
+  on a sample grid; short chunks drop finished orbits sooner, long chunks launch
+  less often.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import chs
+from .inputs import hh_section_box, normal_mode_draws
+
+
+def cache_path() -> str:
+    return os.environ.get("CHS_AUTOTUNE_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "chs_autotune.json"))
+
+
+def _load() -> dict:
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key: str, value: dict) -> None:
+    d = _load()
+    d[key] = value
+    os.makedirs(os.path.dirname(cache_path()), exist_ok=True)
+    tmp = cache_path() + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(d, f, indent=1)
+    os.replace(tmp, cache_path())
+
+
+def _gpu() -> str:
+    return torch.cuda.get_device_name(torch.cuda.current_device())
+
+
+def tune_fput_qr(N: int, candidates=(10, 20, 50, 100), reference: int = 10, tol: float = 1e-10,
+                 n_orbits: int = 1216, steps: int = 2000, dt: float = 0.05, refresh: bool = False) -> dict:
+    """Pick qr_every for the FPUT-beta chain of N sites (energy density 0.1)."""
+    key = f"fput_qr|{_gpu()}|N={N}|ref={reference}|cand={','.join(map(str, candidates))}|tol={tol}"
+    if not refresh:
+        hit = _load().get(key)
+        if hit:
+            return hit
+    S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
+    Q, P = normal_mode_draws(4242 + N, N, n_orbits)
+    ics = torch.empty((2 * N, n_orbits), dtype=torch.float64, device="cuda")
+    chs.chs_fput_mode_ics(S.h, n_orbits, torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(),
+                          torch.full((n_orbits,), 0.1 * N, dtype=torch.float64, device="cuda"), ics)
+    lam = {q: torch.empty((2 * N, n_orbits), dtype=torch.float64, device="cuda") for q in candidates}
+    st = torch.empty(n_orbits, dtype=torch.int32, device="cuda")
+    times = {}
+    for q in candidates:
+        prm = chs.params(dt, steps, qr_every=q, sample_every=100)
+        chs.chs_lyapunov_spectrum(S.h, prm, n_orbits, ics, None, lam[q], st)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        chs.chs_lyapunov_spectrum(S.h, prm, n_orbits, ics, None, lam[q], st)
+        torch.cuda.synchronize()
+        times[q] = time.perf_counter() - t0
+    ref = lam[reference].cpu().numpy()
+    errs = {q: float(np.abs(lam[q].cpu().numpy() - ref).max()) for q in candidates}
+    ok = [q for q in candidates if errs[q] <= tol]
+    best = min(ok, key=lambda q: times[q])
+    out = {"qr_every": int(best), "seconds": {str(q): times[q] for q in candidates},
+           "max_abs_diff_vs_ref": {str(q): errs[q] for q in candidates}, "n_orbits": n_orbits,
+           "steps": steps}
+    _store(key, out)
+    return out
+
+
+def tune_compact_chunk(E: float = 0.125, side: int = 256, steps: int = 100_000, k: int = 2,
+                       candidates=(500, 1000, 2000, 5000, 10000), refresh: bool = False) -> dict:
+    """Pick chunk_steps for compacted Henon-Heiles grid runs (FP32 frame, early exit)."""
+    key = f"compact_chunk|{_gpu()}|E={E}|side={side}|k={k}|cand={','.join(map(str, candidates))}"
+    if not refresh:
+        hit = _load().get(key)
+        if hit:
+            return hit
+    S = chs.System(chs.HENON_HEILES, 2)
+    y0, y1, p0, p1 = hh_section_box(E)
+    n = side * side
+    ics = torch.empty((4, n), dtype=torch.float64, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    chs.chs_section_grid_ics(S.h, E, y0, y1, side, p0, p1, side, ics, st)
+    kw = dict(n_dev=k, ld_p=0.5, escape_r2=4.0, vec_precision=chs.VEC_FP32, early_exit=True)
+    work = chs.compact_work(n)
+    times = {}
+    for c in candidates:
+        best = None
+        for _ in range(2):
+            ens = chs.DeviceEnsemble.empty(n, 4, k, vec_fp32=True)
+            abi = ens.abi()
+            chs.chs_ensemble_init(S.h, chs.params(0.01, 1, **kw), abi, ics, st)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            chs.chs_integrate_compacted(S.h, chs.params(0.01, steps, **kw), abi, c, work)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        times[c] = best
+    choice = min(candidates, key=lambda c: times[c])
+    out = {"chunk_steps": int(choice), "seconds": {str(c): times[c] for c in candidates},
+           "side": side, "steps": steps}
+    _store(key, out)
+    return out

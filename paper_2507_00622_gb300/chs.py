@@ -27,7 +27,7 @@ EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_sec
            "chs_fput_mode_ics", "chs_shell_ics", "chs_ensemble_init", "chs_integrate_batch",
            "chs_compact_work_size", "chs_integrate_compacted", "chs_integrate_compacted_static",
            "chs_indicators",
-           "chs_lyapunov_spectrum", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
+           "chs_lyapunov_spectrum", "chs_lyapunov_batch", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
            "chs_mlp_loss_grad", "chs_mlp_backward", "chs_mlp_adam", "chs_surrogate_decide",
            "chs_last_error", "chs_version")
 
@@ -44,6 +44,11 @@ class Params(C.Structure):
                 ("qr_every", C.c_int32), ("vec_precision", C.c_int32), ("early_exit", C.c_int32),
                 ("ld_p", C.c_double), ("escape_r2", C.c_double), ("dh_limit", C.c_double),
                 ("sali_threshold", C.c_double), ("seed", C.c_uint64)]
+
+
+class LyapJob(C.Structure):
+    _fields_ = [("sys", C.c_void_p), ("params", Params), ("n_orbits", C.c_int64), ("ics", C.c_void_p),
+                ("ic_status", C.c_void_p), ("lambda_out", C.c_void_p), ("status_out", C.c_void_p)]
 
 
 class Ensemble(C.Structure):
@@ -82,6 +87,7 @@ def load(path: str | None = None):
         "chs_indicators": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), I32, I32, P, P,
                                      P, P, P]),
         "chs_lyapunov_spectrum": (C.c_int, [P, C.POINTER(Params), I64, P, P, P, P, P]),
+        "chs_lyapunov_batch": (C.c_int, [C.POINTER(LyapJob), I32, P]),
         "chs_mlp_param_count": (C.c_size_t, []),
         "chs_mlp_features": (C.c_int, [P, I32, P, D, P, I64, P, P]),
         "chs_mlp_forward": (C.c_int, [P, P, I64, P, P, P]),
@@ -197,6 +203,15 @@ def chs_indicators(h, prm: Params, ens: Ensemble, grid_ny=0, grid_npy=0, sali=No
 def chs_lyapunov_spectrum(h, prm: Params, n, ics, ic_status, lam, status, stream=None):
     _check(load().chs_lyapunov_spectrum(h, C.byref(prm), n, _ptr(ics), _ptr(ic_status), _ptr(lam),
                                         _ptr(status), _stream(stream)))
+
+
+def chs_lyapunov_batch(jobs, stream=None):
+    """jobs: list of (handle, Params, n, ics, ic_status, lam, status) tuples."""
+    arr = (LyapJob * len(jobs))()
+    for i, (h, prm, n, ics, ic_st, lam, st) in enumerate(jobs):
+        arr[i] = LyapJob(h.value if isinstance(h, C.c_void_p) else h, prm, n, _ptr(ics), _ptr(ic_st),
+                         _ptr(lam), _ptr(st))
+    _check(load().chs_lyapunov_batch(arr, len(jobs), _stream(stream)))
 
 
 def chs_mlp_param_count() -> int:

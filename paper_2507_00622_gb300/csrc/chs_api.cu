@@ -410,9 +410,82 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
     return ok();
 }
 
-chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n, const double* ics,
-                                 const int32_t* ic_status, double* lambda_out, int32_t* status_out,
-                                 void* stream)
+static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const double* ics,
+                             double* lambda_out, int32_t* status_out);
+
+static chs_status lyap_launch(chs_system s, const chs_params* p, int64_t n, const double* ics,
+                              const int32_t* ic_status, double* lambda_out, int32_t* status_out,
+                              cudaStream_t st)
+{
+    const chs::StepArgs a = step_args(p);
+    if (s->sp.model == CHS_FPUT)
+        return cuda_status(chs::launch_fput_lyap(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
+                           "FPUT Lyapunov launch");
+    return cuda_status(chs::launch_lyap_small(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
+                       "Lyapunov launch");
+}
+
+chs_status chs_lyapunov_batch(const chs_lyap_job* jobs, int32_t n_jobs, void* stream)
+{
+    constexpr int kMaxJobs = 16;
+    if (!jobs || n_jobs < 1 || n_jobs > kMaxJobs) return fail(CHS_E_INVALID, "need 1..16 jobs");
+    for (int i = 0; i < n_jobs; ++i) {
+        const chs_lyap_job& j = jobs[i];
+        chs_status r = lyap_check(j.sys, &j.params, j.n_orbits, j.ics, j.lambda_out, j.status_out);
+        if (r != CHS_OK) return r;
+    }
+    // private streams and events for recording the fork/join graph (per thread, created once)
+    thread_local cudaStream_t lanes[kMaxJobs + 1] = {};
+    thread_local cudaEvent_t evs[kMaxJobs + 1] = {};
+    thread_local int lanes_device = -1;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (lanes_device != dev) {
+        for (int i = 0; i <= kMaxJobs; ++i) {
+            cudaError_t e = cudaStreamCreateWithFlags(&lanes[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_status(e, "batch streams");
+        }
+        lanes_device = dev;
+    }
+    // kernel attributes are set before recording (no such calls inside a capture)
+    for (int i = 0; i < n_jobs; ++i)
+        if (jobs[i].sys->sp.model == CHS_FPUT) {
+            cudaError_t pe = chs::prepare_fput_lyap(jobs[i].sys->sp.n_dof);
+            if (pe != cudaSuccess) return cuda_status(pe, "FPUT kernel attributes");
+        }
+    cudaStream_t root = lanes[kMaxJobs];
+    cudaError_t e = cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_status(e, "begin capture");
+    cudaError_t le = cudaEventRecord(evs[kMaxJobs], root);
+    chs_status r = CHS_OK;
+    for (int i = 0; i < n_jobs && le == cudaSuccess && r == CHS_OK; ++i) {
+        const chs_lyap_job& j = jobs[i];
+        le = cudaStreamWaitEvent(lanes[i], evs[kMaxJobs], 0);
+        if (le != cudaSuccess) break;
+        r = lyap_launch(j.sys, &j.params, j.n_orbits, j.ics, j.ic_status, j.lambda_out, j.status_out, lanes[i]);
+        if (r != CHS_OK) break;
+        le = cudaEventRecord(evs[i], lanes[i]);
+        if (le == cudaSuccess) le = cudaStreamWaitEvent(root, evs[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(root, &graph);
+    if (r != CHS_OK || le != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (r != CHS_OK) return r;
+        return cuda_status(le != cudaSuccess ? le : e, "recording the batch");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_status(e, "batch instantiate");
+    e = cudaGraphLaunch(exec, as_stream(stream));
+    cudaGraphExecDestroy(exec);
+    return cuda_status(e, "batch launch");
+}
+
+static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const double* ics,
+                             double* lambda_out, int32_t* status_out)
 {
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
@@ -424,20 +497,24 @@ chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n, c
     if (p->vec_precision != CHS_VEC_FP64) return fail(CHS_E_UNSUPPORTED, "the Lyapunov path is FP64 only");
     if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
     if (n > ((int64_t)1 << 31)) return fail(CHS_E_SIZE, "n exceeds 2^31");
-    if (n == 0) return ok();
-    if (!ics || !lambda_out || !status_out) return fail(CHS_E_INVALID, "pointers must be non-NULL");
-    const chs::StepArgs a = step_args(p);
-    cudaStream_t st = as_stream(stream);
+    if (n > 0 && (!ics || !lambda_out || !status_out)) return fail(CHS_E_INVALID, "pointers must be non-NULL");
     if (s->sp.model == CHS_FPUT) {
         if (!chs::fput_lyap_supported(s->sp.n_dof))
             return fail(CHS_E_UNSUPPORTED, "FPUT Lyapunov supports N in {4, 8, 16, 32, 64}");
-        return cuda_status(chs::launch_fput_lyap(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
-                           "FPUT Lyapunov launch");
+    } else if (!(s->sp.model == CHS_HENON_HEILES || s->sp.model == CHS_HARMONIC || s->sp.model == CHS_INVERTED)) {
+        return fail(CHS_E_UNSUPPORTED, "Lyapunov spectrum not implemented for this model");
     }
-    if (s->sp.model == CHS_HENON_HEILES || s->sp.model == CHS_HARMONIC || s->sp.model == CHS_INVERTED)
-        return cuda_status(chs::launch_lyap_small(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
-                           "Lyapunov launch");
-    return fail(CHS_E_UNSUPPORTED, "Lyapunov spectrum not implemented for this model");
+    return CHS_OK;
+}
+
+chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n, const double* ics,
+                                 const int32_t* ic_status, double* lambda_out, int32_t* status_out,
+                                 void* stream)
+{
+    chs_status r = lyap_check(s, p, n, ics, lambda_out, status_out);
+    if (r != CHS_OK) return r;
+    if (n == 0) return ok();
+    return lyap_launch(s, p, n, ics, ic_status, lambda_out, status_out, as_stream(stream));
 }
 
 size_t chs_mlp_param_count(void) { return chs::mlp_param_count(); }

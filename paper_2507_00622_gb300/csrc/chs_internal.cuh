@@ -88,6 +88,7 @@ cudaError_t launch_lyap_small(const SysPar& sp, const StepArgs& a, int64_t n, co
 cudaError_t launch_fput_lyap(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
                              const int32_t* ic_status, double* lambda, int32_t* status,
                              cudaStream_t st);
+cudaError_t prepare_fput_lyap(int n_dof);  // sets the shared-memory attribute once
 
 // Surrogate perceptron (k_mlp.cu).
 size_t mlp_param_count();

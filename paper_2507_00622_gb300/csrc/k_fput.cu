@@ -281,13 +281,35 @@ bool fput_lyap_supported(int n_dof)
 }
 
 template <int N>
+static cudaError_t prepare_n()
+{
+    static bool done = false;  // idempotent; set before any stream capture
+    if (done) return cudaSuccess;
+    cudaError_t err = cudaFuncSetAttribute(k_fput_lyap<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)FputLyapCfg<N>::SMEM);
+    if (err == cudaSuccess) done = true;
+    return err;
+}
+
+cudaError_t prepare_fput_lyap(int n_dof)
+{
+    switch (n_dof) {
+    case 4: return prepare_n<4>();
+    case 8: return prepare_n<8>();
+    case 16: return prepare_n<16>();
+    case 32: return prepare_n<32>();
+    case 64: return prepare_n<64>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int N>
 static cudaError_t fput_lyap_n(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
                                const int32_t* ic_status, double* lambda, int32_t* status,
                                cudaStream_t st)
 {
     using Cfg = FputLyapCfg<N>;
-    cudaError_t err = cudaFuncSetAttribute(k_fput_lyap<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)Cfg::SMEM);
+    cudaError_t err = prepare_n<N>();
     if (err != cudaSuccess) return err;
     k_fput_lyap<N><<<blocks_for(n, Cfg::G), Cfg::THREADS, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status,
                                                                           lambda, status);
