@@ -196,7 +196,9 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
  * fixed-step solver variant with vector normalisation, Sec. Functionalities);
  * in FP32 mode the frame Q is advanced by the exact
  * one-step RK4 propagator of the variational equations and re-orthonormalised
- * (Phi Q = Q' S, R <- S R with unit columns), the orbit and LD staying FP64;
+ * (Phi Q = Q' S, R <- S R with unit columns), the orbit staying FP64 and the
+ * LD accumulated in FP64 from an integrand summed in FP32 (correctly rounded
+ * FP32 square roots; about 1e-7 per term, averaging out along the orbit);
  * an orbit with sum_i q_i^2 > escape_r2 freezes as ESCAPED.  At absolute steps divisible by sample_every: non-finite -> frozen
  * NONFINITE; dh_max <- max(dh_max, |H - h0|); |H - h0| > dh_limit -> frozen
  * ENERGY_DRIFT; with early_exit, SALI < sali_threshold -> frozen EARLY_CHAOTIC.

@@ -49,6 +49,21 @@ __device__ __forceinline__ bool in_f32_range(int hi)
     return (unsigned)(hi - ((1023 - 126) << 20)) < (unsigned)(((1023 + 127) - (1023 - 126)) << 20);
 }
 
+// Round-to-nearest FP64 -> FP32 on the integer pipe (no FP64-pipe conversion):
+// values below FLT_MIN flush to zero, values beyond FLT_MAX become infinity.
+__device__ __forceinline__ float f32_from_f64(double a)
+{
+    const long long r = __double_as_longlong(a) + (1LL << 28);
+    const int hi = (int)(r >> 32);
+    const unsigned lo = (unsigned)r;
+    const int sgn = hi & (int)0x80000000;
+    const int ah = hi & 0x7fffffff;
+    int fb = ((ah - kBiasShift) << 3) | (int)(lo >> 29);
+    fb = ah < ((1023 - 126) << 20) ? 0 : fb;
+    fb = ah >= ((1023 + 128) << 20) ? 0x7f800000 : fb;
+    return __int_as_float(fb | sgn);
+}
+
 // sqrt(a) for a >= 0, relative error ~1e-13.
 __device__ __forceinline__ double sqrt_nr(double a)
 {

@@ -16,7 +16,10 @@
 //   GALI_m = prod_{j < m} R_jj,   SALI = R_11 sqrt(2 / (1 + |R_01|)),
 // which are the GALI and SALI of the unit vectors w_j / |w_j| (the re-
 // orthonormalisation of every step is the per-step renormalisation).  The
-// orbit, its energy check and the LD stay in FP64.
+// orbit and its energy check stay in FP64; the LD is accumulated in FP64 from
+// an integrand summed in FP32 (correctly rounded FP32 square roots of |f_i|
+// rounded to FP32), which takes the LD's square roots off the FP64 pipe at a
+// relative cost of about 1e-7 per term, averaging out along the orbit.
 //
 // Ensemble vector buffer in this mode: FP32, [k*d + k(k+1)/2][n]: rows j*d + c
 // hold Q (vector j, component c), rows k*d + j(j+1)/2 + i hold R_ij (i <= j).
@@ -27,21 +30,6 @@
 namespace chs {
 
 __host__ __device__ constexpr int tri(int i, int j) { return j * (j + 1) / 2 + i; }
-
-// Round-to-nearest FP64 -> FP32 on the integer pipe (no FP64-pipe conversion):
-// values below FLT_MIN flush to zero, values beyond FLT_MAX become infinity.
-__device__ __forceinline__ float f32_from_f64(double a)
-{
-    const long long r = __double_as_longlong(a) + (1LL << 28);
-    const int hi = (int)(r >> 32);
-    const unsigned lo = (unsigned)r;
-    const int sgn = hi & (int)0x80000000;
-    const int ah = hi & 0x7fffffff;
-    int fb = ((ah - kBiasShift) << 3) | (int)(lo >> 29);
-    fb = ah < ((1023 - 126) << 20) ? 0 : fb;
-    fb = ah >= ((1023 + 128) << 20) ? 0x7f800000 : fb;
-    return __int_as_float(fb | sgn);
-}
 
 __device__ __forceinline__ uint64_t splitmix64_at32(uint64_t seed, uint64_t m)
 {
@@ -164,7 +152,7 @@ k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitL
     while (s < todo) {
         ++s;
         double H[4][NH];
-        rk4_state_capture<Sys, LD>(x, L, a.dt, a.ld_sqrt, a.ld_p, sp, H);
+        rk4_state_capture<Sys, LD, true>(x, L, a.dt, a.ld_sqrt, a.ld_p, sp, H);
         float Hf[4][NH];
 #pragma unroll
         for (int q = 0; q < 4; ++q)

@@ -25,11 +25,38 @@ __device__ __forceinline__ double ld_integrand(const double* f, int ld_sqrt, dou
     return acc;
 }
 
+// The LD integrand summed in FP32: each |f_i| rounded to FP32 (integer pipe),
+// its correctly rounded FP32 root (or power), the sum widened exactly to FP64.
+template <int D>
+__device__ __forceinline__ double ld_integrand_f32(const double* f, int ld_sqrt, double p)
+{
+    float acc = 0.0f;
+    if (ld_sqrt) {
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc += sqrtf(fabsf(f32_from_f64(f[i])));
+    } else {
+        const float pf = (float)p;
+#pragma unroll
+        for (int i = 0; i < D; ++i) acc += powf(fabsf(f32_from_f64(f[i])), pf);
+    }
+    return acc < 1.17549435e-38f ? 0.0 : f32_to_f64_bits(acc);
+}
+
+template <int D, bool LD32>
+__device__ __forceinline__ double ld_term(const double* f, int ld_sqrt, double p)
+{
+    if constexpr (LD32)
+        return ld_integrand_f32<D>(f, ld_sqrt, p);
+    else
+        return ld_integrand<D>(f, ld_sqrt, p);
+}
+
 // One classic RK4 step of the orbit x and its LD accumulator L,
 //   k1 = f(x), k2 = f(x + h/2 k1), k3 = f(x + h/2 k2), k4 = f(x + h k3),
 //   x <- x + h/6 (k1 + 2 k2 + 2 k3 + k4),
 // recording Hess V at the four stage states in H[s] (packed upper triangle).
-template <class Sys, bool LD>
+// LD32: the LD integrand is summed in FP32 (ld_integrand_f32).
+template <class Sys, bool LD, bool LD32 = false>
 __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const double h,
                                                   const int ld_sqrt, const double ld_p,
                                                   const SysPar& sp, double (*H)[Sys::NH])
@@ -44,7 +71,7 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
         ax[c] = f[c];
         xs[c] = fma(hh, f[c], x[c]);
     }
-    if (LD) aL = ld_integrand<D>(f, ld_sqrt, ld_p);
+    if (LD) aL = ld_term<D, LD32>(f, ld_sqrt, ld_p);
 #pragma unroll
     for (int s = 1; s < 3; ++s) {
         const double cs = (s == 1) ? hh : h;
@@ -54,12 +81,12 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
             ax[c] = fma(2.0, f[c], ax[c]);
             xs[c] = fma(cs, f[c], x[c]);
         }
-        if (LD) aL = fma(2.0, ld_integrand<D>(f, ld_sqrt, ld_p), aL);
+        if (LD) aL = fma(2.0, ld_term<D, LD32>(f, ld_sqrt, ld_p), aL);
     }
     Sys::eval(xs, f, H[3], sp);
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = fma(h6, ax[c] + f[c], x[c]);
-    if (LD) L = fma(h6, aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
+    if (LD) L = fma(h6, aL + ld_term<D, LD32>(f, ld_sqrt, ld_p), L);
 }
 
 // Exact one-step propagator of RK4 on the linear variational equation
