@@ -537,6 +537,69 @@ def run_classify(args):
     return 0
 
 
+def run_quartic(args):
+    """The coupled quartic oscillator run: 4,194,304 states on energy shells
+    E ~ U[1, 10] (random directions), eps = 0.1, k = 6 FP32 frame vectors (GALI_2..6),
+    per-orbit end times t_end ~ U[1e3, 1e4] with early exit, compacted CUDA-graph
+    chunks.  One bench step advances every live orbit by --chunk steps and
+    evaluates SALI and GALI_2..6."""
+    import torch
+
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+
+    cuda_build.build()
+    chs.load()
+    n = args.quartic_orbits
+    rng = np.random.default_rng(5)
+    dirs = torch.from_numpy(rng.standard_normal((6, n))).cuda()
+    E = torch.from_numpy(rng.uniform(1.0, 10.0, n)).cuda()
+    t_end = torch.from_numpy(rng.integers(100_000, 1_000_001, n).astype(np.int64)).cuda()
+    S = chs.System(chs.QUARTIC3, 3, (0.1,))
+    ics = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    chs.chs_shell_ics(S.h, n, dirs, E, ics)
+    del dirs
+    k = 6
+    kw = dict(n_dev=k, escape_r2=0.0, seed=3, vec_precision=chs.VEC_FP32, early_exit=True)
+    ens = chs.DeviceEnsemble.empty(n, 6, k, vec_fp32=True)
+    abi = ens.abi(with_ld=False, t_end=t_end)
+    chs.chs_ensemble_init(S.h, chs.params(0.01, 1, **kw), abi, ics)
+    work = chs.compact_work(n)
+    sali = torch.empty(n, dtype=torch.float64, device="cuda")
+    gali = torch.empty((k - 1, n), dtype=torch.float64, device="cuda")
+    step = 0
+    stream = torch.cuda.current_stream()
+
+    def one():
+        nonlocal step
+        chs.chs_integrate_compacted(S.h, chs.params(0.01, args.chunk, step0=step, **kw), abi, 500, work)
+        chs.chs_indicators(S.h, chs.params(0.01, 0, **kw), abi, sali=sali, gali=gali)
+        step += args.chunk
+
+    for _ in range(args.warmup):
+        one()
+    torch.cuda.synchronize()
+    e0 = int(ens.n_exec.sum())
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        one()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    done = int(ens.n_exec.sum()) - e0
+    st = ens.status.cpu().numpy()
+    print(json.dumps({"metric": METRIC, "value": done / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "f64 orbit + f32 frame", "data": "synthetic",
+                      "config": {"workload": "quartic3_eps0.1_shellE1-10_k6_fp32frame_gali2-6",
+                                 "n_orbits": n, "rk4_steps_per_bench_step": args.chunk,
+                                 "t_window": [args.warmup * args.chunk * 0.01, step * 0.01],
+                                 "early_exited": int((st == chs.ORBIT_EARLY_CHAOTIC).sum())}}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,7 +613,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
-    ap.add_argument("--workload", choices=["grid", "fput", "classify"], default="grid")
+    ap.add_argument("--workload", choices=["grid", "fput", "classify", "quartic"], default="grid")
+    ap.add_argument("--quartic-orbits", type=int, default=4_194_304)
     ap.add_argument("--final-steps", type=int, default=1_000_000)
     ap.add_argument("--confidence", type=float, default=None)
     ap.add_argument("--classify-side", type=int, default=256,
@@ -566,6 +630,8 @@ def main():
         return run_fput(args)
     if args.workload == "classify":
         return run_classify(args)
+    if args.workload == "quartic":
+        return run_quartic(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
