@@ -54,7 +54,7 @@ def _gpu() -> str:
     return torch.cuda.get_device_name(torch.cuda.current_device())
 
 
-def tune_fput_qr(N: int, candidates=(10, 20, 50, 100), reference: int = 10, tol: float = 1e-10,
+def tune_fput_qr(N: int, candidates=(10, 20, 50, 100, 200, 500), reference: int = 10, tol: float = 1e-10,
                  n_orbits: int = 1216, steps: int = 2000, dt: float = 0.05, refresh: bool = False) -> dict:
     """Pick qr_every for the FPUT-beta chain of N sites (energy density 0.1)."""
     key = f"fput_qr|{_gpu()}|N={N}|ref={reference}|cand={','.join(map(str, candidates))}|tol={tol}"
