@@ -440,3 +440,65 @@ def test_quartic_shell_ics_and_fp32_gali6():
     big = np.abs(r["gali"]) > 1e-6
     rel = np.abs(g["gali"][big] - r["gali"][big]) / r["gali"][big]
     assert np.median(rel) < 1e-3
+
+
+# --------------------------------------------------------------------------
+# full-size workloads of the other configurations, sampled
+# --------------------------------------------------------------------------
+
+def test_fput_bench_size_sampled_against_oracle():
+    """The FPUT Lyapunov run at bench size (4096 orbits per chain length, one
+    launch each, QR interval 10): 12 strided orbits per N recomputed by the oracle."""
+    steps = 200
+    for N in (4, 8, 16, 32, 64):
+        n = 4096
+        Q, P = normal_mode_draws(1000 + N, N, n)
+        S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
+        ics = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+        chs.chs_fput_mode_ics(S.h, n, torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(),
+                              torch.full((n,), 0.1 * N, dtype=torch.float64, device="cuda"), ics)
+        lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, steps, qr_every=10, sample_every=100), n, ics,
+                                  None, lam, st)
+        torch.cuda.synchronize()
+        idx = strided_sample(n, 12)
+        ics_h = ics.cpu().numpy()[:, idx]
+        r, rs = O.lyapunov(O.fput(N), O.params(0.05, steps, qr_every=10, sample_every=100), ics_h)
+        assert np.abs(lam.cpu().numpy()[:, idx] - r).max() < 1e-8
+        np.testing.assert_array_equal(st.cpu().numpy()[idx], rs)
+
+
+def test_quartic_bench_size_sampled_against_oracle():
+    """The quartic-3 run at its full size (4,194,304 shell states, k = 6 FP32 frame,
+    uneven end steps, early exit), 1000 steps: 256 strided orbits recomputed by
+    the oracle with FP64 vectors."""
+    n = 4_194_304
+    rng = np.random.default_rng(5)
+    dirs = rng.standard_normal((6, n))
+    E = rng.uniform(1.0, 10.0, n)
+    t_end = rng.integers(100, 1001, n).astype(np.int64)
+    S = chs.System(chs.QUARTIC3, 3, (0.1,))
+    ics = torch.empty((6, n), dtype=torch.float64, device="cuda")
+    chs.chs_shell_ics(S.h, n, torch.from_numpy(dirs).cuda(), torch.from_numpy(E).cuda(), ics)
+    idx = strided_sample(n, 256)
+    ics_h = ics[:, torch.from_numpy(idx).cuda()].cpu().numpy()
+    kw = dict(dt=0.01, n_steps=1000, k=6, ld_p=0.0, sys_params=(0.1,), seed=3, early_exit=True)
+    ens = chs.DeviceEnsemble.empty(n, 6, 6, vec_fp32=True)
+    te = torch.from_numpy(t_end).cuda()
+    abi = ens.abi(with_ld=False, t_end=te)
+    prm = chs.params(0.01, 1000, n_dev=6, seed=3, vec_precision=chs.VEC_FP32, early_exit=True)
+    chs.chs_ensemble_init(S.h, prm, abi, ics)
+    work = chs.compact_work(n)
+    chs.chs_integrate_compacted(S.h, prm, abi, 500, work)
+    gali = torch.empty((5, n), dtype=torch.float64, device="cuda")
+    chs.chs_indicators(S.h, prm, abi, gali=gali)
+    torch.cuda.synchronize()
+    w_full = O.seed_vectors(3, n, 6, 6)
+    r = oracle_run(chs.QUARTIC3, 3, ics_h, None, w_in=w_full[:, idx], t_end=t_end[idx], **kw)
+    np.testing.assert_array_equal(ens.n_exec.cpu().numpy()[idx], r["n_exec"])
+    assert state_rel_err(ens.x.cpu().numpy()[:, idx], r["x"]).max() < STATE_RTOL
+    g = gali.cpu().numpy()[:, idx]
+    big = np.abs(r["gali"]) > 1e-6
+    rel = np.abs(g[big] - r["gali"][big]) / r["gali"][big]
+    assert np.median(rel) < 1e-3 and rel.max() < 5e-2
