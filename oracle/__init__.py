@@ -12,9 +12,13 @@ orbit ``o``; the phase-space order is ``(q_1..q_N, p_1..p_N)``.
 
 Each wrapper names the passage of arXiv 2507.00622 ("Chaoticus") it follows:
   energy / rhs / hessian   Eqs. Ham_HH, ham_eqs_HH, ham_FPU, ham_eqs_FPU
-  integrate                fixed-step RK4 on the variational system, vector
-                           normalisation and the LD (Sec. Functionalities,
-                           Sec. Statement of need)
+  integrate                fixed-step RK4 (or DOP853, the paper's DOP 8) on
+                           the variational system, vector normalisation and
+                           the LD (Sec. Functionalities, Sec. Statement of need)
+  integrate_adaptive       DOP 8(5) with adaptive step size and per-step error
+                           (Sec. Functionalities)
+  dop853_tableau           the DOP853 coefficients (Hairer, Norsett and Wanner,
+                           Solving ODEs I, Sec. II.10)
   indicators               SALI and GALI_k by SVD (Sec. Functionalities)
   ld_indicators            LD-based indicators from neighbouring cells
                            (Sec. Functionalities)
@@ -38,7 +42,8 @@ _lib = None
 
 HENON_HEILES, FPUT, QUARTIC3, HARMONIC, INVERTED = 1, 2, 3, 100, 101
 OK, FORBIDDEN, ESCAPED, NONFINITE, ENERGY_DRIFT, EARLY_CHAOTIC = 0, 1, 2, 3, 4, 5
-RK4, YOSHIDA4 = 0, 1
+STEP_FAIL = 7
+RK4, YOSHIDA4, DOP853 = 0, 1, 2
 
 
 class System(C.Structure):
@@ -52,6 +57,11 @@ class Params(C.Structure):
                 ("qr_every", C.c_int), ("integrator", C.c_int), ("ld_p", C.c_double),
                 ("escape_r2", C.c_double), ("dh_limit", C.c_double), ("early_exit", C.c_int),
                 ("sali_threshold", C.c_double)]
+
+
+class Adaptive(C.Structure):
+    _fields_ = [("t_final", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
+                ("h_max", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -90,6 +100,10 @@ def lib():
                                       C.c_uint64, P, P, P, P, P, P, P]
         L.o_integrate.argtypes = [C.POINTER(System), C.POINTER(Params), C.c_int64, P, P, P, P,
                                   P, P, P, P, C.c_int]
+        L.o_integrate_adaptive.argtypes = [C.POINTER(System), C.POINTER(Params),
+                                           C.POINTER(Adaptive), C.c_int64, P, P, P, P, P, P, P,
+                                           P, P, P, P, P, C.c_int]
+        L.o_dop853_tableau.argtypes = [P, P, P, P]
         L.o_shell_ics.restype = C.c_int
         L.o_shell_ics.argtypes = [C.POINTER(System), C.c_int64, P, P, P]
         L.o_jacobi_sv.argtypes = [C.c_int, C.c_int, P, P]
@@ -215,6 +229,26 @@ class Ensemble:
                           _p(self.status), _p(te), nthreads)
         return self
 
+    def integrate_adaptive(self, prm: Params, t_final: float, rtol: float, atol: float,
+                           h_max: float = 0.0, nthreads: int = 0) -> "Ensemble":
+        """DOP 8(5) with adaptive steps up to time t_final, at most prm.n_steps
+        accepted steps per orbit in this call.  The per-orbit time ``t``, next
+        step ``h`` (first call: prm.dt), last and largest accepted-step error and
+        rejection count live on the ensemble."""
+        if not hasattr(self, "t"):
+            self.t = np.zeros(self.n)
+            self.h = np.full(self.n, prm.dt)
+            self.err_last = np.zeros(self.n)
+            self.err_max = np.zeros(self.n)
+            self.n_rej = np.zeros(self.n, dtype=np.int64)
+        ad = Adaptive(t_final, rtol, atol, h_max)
+        lib().o_integrate_adaptive(C.byref(self.sysd), C.byref(prm), C.byref(ad), self.n,
+                                   _p(self.x), _p(self.w), _p(self.ld), _p(self.h0),
+                                   _p(self.dh_max), _p(self.n_exec), _p(self.status), _p(self.t),
+                                   _p(self.h), _p(self.err_last), _p(self.err_max),
+                                   _p(self.n_rej), nthreads)
+        return self
+
     def indicators(self, sali_threshold: float = 1e-8):
         n, k = self.n, self.k
         sali = np.empty(n)
@@ -233,6 +267,14 @@ def shell_ics(sysd: System, dirs, E):
     if lib().o_shell_ics(C.byref(sysd), n, _p(dirs), _p(E), _p(ics)) != 0:
         raise ValueError("shell initial conditions are defined for QUARTIC3")
     return ics
+
+
+def dop853_tableau():
+    """(a [12, 12], b, e5, b3) of the DOP853 pair as the oracle holds them."""
+    a = np.empty((12, 12))
+    b, e5, b3 = np.empty(12), np.empty(12), np.empty(12)
+    lib().o_dop853_tableau(_p(a), _p(b), _p(e5), _p(b3))
+    return a, b, e5, b3
 
 
 def jacobi_sv(A) -> np.ndarray:

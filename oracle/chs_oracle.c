@@ -35,6 +35,17 @@
  *                                  lopesino2017).  A 4th-order Yoshida
  *                                  splitting with its tangent map is kept as
  *                                  an independent cross-check integrator.
+ *   o_dop853_step                  the paper's own 8th-order solver (DOP 8,
+ *                                  Sec. Functionalities, ref prince1981):
+ *                                  the DOP853 pair of Dormand and Prince as
+ *                                  published in Hairer, Norsett and Wanner,
+ *                                  Solving Ordinary Differential Equations I
+ *                                  (2nd ed., Sec. II.10), in fixed-step use.
+ *   o_integrate_adaptive           DOP 8(5) with adaptive step size and the
+ *                                  per-step error (Sec. Functionalities):
+ *                                  the same pair with its 5th/3rd-order error
+ *                                  estimate and the standard step-size
+ *                                  controller (Hairer et al., Sec. II.4).
  *   o_indicators                   SALI (refs Skokos2001/03/04) and GALI_k as
  *                                  the product of the singular values of the
  *                                  d x k matrix of unit deviation vectors,
@@ -64,8 +75,8 @@
 
 enum { O_HENON_HEILES = 1, O_FPUT = 2, O_QUARTIC3 = 3, O_HARMONIC = 100, O_INVERTED = 101 };
 enum { OS_OK = 0, OS_FORBIDDEN = 1, OS_ESCAPED = 2, OS_NONFINITE = 3, OS_ENERGY_DRIFT = 4,
-       OS_EARLY_CHAOTIC = 5 };
-enum { OI_RK4 = 0, OI_YOSHIDA4 = 1 };
+       OS_EARLY_CHAOTIC = 5, OS_STEP_FAIL = 7 };
+enum { OI_RK4 = 0, OI_YOSHIDA4 = 1, OI_DOP853 = 2 };
 
 typedef struct {
     int model;
@@ -84,7 +95,7 @@ typedef struct {
     int renorm;           /* 1: normalise every deviation vector after each step */
     int sample_every;     /* health checks at absolute steps divisible by this */
     int qr_every;         /* Lyapunov: QR at steps divisible by this (and the last) */
-    int integrator;       /* OI_RK4 or OI_YOSHIDA4 */
+    int integrator;       /* OI_RK4, OI_YOSHIDA4 or OI_DOP853 */
     double ld_p;          /* exponent p of the LD; 0 switches the LD off */
     double escape_r2;     /* escape when sum_i q_i^2 exceeds this; 0 = off */
     double dh_limit;      /* ENERGY_DRIFT when |H - H0| exceeds this; 0 = off */
@@ -321,6 +332,121 @@ static void o_yoshida_step(const o_joint* J, double* z, double h)
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* DOP853: 12-stage explicit Runge-Kutta pair of order 8(5,3)                */
+/* ------------------------------------------------------------------------ */
+
+/* Coefficients of the DOP853 pair of Dormand and Prince (Hairer, Norsett and
+ * Wanner, Solving ODEs I, 2nd ed., Sec. II.10): nodes c_s (implied: c_s =
+ * sum_j a_sj), the strictly lower-triangular a_sj, the 8th-order weights b_s,
+ * the 5th-order error weights e5_s = b_s - bhat_s, and the 3rd-order weights
+ * b3_s on stages 1, 9 and 12 (error weights b_s - b3_s).  Stages are numbered
+ * from 0 here. */
+static const double o_dp_a[12][11] = {
+    {0},
+    {5.26001519587677318785587544488e-2},
+    {1.97250569845378994544595329183e-2, 5.91751709536136983633785987549e-2},
+    {2.95875854768068491816892993775e-2, 0.0, 8.87627564304205475450678981324e-2},
+    {2.41365134159266685502369798665e-1, 0.0, -8.84549479328286085344864962717e-1,
+     9.24834003261792003115737966543e-1},
+    {3.7037037037037037037037037037e-2, 0.0, 0.0, 1.70828608729473871279604482173e-1,
+     1.25467687566822425016691814123e-1},
+    {3.7109375e-2, 0.0, 0.0, 1.70252211019544039314978060272e-1,
+     6.02165389804559606850219397283e-2, -1.7578125e-2},
+    {3.70920001185047927108779319836e-2, 0.0, 0.0, 1.70383925712239993810214054705e-1,
+     1.07262030446373284651809199168e-1, -1.53194377486244017527936158236e-2,
+     8.27378916381402288758473766002e-3},
+    {6.24110958716075717114429577812e-1, 0.0, 0.0, -3.36089262944694129406857109825e0,
+     -8.68219346841726006818189891453e-1, 2.75920996994467083049415600797e1,
+     2.01540675504778934086186788979e1, -4.34898841810699588477366255144e1},
+    {4.77662536438264365890433908527e-1, 0.0, 0.0, -2.48811461997166764192642586468e0,
+     -5.90290826836842996371446475743e-1, 2.12300514481811942347288949897e1,
+     1.52792336328824235832596922938e1, -3.32882109689848629194453265587e1,
+     -2.03312017085086261358222928593e-2},
+    {-9.3714243008598732571704021658e-1, 0.0, 0.0, 5.18637242884406370830023853209e0,
+     1.09143734899672957818500254654e0, -8.14978701074692612513997267357e0,
+     -1.85200656599969598641566180701e1, 2.27394870993505042818970056734e1,
+     2.49360555267965238987089396762e0, -3.0467644718982195003823669022e0},
+    {2.27331014751653820792359768449e0, 0.0, 0.0, -1.05344954667372501984066689879e1,
+     -2.00087205822486249909675718444e0, -1.79589318631187989172765950534e1,
+     2.79488845294199600508499808837e1, -2.85899827713502369474065508674e0,
+     -8.87285693353062954433549289258e0, 1.23605671757943030647266201528e1,
+     6.43392746015763530355970484046e-1},
+};
+static const double o_dp_b[12] = {
+    5.42937341165687622380535766363e-2, 0.0, 0.0, 0.0, 0.0, 4.45031289275240888144113950566e0,
+    1.89151789931450038304281599044e0, -5.8012039600105847814672114227e0,
+    3.1116436695781989440891606237e-1, -1.52160949662516078556178806805e-1,
+    2.01365400804030348374776537501e-1, 4.47106157277725905176885569043e-2};
+static const double o_dp_e5[12] = {
+    1.312004499419488073250102996e-2, 0.0, 0.0, 0.0, 0.0, -1.225156446376204440720569753e0,
+    -4.957589496572501915214079952e-1, 1.664377182454986536961530415e0,
+    -3.503288487499736816886487290e-1, 3.341791187130174790297318841e-1,
+    8.192320648511571246570742613e-2, -2.235530786388629525884427845e-2};
+static const double o_dp_b3[12] = {
+    2.44094488188976377952755905512e-1, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0,
+    7.33846688281611857341361741547e-1, 0.0, 0.0, 2.20588235294117647058823529412e-2};
+
+/* Copies the tableau out (for the order-condition tests): a [12][12]
+ * row-major (zeros above the diagonal), b, e5, b3 [12]. */
+void o_dop853_tableau(double* a, double* b, double* e5, double* b3)
+{
+    for (int s = 0; s < 12; ++s) {
+        for (int j = 0; j < 12; ++j) a[s * 12 + j] = (j < s) ? o_dp_a[s][j] : 0.0;
+        b[s] = o_dp_b[s];
+        e5[s] = o_dp_e5[s];
+        b3[s] = o_dp_b3[s];
+    }
+}
+
+/* One DOP853 step of size h from z (length D) into zn:
+ *   K_s = F(z + h sum_{j<s} a_sj K_j),  s = 0..11,
+ *   zn  = z + h sum_s b_s K_s,
+ * and the error estimates (without the factor h) err5_i = sum_s e5_s K_s,i and
+ * err3_i = sum_s (b_s - b3_s) K_s,i.  K holds 12*D doubles, zt D doubles. */
+static void o_dop853_step(const o_joint* J, const double* z, double* zn, int D, double h,
+                          double* K, double* zt, double* err5, double* err3)
+{
+    for (int s = 0; s < 12; ++s) {
+        for (int i = 0; i < D; ++i) {
+            double acc = 0.0;
+            for (int j = 0; j < s; ++j) acc += o_dp_a[s][j] * K[j * D + i];
+            zt[i] = z[i] + h * acc;
+        }
+        o_joint_f(J, zt, K + s * D);
+    }
+    for (int i = 0; i < D; ++i) {
+        double sb = 0.0, s5 = 0.0, s3 = 0.0;
+        for (int s = 0; s < 12; ++s) {
+            sb += o_dp_b[s] * K[s * D + i];
+            s5 += o_dp_e5[s] * K[s * D + i];
+            s3 += (o_dp_b[s] - o_dp_b3[s]) * K[s * D + i];
+        }
+        zn[i] = z[i] + h * sb;
+        if (err5) err5[i] = s5;
+        if (err3) err3[i] = s3;
+    }
+}
+
+/* Error norm of a DOP853 step over the first m components (the orbit):
+ *   sc_i = atol + rtol max(|z_i|, |zn_i|),
+ *   E5 = sum_i (err5_i / sc_i)^2,  E3 = sum_i (err3_i / sc_i)^2,
+ *   err = |h| E5 / sqrt(m (E5 + 0.01 E3))     (0 when E5 = E3 = 0),
+ * the combined 5th/3rd-order estimate of the DOP853 pair. */
+static double o_dop853_err(const double* z, const double* zn, const double* err5,
+                           const double* err3, int m, double h, double atol, double rtol)
+{
+    double E5 = 0.0, E3 = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double a = fabs(z[i]), b = fabs(zn[i]);
+        double sc = atol + rtol * (a > b ? a : b);
+        E5 += (err5[i] / sc) * (err5[i] / sc);
+        E3 += (err3[i] / sc) * (err3[i] / sc);
+    }
+    if (E5 == 0.0 && E3 == 0.0) return 0.0;
+    return fabs(h) * E5 / sqrt((double)m * (E5 + 0.01 * E3));
+}
+
 static double o_norm(const double* v, int d)
 {
     double acc = 0.0;
@@ -541,6 +667,76 @@ static double o_sali_of(const double* a, const double* b, int d)
     return sp < sm ? sp : sm;
 }
 
+/* What follows each completed step: renormalise the vectors (if prm->renorm),
+ * freeze as ESCAPED if sum_i q_i^2 > escape_r2, and, when `check` is set (a
+ * health-check step), freeze as NONFINITE on any non-finite value, update
+ * dH_max, freeze as ENERGY_DRIFT beyond dh_limit and, with early_exit and
+ * k >= 2, as EARLY_CHAOTIC once SALI < sali_threshold.  Returns the status. */
+static int32_t o_post_step(const o_system* s, const o_params* prm, double* z, int D, int check,
+                           double h0, double* dhm)
+{
+    int d = 2 * s->n_dof, k = prm->n_dev, N = s->n_dof;
+    if (prm->renorm) {
+        for (int j = 0; j < k; ++j) {
+            double* v = z + d + j * d;
+            double nr = o_norm(v, d);
+            for (int c = 0; c < d; ++c) v[c] = v[c] / nr;
+        }
+    }
+    if (prm->escape_r2 > 0.0) {
+        double r2 = 0.0;
+        for (int i = 0; i < N; ++i) r2 += z[i] * z[i];
+        if (r2 > prm->escape_r2) return OS_ESCAPED;
+    }
+    if (check) {
+        if (!o_all_finite(z, D)) return OS_NONFINITE;
+        double dH = fabs(o_energy(s, z) - h0);
+        if (dH > *dhm) *dhm = dH;
+        if (prm->dh_limit > 0.0 && dH > prm->dh_limit) return OS_ENERGY_DRIFT;
+        if (prm->early_exit && k >= 2 && o_sali_of(z + d, z + 2 * d, d) < prm->sali_threshold)
+            return OS_EARLY_CHAOTIC;
+    }
+    return OS_OK;
+}
+
+/* Scratch of one orbit's integration: the joint state z, the RK4 stages or the
+ * twelve DOP853 stages, a trial state and the error estimates. */
+typedef struct {
+    double *z, *zn, *zt, *K, *e5, *e3, *Hm;
+} o_work;
+
+static o_work o_work_alloc(int D, int N)
+{
+    o_work W;
+    W.z = (double*)malloc(sizeof(double) * (size_t)D * 17);
+    W.zn = W.z + D;
+    W.zt = W.z + 2 * D;
+    W.e5 = W.z + 3 * D;
+    W.e3 = W.z + 4 * D;
+    W.K = W.z + 5 * D;
+    W.Hm = (double*)malloc(sizeof(double) * (size_t)N * N);
+    return W;
+}
+
+static void o_work_free(o_work* W)
+{
+    free(W->Hm);
+    free(W->z);
+}
+
+/* One fixed step of the selected integrator on the joint state W->z. */
+static void o_fixed_step(const o_joint* J, const o_params* prm, o_work* W, int D)
+{
+    if (prm->integrator == OI_YOSHIDA4) {
+        o_yoshida_step(J, W->z, prm->dt);
+    } else if (prm->integrator == OI_DOP853) {
+        o_dop853_step(J, W->z, W->zn, D, prm->dt, W->K, W->zt, NULL, NULL);
+        memcpy(W->z, W->zn, sizeof(double) * (size_t)D);
+    } else {
+        o_rk4_step(J, W->z, D, prm->dt, W->K, W->K + D, W->K + 2 * D, W->K + 3 * D, W->zt);
+    }
+}
+
 void o_integrate(const o_system* s, const o_params* prm, int64_t n, double* x, double* w,
                  double* ld, const double* h0, double* dh_max, int64_t* n_exec, int32_t* status,
                  const int64_t* t_end, int nthreads)
@@ -553,10 +749,9 @@ void o_integrate(const o_system* s, const o_params* prm, int64_t n, double* x, d
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
     for (int64_t o = 0; o < n; ++o) {
         if (status[o] != OS_OK) continue;
-        double* z = (double*)malloc(sizeof(double) * (size_t)D * 6);
-        double* Hm = (double*)malloc(sizeof(double) * (size_t)N * N);
-        double *k1 = z + D, *k2 = z + 2 * D, *k3 = z + 3 * D, *k4 = z + 4 * D, *zt = z + 5 * D;
-        o_joint J = {s, d, k, use_ld, prm->ld_p, Hm};
+        o_work W = o_work_alloc(D, N);
+        double* z = W.z;
+        o_joint J = {s, d, k, use_ld, prm->ld_p, W.Hm};
         for (int c = 0; c < d; ++c) z[c] = x[c * n + o];
         for (int j = 0; j < k; ++j)
             for (int c = 0; c < d; ++c) z[d + j * d + c] = w[((int64_t)j * d + c) * n + o];
@@ -567,43 +762,12 @@ void o_integrate(const o_system* s, const o_params* prm, int64_t n, double* x, d
         int64_t todo = prm->n_steps;
         if (t_end && t_end[o] - n_exec[o] < todo) todo = t_end[o] - n_exec[o] > 0 ? t_end[o] - n_exec[o] : 0;
         for (int64_t sidx = 1; sidx <= todo; ++sidx) {
-            if (prm->integrator == OI_YOSHIDA4)
-                o_yoshida_step(&J, z, prm->dt);
-            else
-                o_rk4_step(&J, z, D, prm->dt, k1, k2, k3, k4, zt);
+            o_fixed_step(&J, prm, &W, D);
             done = sidx;
             int64_t abs_step = prm->step0 + sidx;
-            if (prm->renorm) {
-                for (int j = 0; j < k; ++j) {
-                    double* v = z + d + j * d;
-                    double nr = o_norm(v, d);
-                    for (int c = 0; c < d; ++c) v[c] = v[c] / nr;
-                }
-            }
-            if (prm->escape_r2 > 0.0) {
-                double r2 = 0.0;
-                for (int i = 0; i < N; ++i) r2 += z[i] * z[i];
-                if (r2 > prm->escape_r2) {
-                    st = OS_ESCAPED;
-                    break;
-                }
-            }
-            if (prm->sample_every > 0 && abs_step % prm->sample_every == 0) {
-                if (!o_all_finite(z, D)) {
-                    st = OS_NONFINITE;
-                    break;
-                }
-                double dH = fabs(o_energy(s, z) - h0[o]);
-                if (dH > dhm) dhm = dH;
-                if (prm->dh_limit > 0.0 && dH > prm->dh_limit) {
-                    st = OS_ENERGY_DRIFT;
-                    break;
-                }
-                if (prm->early_exit && k >= 2 && o_sali_of(z + d, z + 2 * d, d) < prm->sali_threshold) {
-                    st = OS_EARLY_CHAOTIC;
-                    break;
-                }
-            }
+            int check = prm->sample_every > 0 && abs_step % prm->sample_every == 0;
+            st = o_post_step(s, prm, z, D, check, h0[o], &dhm);
+            if (st != OS_OK) break;
         }
         for (int c = 0; c < d; ++c) x[c * n + o] = z[c];
         for (int j = 0; j < k; ++j)
@@ -612,8 +776,112 @@ void o_integrate(const o_system* s, const o_params* prm, int64_t n, double* x, d
         dh_max[o] = dhm;
         n_exec[o] += done;
         status[o] = st;
-        free(Hm);
-        free(z);
+        o_work_free(&W);
+    }
+}
+
+/* DOP 8(5) with adaptive step size (Sec. Functionalities).  Orbit o carries
+ * its time t[o] and its next step size hs[o]; a call advances it until
+ * t[o] = ad->t_final, or until prm->n_steps steps have been accepted in this
+ * call, or until it freezes.  Each step (Hairer et al., Sec. II.4, the
+ * standard controller with safety factor 0.9, growth at most 10, shrink at
+ * least 0.2):
+ *   the step size is clamped to [10 ulp(t), h_max] (h_max <= 0: no upper bound);
+ *   repeat: clip so that t + h <= t_final; take a DOP853 step; err = the
+ *     combined error norm over the d orbit components;
+ *     err < 1: accept, next h = h min(10, 0.9 err^(-1/8)) (10 when err = 0),
+ *              at most h if this step had a rejected attempt;
+ *     else   : reject (also when err is not finite), h = h max(0.2,
+ *              0.9 err^(-1/8)), count the rejection, and freeze as STEP_FAIL
+ *              (state kept) once h < 10 ulp(t).
+ * After each accepted step the checks of o_post_step run, health checks at
+ * accepted-step counts n_exec divisible by sample_every.  err_last[o] is the
+ * error of the last accepted step, err_max[o] the largest so far (both
+ * optional), n_rej[o] counts rejected attempts (optional). */
+typedef struct {
+    double t_final;
+    double rtol, atol;
+    double h_max;
+} o_adaptive;
+
+void o_integrate_adaptive(const o_system* s, const o_params* prm, const o_adaptive* ad, int64_t n,
+                          double* x, double* w, double* ld, const double* h0, double* dh_max,
+                          int64_t* n_exec, int32_t* status, double* t, double* hs,
+                          double* err_last, double* err_max, int64_t* n_rej, int nthreads)
+{
+    int d = 2 * s->n_dof, k = prm->n_dev, N = s->n_dof;
+    int use_ld = (prm->ld_p != 0.0) && ld != NULL;
+    int D = d + k * d + (use_ld ? 1 : 0);
+    int nt = o_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t o = 0; o < n; ++o) {
+        if (status[o] != OS_OK) continue;
+        o_work W = o_work_alloc(D, N);
+        double* z = W.z;
+        o_joint J = {s, d, k, use_ld, prm->ld_p, W.Hm};
+        for (int c = 0; c < d; ++c) z[c] = x[c * n + o];
+        for (int j = 0; j < k; ++j)
+            for (int c = 0; c < d; ++c) z[d + j * d + c] = w[((int64_t)j * d + c) * n + o];
+        if (use_ld) z[D - 1] = ld[o];
+        double dhm = dh_max[o];
+        double tt = t[o], h = hs[o];
+        double el = err_last ? err_last[o] : 0.0, em = err_max ? err_max[o] : 0.0;
+        int64_t rej = n_rej ? n_rej[o] : 0;
+        int32_t st = OS_OK;
+        int64_t done = 0;
+        while (done < prm->n_steps && tt < ad->t_final) {
+            double min_step = 10.0 * (nextafter(tt, INFINITY) - tt);
+            if (ad->h_max > 0.0 && h > ad->h_max) h = ad->h_max;
+            if (h < min_step) h = min_step;
+            int rejected = 0;
+            for (;;) {
+                if (h < min_step) {
+                    st = OS_STEP_FAIL;
+                    break;
+                }
+                double tn = tt + h;
+                if (tn > ad->t_final) tn = ad->t_final;
+                double hh = tn - tt;
+                o_dop853_step(&J, z, W.zn, D, hh, W.K, W.zt, W.e5, W.e3);
+                double err = o_dop853_err(z, W.zn, W.e5, W.e3, d, hh, ad->atol, ad->rtol);
+                if (err < 1.0) {
+                    double fac = (err == 0.0) ? 10.0 : 0.9 * pow(err, -1.0 / 8.0);
+                    if (fac > 10.0) fac = 10.0;
+                    if (rejected && fac > 1.0) fac = 1.0;
+                    h = hh * fac;
+                    memcpy(z, W.zn, sizeof(double) * (size_t)D);
+                    tt = tn;
+                    el = err;
+                    if (err > em) em = err;
+                    break;
+                }
+                double fac = 0.9 * pow(err, -1.0 / 8.0);
+                if (!(fac >= 0.2)) fac = 0.2;   /* also for a non-finite err */
+                h = hh * fac;
+                rejected = 1;
+                ++rej;
+            }
+            if (st != OS_OK) break;
+            ++done;
+            int64_t cnt = n_exec[o] + done;
+            int check = prm->sample_every > 0 && cnt % prm->sample_every == 0;
+            st = o_post_step(s, prm, z, D, check, h0[o], &dhm);
+            if (st != OS_OK) break;
+        }
+        for (int c = 0; c < d; ++c) x[c * n + o] = z[c];
+        for (int j = 0; j < k; ++j)
+            for (int c = 0; c < d; ++c) w[((int64_t)j * d + c) * n + o] = z[d + j * d + c];
+        if (use_ld) ld[o] = z[D - 1];
+        dh_max[o] = dhm;
+        n_exec[o] += done;
+        status[o] = st;
+        t[o] = tt;
+        hs[o] = h;
+        if (err_last) err_last[o] = el;
+        if (err_max) err_max[o] = em;
+        if (n_rej) n_rej[o] = rej;
+        o_work_free(&W);
     }
 }
 
@@ -773,19 +1041,15 @@ void o_lyapunov(const o_system* s, const o_params* prm, int64_t n, const double*
             for (int i = 0; i < d; ++i) lambda[(int64_t)i * n + o] = NAN;
             continue;
         }
-        double* z = (double*)malloc(sizeof(double) * (size_t)D * 6);
-        double* Hm = (double*)malloc(sizeof(double) * (size_t)N * N);
+        o_work Wk = o_work_alloc(D, N);
+        double* z = Wk.z;
         double* S = (double*)calloc((size_t)d, sizeof(double));
-        double *k1 = z + D, *k2 = z + 2 * D, *k3 = z + 3 * D, *k4 = z + 4 * D, *zt = z + 5 * D;
-        o_joint J = {s, d, d, 0, 0.0, Hm};
+        o_joint J = {s, d, d, 0, 0.0, Wk.Hm};
         for (int c = 0; c < d; ++c) z[c] = ics[(int64_t)c * n + o];
         for (int j = 0; j < d; ++j)
             for (int c = 0; c < d; ++c) z[d + j * d + c] = (c == j) ? 1.0 : 0.0;
         for (int64_t sidx = 1; sidx <= prm->n_steps; ++sidx) {
-            if (prm->integrator == OI_YOSHIDA4)
-                o_yoshida_step(&J, z, prm->dt);
-            else
-                o_rk4_step(&J, z, D, prm->dt, k1, k2, k3, k4, zt);
+            o_fixed_step(&J, prm, &Wk, D);
             if ((prm->qr_every > 0 && sidx % prm->qr_every == 0) || sidx == prm->n_steps) {
                 for (int j = 0; j < d; ++j) {
                     double* wj = z + d + j * d;
@@ -809,7 +1073,6 @@ void o_lyapunov(const o_system* s, const o_params* prm, int64_t n, const double*
         for (int i = 0; i < d; ++i) lambda[(int64_t)i * n + o] = (st == OS_OK) ? S[i] / T : NAN;
         status[o] = st;
         free(S);
-        free(Hm);
-        free(z);
+        o_work_free(&Wk);
     }
 }
