@@ -73,16 +73,30 @@ enum {
     CHS_ORBIT_EARLY_CHAOTIC = 5, /* SALI fell below sali_threshold at a health check with
                                     early_exit set, or the surrogate predicted "chaotic" with
                                     confidence; frozen, labelled chaotic */
-    CHS_ORBIT_PREDICTED_REGULAR = 6 /* the surrogate predicted "regular" with confidence;
-                                       frozen, labelled regular */
+    CHS_ORBIT_PREDICTED_REGULAR = 6, /* the surrogate predicted "regular" with confidence;
+                                        frozen, labelled regular */
+    CHS_ORBIT_STEP_FAIL = 7     /* adaptive DOP 8(5): the step size fell below 10 ulp(t)
+                                   after a rejection; frozen at the last accepted step */
 };
+
+/* Integrators (chs_params.integrator).
+ *   CHS_RK4     classic 4th-order Runge-Kutta, fixed step.
+ *   CHS_DOP853  the paper's 8th-order solver (DOP 8, Sec. Functionalities,
+ *               ref prince1981): the 12-stage DOP853 pair of Dormand and
+ *               Prince (Hairer, Norsett and Wanner, Solving ODEs I, 2nd ed.,
+ *               Sec. II.10); fixed step in chs_integrate_batch /
+ *               chs_integrate_compacted / chs_lyapunov_spectrum, adaptive with
+ *               its 5th/3rd-order error estimate in chs_integrate_adaptive.
+ *               FP64 deviation vectors only.
+ * The value 1 is not used by the library. */
+enum { CHS_RK4 = 0, CHS_DOP853 = 2 };
 
 /* Deviation-vector storage precision. */
 enum { CHS_VEC_FP64 = 0, CHS_VEC_FP32 = 1 };
 
 /* Integration and indicator parameters (plain old data). */
 typedef struct {
-    double dt;               /* fixed RK4 step h */
+    double dt;               /* fixed step h (adaptive runs: see chs_integrate_adaptive) */
     int64_t n_steps;         /* steps to take in this call */
     int64_t step0;           /* absolute index of the last step already taken */
     int32_t n_dev;           /* number k of deviation vectors (0..6; must match the ensemble) */
@@ -97,6 +111,8 @@ typedef struct {
     double dh_limit;         /* ENERGY_DRIFT when |H - H0| > dh_limit; 0 = off */
     double sali_threshold;   /* label: chaotic when SALI < sali_threshold */
     uint64_t seed;           /* SplitMix64 seed for device-seeded deviation vectors */
+    int32_t integrator;      /* CHS_RK4 or CHS_DOP853 */
+    int32_t reserved;        /* ignored */
 } chs_params;
 
 /* Resumable ensemble state: caller-owned device arrays over n_orbits orbits.
@@ -186,12 +202,13 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
                              const double* ics, const int32_t* ic_status, const void* w_in,
                              void* stream);
 
-/* Advances every OK orbit of the ensemble by p->n_steps classic RK4 steps of
- * size p->dt on the joint system (x, w_1..w_k, M_p):
+/* Advances every OK orbit of the ensemble by p->n_steps steps of size p->dt
+ * of the integrator p->integrator (classic RK4, or DOP853, the paper's DOP 8)
+ * on the joint system (x, w_1..w_k, M_p):
  *   x' = f(x) (Hamilton's equations), w_j' = J(x) w_j (variational equations,
  *   Sec. Statement of need), M_p' = sum_i |f_i(x)|^p (the LD, Sec. Statement
  *   of need),
- * the fixed-step integrator of Sec. Functionalities (RK4 in place of DOP8).
+ * the fixed-step integrators of Sec. Functionalities.
  * After each step: vectors are renormalised when p->renorm is set (the
  * fixed-step solver variant with vector normalisation, Sec. Functionalities);
  * in FP32 mode the frame Q is advanced by the exact
@@ -207,6 +224,43 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
  * (k <= 4) and QUARTIC3 (k <= 6). */
 chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ensemble* e,
                                void* stream);
+
+/* Adaptive-step controls of chs_integrate_adaptive. */
+typedef struct {
+    double t_final;  /* every orbit is integrated from its time t[o] up to t_final */
+    double rtol;     /* error tolerances: scale_i = atol + rtol * max(|x_i|, |x_new_i|) */
+    double atol;
+    double h_max;    /* largest step size; <= 0: no limit */
+} chs_adaptive;
+
+/* DOP 8(5) with adaptive step size and the error of each step (Sec.
+ * Functionalities): the DOP853 pair (p->integrator must be CHS_DOP853) on the
+ * same joint system and with the same per-step checks as chs_integrate_batch.
+ * Orbit o carries its time t[o] and its next step size h[o] (caller-owned
+ * device arrays [n]; start with t = 0 and h = a first guess).  A call advances
+ * every OK orbit until t[o] reaches a->t_final or p->n_steps steps have been
+ * accepted in this call.  Each step:
+ *   h is clamped to [10 ulp(t), h_max]; then, until a trial is accepted:
+ *   the trial step is clipped so that t + h <= t_final; the error of the trial
+ *   over the d orbit components is the combined 5th/3rd-order estimate of the
+ *   DOP853 pair,
+ *     err = |h| E5 / sqrt(d (E5 + 0.01 E3)),  E5 = sum_i (err5_i / scale_i)^2,
+ *   E3 likewise; err < 1 accepts the trial and sets the next
+ *   h = h min(10, 0.9 err^(-1/8)) (10 when err = 0; at most h after a rejected
+ *   trial in the same step); otherwise (also when err is not finite) the trial is
+ *   rejected, h = h max(0.2, 0.9 err^(-1/8)), and the orbit freezes as
+ *   STEP_FAIL once h < 10 ulp(t).
+ * Accepted steps count in n_exec; health checks run at accepted-step counts
+ * divisible by p->sample_every.  Optional outputs (NULL to skip), all [n]:
+ * err_last (the error of the last accepted step), err_max (running maximum,
+ * read and updated), n_rejected (running count of rejected trials, read and
+ * updated).  The deviation vectors and the LD do not enter the error (their
+ * stages are computed only for accepted trials).  p->dt, p->step0 and e->t_end
+ * are not used (t_end must be NULL).  Supported: HENON_HEILES, HARMONIC,
+ * INVERTED (k <= 4), QUARTIC3 (k <= 6); FP64 vectors. */
+chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_adaptive* a,
+                                  const chs_ensemble* e, double* t, double* h, double* err_last,
+                                  double* err_max, int64_t* n_rejected, void* stream);
 
 /* Bytes of device scratch that chs_integrate_compacted needs for n orbits. */
 size_t chs_compact_work_size(int64_t n_orbits);
@@ -268,7 +322,9 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
 
 /* Lyapunov spectrum by periodic QR (Sec. Functionalities, Lyapunov item;
  * FPU example of Sec. Examples).  d deviation vectors start as the identity
- * and follow the variational equations under RK4 with the orbit; every
+ * and follow the variational equations with the orbit under p->integrator
+ * (RK4 for every supported system; DOP853 for HENON_HEILES, HARMONIC and
+ * INVERTED); every
  * p->qr_every steps and at the last step the vector matrix W is factorised
  * W = QR with R_ii > 0, S_i += ln R_ii and W <- Q.  lambda_out [d][n] gets
  * S_i / (n_steps * dt) in column order; status_out [n] gets the orbit status

@@ -20,11 +20,13 @@ LIB_PATH = os.path.join(_HERE, "libchs.so")
 CHS_OK, CHS_E_INVALID, CHS_E_UNSUPPORTED, CHS_E_CUDA, CHS_E_NOMEM, CHS_E_SIZE = range(6)
 HENON_HEILES, FPUT, QUARTIC3, HARMONIC, INVERTED = 1, 2, 3, 100, 101
 (ORBIT_OK, ORBIT_FORBIDDEN, ORBIT_ESCAPED, ORBIT_NONFINITE, ORBIT_ENERGY_DRIFT,
- ORBIT_EARLY_CHAOTIC, ORBIT_PREDICTED_REGULAR) = range(7)
+ ORBIT_EARLY_CHAOTIC, ORBIT_PREDICTED_REGULAR, ORBIT_STEP_FAIL) = range(8)
 VEC_FP64, VEC_FP32 = 0, 1
+RK4, DOP853 = 0, 2
 
 EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_section_grid_ics",
            "chs_fput_mode_ics", "chs_shell_ics", "chs_ensemble_init", "chs_integrate_batch",
+           "chs_integrate_adaptive",
            "chs_compact_work_size", "chs_integrate_compacted", "chs_integrate_compacted_static",
            "chs_indicators",
            "chs_lyapunov_spectrum", "chs_lyapunov_batch", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
@@ -43,7 +45,13 @@ class Params(C.Structure):
                 ("n_dev", C.c_int32), ("renorm", C.c_int32), ("sample_every", C.c_int32),
                 ("qr_every", C.c_int32), ("vec_precision", C.c_int32), ("early_exit", C.c_int32),
                 ("ld_p", C.c_double), ("escape_r2", C.c_double), ("dh_limit", C.c_double),
-                ("sali_threshold", C.c_double), ("seed", C.c_uint64)]
+                ("sali_threshold", C.c_double), ("seed", C.c_uint64), ("integrator", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class Adaptive(C.Structure):
+    _fields_ = [("t_final", C.c_double), ("rtol", C.c_double), ("atol", C.c_double),
+                ("h_max", C.c_double)]
 
 
 class LyapJob(C.Structure):
@@ -84,6 +92,8 @@ def load(path: str | None = None):
                                                      I32, P]),
         "chs_ensemble_init": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), P, P, P, P]),
         "chs_integrate_batch": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), P]),
+        "chs_integrate_adaptive": (C.c_int, [P, C.POINTER(Params), C.POINTER(Adaptive),
+                                             C.POINTER(Ensemble), P, P, P, P, P, P]),
         "chs_indicators": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), I32, I32, P, P,
                                      P, P, P]),
         "chs_lyapunov_spectrum": (C.c_int, [P, C.POINTER(Params), I64, P, P, P, P, P]),
@@ -131,9 +141,10 @@ def _stream(stream):
 def params(dt: float, n_steps: int, *, step0: int = 0, n_dev: int = 0, renorm: bool = True,
            sample_every: int = 100, qr_every: int = 10, vec_precision: int = VEC_FP64,
            ld_p: float = 0.0, escape_r2: float = 0.0, dh_limit: float = 0.0,
-           sali_threshold: float = 1e-8, seed: int = 1, early_exit: bool = False) -> Params:
+           sali_threshold: float = 1e-8, seed: int = 1, early_exit: bool = False,
+           integrator: int = RK4) -> Params:
     return Params(dt, n_steps, step0, n_dev, int(renorm), sample_every, qr_every, vec_precision,
-                  int(early_exit), ld_p, escape_r2, dh_limit, sali_threshold, seed)
+                  int(early_exit), ld_p, escape_r2, dh_limit, sali_threshold, seed, integrator, 0)
 
 
 # ----------------------------------------------------------------------------
@@ -192,6 +203,13 @@ def chs_ensemble_init(h, prm: Params, ens: Ensemble, ics, ic_status=None, w_in=N
 
 def chs_integrate_batch(h, prm: Params, ens: Ensemble, stream=None):
     _check(load().chs_integrate_batch(h, C.byref(prm), C.byref(ens), _stream(stream)))
+
+
+def chs_integrate_adaptive(h, prm: Params, ad: Adaptive, ens: Ensemble, t, hstep, err_last=None,
+                           err_max=None, n_rejected=None, stream=None):
+    _check(load().chs_integrate_adaptive(h, C.byref(prm), C.byref(ad), C.byref(ens), _ptr(t),
+                                         _ptr(hstep), _ptr(err_last), _ptr(err_max),
+                                         _ptr(n_rejected), _stream(stream)))
 
 
 def chs_indicators(h, prm: Params, ens: Ensemble, grid_ny=0, grid_npy=0, sali=None, gali=None,

@@ -11,6 +11,7 @@
 #include <utility>
 
 #include "chs_internal.cuh"
+#include "k_dop853.cuh"
 
 // Recorded chunk sequence of chs_integrate_compacted and the inputs it was
 // recorded for.
@@ -92,6 +93,10 @@ chs_status check_params(const chs_params* p, const chs::SysPar& sp)
     if (!(p->ld_p >= 0.0) || !isfinite(p->ld_p)) return fail(CHS_E_INVALID, "ld_p must be finite and >= 0");
     if (!(p->escape_r2 >= 0.0)) return fail(CHS_E_INVALID, "escape_r2 must be >= 0");
     if (!(p->dh_limit >= 0.0)) return fail(CHS_E_INVALID, "dh_limit must be >= 0");
+    if (p->integrator != CHS_RK4 && p->integrator != CHS_DOP853)
+        return fail(CHS_E_INVALID, "integrator must be CHS_RK4 or CHS_DOP853");
+    if (p->integrator == CHS_DOP853 && p->vec_precision == CHS_VEC_FP32 && p->n_dev > 0)
+        return fail(CHS_E_UNSUPPORTED, "DOP853 runs with FP64 deviation vectors only");
     return ok();
 }
 
@@ -126,6 +131,15 @@ chs::StepArgs step_args(const chs_params* p)
     return a;
 }
 
+// The integrate launch of the selected integrator (whole ensemble, or over the
+// orbit list ol).
+cudaError_t launch_selected(const chs::SysPar& sp, const chs_params* p, const chs::StepArgs& a,
+                            const chs::EnsPtrs& ep, const chs::OrbitList* ol, cudaStream_t st)
+{
+    if (p->integrator == CHS_DOP853) return chs::launch_integrate_dp(sp, p->n_dev, p->ld_p > 0.0, a, ep, ol, st);
+    return chs::launch_integrate(sp, p->n_dev, p->vec_precision, p->ld_p > 0.0, a, ep, ol, st);
+}
+
 chs_status check_handle(chs_system s)
 {
     if (!s) return fail(CHS_E_INVALID, "system handle is NULL");
@@ -154,6 +168,11 @@ chs_status api_validate_run(chs_system s, const chs_params* p, const chs_ensembl
 chs_status api_fail(chs_status code, const char* msg) { return fail(code, "%s", msg); }
 StepArgs api_step_args(const chs_params* p) { return step_args(p); }
 EnsPtrs api_ens_ptrs(const chs_ensemble* e) { return ens_ptrs(e); }
+cudaError_t api_launch_integrate(const SysPar& sp, const chs_params* p, const StepArgs& a,
+                                 const EnsPtrs& ep, const OrbitList* ol, cudaStream_t st)
+{
+    return launch_selected(sp, p, a, ep, ol, st);
+}
 SysPar api_syspar(chs_system s) { return s->sp; }
 }  // namespace chs
 
@@ -290,9 +309,34 @@ chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ense
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
     if ((r = check_ensemble(e, p)) != CHS_OK) return r;
     if (e->n_orbits == 0 || p->n_steps == 0) return ok();
-    return cuda_status(chs::launch_integrate(s->sp, p->n_dev, p->vec_precision, p->ld_p > 0.0,
-                                             step_args(p), ens_ptrs(e), nullptr, as_stream(stream)),
+    return cuda_status(launch_selected(s->sp, p, step_args(p), ens_ptrs(e), nullptr, as_stream(stream)),
                        "integrate launch");
+}
+
+chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_adaptive* a,
+                                  const chs_ensemble* e, double* t, double* h, double* err_last,
+                                  double* err_max, int64_t* n_rejected, void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (!chs::small_model(s->sp.model))
+        return fail(CHS_E_UNSUPPORTED, "integration is implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
+    if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ensemble(e, p)) != CHS_OK) return r;
+    if (p->integrator != CHS_DOP853) return fail(CHS_E_INVALID, "adaptive runs need integrator = CHS_DOP853");
+    if (!a) return fail(CHS_E_INVALID, "adaptive controls are NULL");
+    if (!isfinite(a->t_final)) return fail(CHS_E_INVALID, "t_final must be finite");
+    if (!(a->rtol >= 0.0) || !(a->atol >= 0.0) || !isfinite(a->rtol) || !isfinite(a->atol))
+        return fail(CHS_E_INVALID, "rtol and atol must be finite and >= 0");
+    if (isnan(a->h_max)) return fail(CHS_E_INVALID, "h_max must not be NaN");
+    if (e->t_end) return fail(CHS_E_INVALID, "adaptive runs do not take t_end (use t_final)");
+    if (e->n_orbits > 0 && (!t || !h)) return fail(CHS_E_INVALID, "t and h must be non-NULL");
+    if (e->n_orbits == 0 || p->n_steps == 0) return ok();
+    const chs::AdaptArgs ad{a->t_final, a->rtol, a->atol, a->h_max};
+    const chs::AdaptPtrs ap{t, h, err_last, err_max, n_rejected};
+    return cuda_status(chs::launch_integrate_adaptive(s->sp, p->n_dev, p->ld_p > 0.0, step_args(p), ad,
+                                                      ens_ptrs(e), ap, as_stream(stream)),
+                       "adaptive integrate launch");
 }
 
 size_t chs_compact_work_size(int64_t n_orbits)
@@ -350,9 +394,7 @@ chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_
             a.n_steps = std::min<int64_t>(chunk_steps, p->n_steps - c * chunk_steps);
             le = cudaMemsetAsync(cb, 0, sizeof(int32_t), cs);
             const chs::OrbitList ol{la, ca, lb, cb};
-            if (le == cudaSuccess)
-                le = chs::launch_integrate(s->sp, p->n_dev, p->vec_precision, p->ld_p > 0.0, a, ep,
-                                           &ol, cs);
+            if (le == cudaSuccess) le = launch_selected(s->sp, p, a, ep, &ol, cs);
             std::swap(la, lb);
             std::swap(ca, cb);
         }
@@ -418,6 +460,9 @@ static chs_status lyap_launch(chs_system s, const chs_params* p, int64_t n, cons
                               cudaStream_t st)
 {
     const chs::StepArgs a = step_args(p);
+    if (p->integrator == CHS_DOP853)
+        return cuda_status(chs::launch_lyap_small_dp(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
+                           "Lyapunov launch");
     if (s->sp.model == CHS_FPUT)
         return cuda_status(chs::launch_fput_lyap(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
                            "FPUT Lyapunov launch");
@@ -495,6 +540,10 @@ static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const
     if (p->qr_every < 1) return fail(CHS_E_INVALID, "qr_every must be >= 1");
     if (p->sample_every < 0) return fail(CHS_E_INVALID, "sample_every must be >= 0");
     if (p->vec_precision != CHS_VEC_FP64) return fail(CHS_E_UNSUPPORTED, "the Lyapunov path is FP64 only");
+    if (p->integrator != CHS_RK4 && p->integrator != CHS_DOP853)
+        return fail(CHS_E_INVALID, "integrator must be CHS_RK4 or CHS_DOP853");
+    if (p->integrator == CHS_DOP853 && s->sp.model == CHS_FPUT)
+        return fail(CHS_E_UNSUPPORTED, "the FPUT Lyapunov path integrates with RK4 only");
     if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
     if (n > ((int64_t)1 << 31)) return fail(CHS_E_SIZE, "n exceeds 2^31");
     if (n > 0 && (!ics || !lambda_out || !status_out)) return fail(CHS_E_INVALID, "pointers must be non-NULL");

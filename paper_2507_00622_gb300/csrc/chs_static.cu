@@ -55,6 +55,8 @@ chs_status api_fail(chs_status code, const char* msg);
 StepArgs api_step_args(const chs_params* p);
 EnsPtrs api_ens_ptrs(const chs_ensemble* e);
 SysPar api_syspar(chs_system s);
+cudaError_t api_launch_integrate(const SysPar& sp, const chs_params* p, const StepArgs& a,
+                                 const EnsPtrs& ep, const OrbitList* ol, cudaStream_t st);
 }  // namespace chs
 
 extern "C" chs_status chs_integrate_compacted_static(chs_system s, const chs_params* p,
@@ -98,7 +100,7 @@ extern "C" chs_status chs_integrate_compacted_static(chs_system s, const chs_par
         ce = cudaMemsetAsync(cb, 0, sizeof(int32_t), st);
         const chs::OrbitList ol{la, ca, lb, cb};
         if (ce == cudaSuccess)
-            ce = chs::launch_integrate(sp, p->n_dev, p->vec_precision, p->ld_p > 0.0, a, ep, &ol, st);
+            ce = chs::api_launch_integrate(sp, p, a, ep, &ol, st);
         int32_t* t = la;
         la = lb;
         lb = t;

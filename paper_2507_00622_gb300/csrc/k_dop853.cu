@@ -1,0 +1,213 @@
+// k_dop853.cu -- the paper's own 8th-order solver in fixed-step use (DOP 8,
+// Sec. Functionalities) on the one-orbit-per-thread systems: the joint system
+// (orbit, deviation vectors, LD) with the per-step checks of the RK4 path, over
+// the whole ensemble or a compacted orbit list; and the Lyapunov spectrum of
+// the 2-DOF systems.  Building blocks and design notes: dop853.cuh.
+#include "dop853.cuh"
+
+namespace chs {
+namespace {
+
+using dp::kBlock;
+
+// One orbit per thread.  With ol.list set, thread t takes orbit list[t]
+// (t < *count) and appends the orbit to the next list when it is still running
+// after the call.
+template <class Sys, int K, bool LD>
+__global__ void __launch_bounds__(kBlock)
+k_integrate_dp(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
+{
+    constexpr int N = Sys::N, D = 2 * N;
+    constexpr int KK = K > 0 ? K : 1;
+    const dp::Slab<Sys> sl = dp::my_slab<Sys>();
+    const int64_t n = e.n;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool listed = ol.list != nullptr;
+    int64_t o = t;
+    if (listed) {
+        if (t >= *ol.count) return;
+        o = ol.list[t];
+    }
+    if (o >= n) return;
+    if (e.status[o] != CHS_ORBIT_OK) return;
+
+    double* wg = static_cast<double*>(e.w);
+    double x[D], w[KK][D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int c = 0; c < D; ++c) w[j][c] = wg[(j * D + c) * n + o];
+    double L = LD ? e.ld[o] : 0.0;
+    const double h0 = e.h0[o];
+    double dhm = e.dh_max[o];
+    const int64_t exec0 = e.n_exec[o];
+    int64_t todo = a.n_steps;
+    if (e.t_end) todo = min(todo, max(e.t_end[o] - exec0, (int64_t)0));
+
+    int32_t st = CHS_ORBIT_OK;
+    int64_t until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
+    int64_t s = 0;
+    while (s < todo) {
+        ++s;
+        double xn[D], dL = 0.0;
+        dp::orbit_step<Sys, LD, false>(sl, x, a.dt, a.ld_sqrt, a.ld_p, sp, xn, dL, nullptr, nullptr);
+#pragma unroll
+        for (int j = 0; j < K; ++j) dp::vector_step<Sys>(sl, w[j], a.dt);
+#pragma unroll
+        for (int c = 0; c < D; ++c) x[c] = xn[c];
+        if (LD) L += dL;
+        bool check = false;
+        if (--until == 0) {
+            until = a.sample_every;
+            check = true;
+        }
+        st = dp::post_step<Sys, K>(x, w, L, a, sp, check, h0, dhm);
+        if (st != CHS_ORBIT_OK) break;
+    }
+
+#pragma unroll
+    for (int c = 0; c < D; ++c) e.x[c * n + o] = x[c];
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+        for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = w[j][c];
+    if (LD) e.ld[o] = L;
+    e.dh_max[o] = dhm;
+    e.n_exec[o] = exec0 + s;
+    e.status[o] = st;
+    if (listed) list_append(ol, st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]), (int32_t)o);
+}
+
+// Lyapunov spectrum of the 2-DOF systems: W (4 x 4) in registers.
+template <class Sys>
+__global__ void __launch_bounds__(kBlock)
+k_lyap_small_dp(const StepArgs a, const SysPar sp, const int64_t n, const double* __restrict__ ics,
+                const int32_t* __restrict__ ic_status, double* __restrict__ lambda,
+                int32_t* __restrict__ status_out)
+{
+    constexpr int D = 2 * Sys::N;
+    const dp::Slab<Sys> sl = dp::my_slab<Sys>();
+    const int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+    int32_t st = ic_status ? ic_status[o] : CHS_ORBIT_OK;
+    double x[D], W[D][D], S[D];
+    bool fin = true;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        x[c] = ics[c * n + o];
+        fin = fin && isfinite(x[c]);
+        S[c] = 0.0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) W[j][c] = (j == c) ? 1.0 : 0.0;
+    }
+    if (st == CHS_ORBIT_OK && !fin) st = CHS_ORBIT_NONFINITE;
+    if (st == CHS_ORBIT_OK) {
+        int64_t until_qr = a.qr_every;
+        int64_t until = a.sample_every > 0 ? a.sample_every : -1;
+        for (int64_t s = 1; s <= a.n_steps; ++s) {
+            double xn[D], dL = 0.0;
+            dp::orbit_step<Sys, false, false>(sl, x, a.dt, 0, 0.0, sp, xn, dL, nullptr, nullptr);
+#pragma unroll
+            for (int j = 0; j < D; ++j) dp::vector_step<Sys>(sl, W[j], a.dt);
+#pragma unroll
+            for (int c = 0; c < D; ++c) x[c] = xn[c];
+            if (--until_qr == 0 || s == a.n_steps) {
+                until_qr = a.qr_every;
+                // modified Gram-Schmidt, R_jj > 0: S_j += ln R_jj, W <- Q
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+#pragma unroll
+                    for (int i = 0; i < j; ++i) {
+                        double r = 0.0;
+#pragma unroll
+                        for (int c = 0; c < D; ++c) r = fma(W[i][c], W[j][c], r);
+#pragma unroll
+                        for (int c = 0; c < D; ++c) W[j][c] = fma(-r, W[i][c], W[j][c]);
+                    }
+                    double n2 = 0.0;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) n2 = fma(W[j][c], W[j][c], n2);
+                    S[j] += 0.5 * log(n2);
+                    const double inv = rsqrt_nr(n2);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) W[j][c] *= inv;
+                }
+            }
+            if (--until == 0) {
+                until = a.sample_every;
+                bool f2 = true;
+#pragma unroll
+                for (int c = 0; c < D; ++c) f2 = f2 && isfinite(x[c]) && isfinite(S[c]);
+                if (!f2) {
+                    st = CHS_ORBIT_NONFINITE;
+                    break;
+                }
+            }
+        }
+    }
+    const double T = (double)a.n_steps * a.dt;
+#pragma unroll
+    for (int c = 0; c < D; ++c) lambda[c * n + o] = (st == CHS_ORBIT_OK) ? S[c] / T : qnan;
+    status_out[o] = st;
+}
+
+template <class Sys>
+cudaError_t fixed_sys(int k, bool ld, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
+                      const OrbitList* ol, cudaStream_t st)
+{
+    const unsigned g = blocks_for(e.n, kBlock);
+    const OrbitList l = ol ? *ol : OrbitList{};
+    constexpr size_t sm = dp::slab_bytes<Sys>();
+    return dp::with_k<Sys>(k, [&](auto kc) {
+        constexpr int K = decltype(kc)::value;
+        if (ld)
+            k_integrate_dp<Sys, K, true><<<g, kBlock, sm, st>>>(a, sp, e, l);
+        else
+            k_integrate_dp<Sys, K, false><<<g, kBlock, sm, st>>>(a, sp, e, l);
+    });
+}
+
+}  // namespace
+
+cudaError_t launch_integrate_dp(const SysPar& sp, int k, bool ld, const StepArgs& a,
+                                const EnsPtrs& e, const OrbitList* ol, cudaStream_t st)
+{
+    if (e.n == 0 || a.n_steps == 0) return cudaSuccess;
+    switch (sp.model) {
+    case CHS_HENON_HEILES: return fixed_sys<SysHenonHeiles>(k, ld, a, sp, e, ol, st);
+    case CHS_HARMONIC: return fixed_sys<SysHarmonic>(k, ld, a, sp, e, ol, st);
+    case CHS_INVERTED: return fixed_sys<SysInverted>(k, ld, a, sp, e, ol, st);
+    case CHS_QUARTIC3: return fixed_sys<SysQuartic3>(k, ld, a, sp, e, ol, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_lyap_small_dp(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
+                                 const int32_t* ic_status, double* lambda, int32_t* status,
+                                 cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned g = blocks_for(n, kBlock);
+    switch (sp.model) {
+    case CHS_HENON_HEILES:
+        k_lyap_small_dp<SysHenonHeiles><<<g, kBlock, dp::slab_bytes<SysHenonHeiles>(), st>>>(
+            a, sp, n, ics, ic_status, lambda, status);
+        break;
+    case CHS_HARMONIC:
+        k_lyap_small_dp<SysHarmonic><<<g, kBlock, dp::slab_bytes<SysHarmonic>(), st>>>(
+            a, sp, n, ics, ic_status, lambda, status);
+        break;
+    case CHS_INVERTED:
+        k_lyap_small_dp<SysInverted><<<g, kBlock, dp::slab_bytes<SysInverted>(), st>>>(
+            a, sp, n, ics, ic_status, lambda, status);
+        break;
+    default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace chs

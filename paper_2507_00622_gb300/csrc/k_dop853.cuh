@@ -1,0 +1,39 @@
+// k_dop853.cuh -- launchers of the DOP853 kernels (k_dop853.cu).
+#pragma once
+
+#include "chs_internal.cuh"
+
+namespace chs {
+
+// Adaptive-step controls (mirror of chs_adaptive, validated on the host).
+struct AdaptArgs {
+    double t_final;
+    double rtol, atol;
+    double h_max;  // <= 0: no limit
+};
+
+// Per-orbit state of adaptive runs; err_last, err_max, n_rej may be null.
+struct AdaptPtrs {
+    double* t;
+    double* h;
+    double* err_last;
+    double* err_max;
+    int64_t* n_rej;
+};
+
+// Fixed-step DOP853 on the joint system (the chs_integrate_batch contract);
+// ol != nullptr runs over a compacted orbit list.
+cudaError_t launch_integrate_dp(const SysPar& sp, int k, bool ld, const StepArgs& a,
+                                const EnsPtrs& e, const OrbitList* ol, cudaStream_t st);
+
+// Adaptive DOP 8(5) (the chs_integrate_adaptive contract).
+cudaError_t launch_integrate_adaptive(const SysPar& sp, int k, bool ld, const StepArgs& a,
+                                      const AdaptArgs& ad, const EnsPtrs& e, const AdaptPtrs& ap,
+                                      cudaStream_t st);
+
+// Lyapunov spectrum of the 2-DOF systems with fixed-step DOP853.
+cudaError_t launch_lyap_small_dp(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
+                                 const int32_t* ic_status, double* lambda, int32_t* status,
+                                 cudaStream_t st);
+
+}  // namespace chs

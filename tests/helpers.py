@@ -35,10 +35,11 @@ def oracle_system(model: int, n_dof: int, sys_params=()):
 def oracle_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=True,
                sample_every=100, escape_r2=0.0, dh_limit=0.0, seed=1, w_in=None,
                sali_threshold=1e-8, chunks=None, grid=None, sys_params=(), early_exit=False,
-               t_end=None):
+               t_end=None, integrator=0):
     S = oracle_system(model, n_dof, sys_params)
     kw = dict(n_dev=k, ld_p=ld_p, renorm=renorm, sample_every=sample_every, escape_r2=escape_r2,
-              dh_limit=dh_limit, early_exit=early_exit, sali_threshold=sali_threshold)
+              dh_limit=dh_limit, early_exit=early_exit, sali_threshold=sali_threshold,
+              integrator=integrator)
     e = O.Ensemble(S, O.params(dt, 1, **kw), ics, ic_status, w_in=w_in, seed=seed)
     step = 0
     for c in (chunks or [n_steps]):
@@ -57,7 +58,7 @@ def oracle_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm
 def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=True,
             sample_every=100, escape_r2=0.0, dh_limit=0.0, seed=1, w_in=None,
             sali_threshold=1e-8, chunks=None, grid=None, vec_fp32=False, sys_params=(),
-            early_exit=False, t_end=None, compact_chunk=None):
+            early_exit=False, t_end=None, compact_chunk=None, integrator=0):
     import torch
 
     from paper_2507_00622_gb300 import chs

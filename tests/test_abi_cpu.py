@@ -58,11 +58,31 @@ def test_null_handle_is_rejected(lib):
     assert lib.chs_destroy_system(None) == chs.CHS_OK
 
 
-def test_struct_layouts_match_header(lib):
+def test_struct_layouts_match_header(lib, tmp_path):
+    """The ctypes mirrors of the ABI structs have the size and field offsets
+    that a C compiler gives the header's declarations."""
+    import subprocess
     from paper_2507_00622_gb300 import chs
-    # chs_params: 1 double, 2 int64, 6 int32, 4 double, 1 uint64 = 88 bytes
-    assert C.sizeof(chs.Params) == 88
-    assert C.sizeof(chs.Ensemble) == 72
+    structs = {"chs_params": chs.Params, "chs_ensemble": chs.Ensemble,
+               "chs_adaptive": chs.Adaptive}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "chs.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append('printf("chs_lyap_job %zu\\n", sizeof(chs_lyap_job)); return 0; }')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
+    assert int(got["chs_lyap_job"]) == C.sizeof(chs.LyapJob)
+    assert C.sizeof(chs.Params) == 96 and C.sizeof(chs.Ensemble) == 72
 
 
 def test_binding_refuses_host_tensors(lib):
