@@ -84,6 +84,22 @@ def flops_per_orbit_step(k: int, ld: bool, vec_fp32: bool) -> tuple[int, int]:
     return xs + vs, 0
 
 
+def dp_flops_per_orbit_step(k: int, ld: bool) -> int:
+    """Algorithmic FP64 flops of one DOP853 step of the Henon-Heiles joint system,
+    counted like the RK4 figure (FMA = 2, sqrt and rsqrt = 1).  The tableau has
+    50 nonzero a_sj over the 11 stage inputs and 8 nonzero b_s.
+    Orbit: per stage f and Hess V 10 (12 stages); LD 7 at the 8 stages with
+      b_s != 0; stage inputs 2 per nonzero a_sj plus 2 for x + h * sum, per
+      component; accumulation 17 per component of (x, L) (7 FMA + 1 mul for
+      sum_s b_s K_s, then x + h * sum); escape test 3.
+    Vectors: variational 6 per stage, stage inputs as for the orbit,
+      accumulation 17 per component, renormalisation 12."""
+    inputs = (50 * 2 + 11 * 2) * 4
+    xs = 12 * 10 + (8 * 7 if ld else 0) + inputs + 17 * (4 + (1 if ld else 0)) + 3
+    vs = 12 * 6 + inputs + 17 * 4 + 12
+    return xs + k * vs
+
+
 def fp64_peak_tflops(sm_mhz: float) -> float:
     return SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
 
@@ -163,7 +179,8 @@ def dist_setup():
     return world, rank, local
 
 
-def cpu_oracle_sample(chunk: int, budget_s: float, n_sample: int = 4096, ny: int = 1024):
+def cpu_oracle_sample(chunk: int, budget_s: float, n_sample: int = 4096, ny: int = 1024,
+                      integrator: str = "rk4"):
     """The oracle as it stands on the host cores: a strided sample of valid cells of
     the same grid, integrated chunk by chunk until `budget_s` of CPU time."""
     import oracle as O
@@ -173,7 +190,8 @@ def cpu_oracle_sample(chunk: int, budget_s: float, n_sample: int = 4096, ny: int
     ics, st = O.grid_ics(E_GRID, y0, y1, ny, p0, p1, ny)
     valid = np.where(st == 0)[0]
     idx = valid[strided_sample(valid.size, n_sample)]
-    kw = dict(n_dev=K_DEV, ld_p=0.5, escape_r2=4.0, sample_every=100)
+    kw = dict(n_dev=K_DEV, ld_p=0.5, escape_r2=4.0, sample_every=100,
+              integrator=O.DOP853 if integrator == "dop853" else O.RK4)
     w = O.seed_vectors(1, ics.shape[1], K_DEV, 4)[:, idx]
     ens = O.Ensemble(O.henon_heiles(), O.params(DT, 1, **kw), ics[:, idx], st[idx], w_in=w)
     done, step, t0 = 0, 0, time.perf_counter()
@@ -189,7 +207,7 @@ def cpu_oracle_sample(chunk: int, budget_s: float, n_sample: int = 4096, ny: int
     el = time.perf_counter() - t0
     return {"value": done / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
             "sample": f"{idx.size} strided valid cells of the 1024x1024 E=1/6 grid, k=4, LD, "
-                      f"{step} RK4 steps from t=0 ({done} orbit-steps in {el:.1f} s)"}
+                      f"{step} {integrator.upper()} steps from t=0 ({done} orbit-steps in {el:.1f} s)"}
 
 
 def run_reference(args):
@@ -201,7 +219,7 @@ def run_reference(args):
     t_all = []
     res = None
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_sample(args.chunk, 0.0, n_sample=args.ref_sample)
+        r = cpu_oracle_sample(args.chunk, 0.0, n_sample=args.ref_sample, integrator=args.integrator)
         if i >= args.warmup:
             t_all.append(r["value"])
             res = r
@@ -211,7 +229,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "henon_heiles_E1/6_grid1024x1024_k4_sali_gali2-4_ld_rk4",
+            "config": {"workload": "henon_heiles_E1/6_grid1024x1024_k4_sali_gali2-4_ld_" + args.integrator,
                        "sample_per_step": f"{args.ref_sample} strided valid cells x {args.chunk} steps"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": res["cores"], "kind": "oracle",
                              "sample": res["sample"]},
@@ -250,8 +268,11 @@ def run_gpu(args):
     ics = torch.empty((4, n), dtype=torch.float64, device=dev)
     ic_st = torch.empty(n, dtype=torch.int32, device=dev)
     chs.chs_section_grid_ics(S.h, E_GRID, sy0, sy1, rows, p0, p1, npy, ics, ic_st)
+    dop = args.integrator == "dop853"
+    if dop and vec_fp32:
+        raise SystemExit("DOP853 runs with FP64 deviation vectors only")
     kw = dict(n_dev=K_DEV, ld_p=0.5, escape_r2=4.0, sample_every=100, seed=1 + rank,
-              vec_precision=vp, sali_threshold=1e-8)
+              vec_precision=vp, sali_threshold=1e-8, integrator=chs.DOP853 if dop else chs.RK4)
     ens = chs.DeviceEnsemble.empty(n, 4, K_DEV, vec_fp32, device=dev)
     abi = ens.abi()
     chs.chs_ensemble_init(S.h, chs.params(DT, 1, **kw), abi, ics, ic_st)
@@ -343,7 +364,10 @@ def run_gpu(args):
 
     if rank == 0:
         value = orbit_steps / (total_ms / 1e3)
-        f64, f32 = flops_per_orbit_step(K_DEV, True, vec_fp32)
+        if dop:
+            f64, f32 = dp_flops_per_orbit_step(K_DEV, True), 0
+        else:
+            f64, f32 = flops_per_orbit_step(K_DEV, True, vec_fp32)
         per_launch_steps = (exec1 - exec0) / args.steps
         achieved = f64 * per_launch_steps / (kern_ms / 1e3) / 1e12
         peak_mhz = clk["sm_max_mhz"] or 2070.0
@@ -353,17 +377,21 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if not vec_fp32 else "f64+f32",
             "data": "synthetic",
-            "config": {"workload": "henon_heiles_E1/6_grid1024x1024_k4_sali_gali2-4_ld_rk4",
+            "config": {"workload": "henon_heiles_E1/6_grid1024x1024_k4_sali_gali2-4_ld_"
+                                   + ("dop853" if dop else "rk4"),
                        "grid_per_gpu": [ny, npy], "n_orbits_per_gpu": ny * npy, "dt": DT,
-                       "rk4_steps_per_bench_step": args.chunk,
+                       "integrator": "DOP853 (fixed step)" if dop else "RK4",
+                       "steps_per_bench_step": args.chunk,
                        "t_window": [t_window0, t_window1], "t_end_of_full_run": 1e4,
                        "deviation_vectors": f"{K_DEV} x {'fp32' if vec_fp32 else 'fp64'}",
                        "l2": "inputs larger than L2: ensemble state %.0f MB per GPU" %
                              (h2d / 1e6),
                        "parallelism": f"orbit-range shards x{world}, no data-path collective"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": recorded_traffic(ny, vec_fp32),
-                         "kernel": "k_integrate<HenonHeiles,4,LD>",
+                         "frac": achieved / peak,
+                         "traffic": None if dop else recorded_traffic(ny, vec_fp32),
+                         "kernel": "k_integrate_dp<HenonHeiles,4,LD>" if dop else
+                                   "k_integrate<HenonHeiles,4,LD>",
                          "flops_per_orbit_step": {"fp64": f64, "fp32": f32},
                          "peak_basis": f"152 SMs x 2 DFMA/clk x 2 flop x {peak_mhz:.0f} MHz",
                          "kernel_ms_avg": kern_ms},
@@ -374,7 +402,8 @@ def run_gpu(args):
             "gpu_launches": 3 * args.steps,
         }
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_oracle_sample(args.chunk, args.cpu_budget)
+            line["cpu_baseline"] = cpu_oracle_sample(args.chunk, args.cpu_budget,
+                                                     integrator=args.integrator)
         if world == 1 and args.classify_side > 0:
             c = classify_result(args.classify_side, 1_000_000)
             line["classify"] = {
@@ -609,6 +638,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=1000, help="RK4 steps per bench step")
     ap.add_argument("--n-side", type=int, default=1024, help="grid side per GPU")
     ap.add_argument("--vec", choices=["fp64", "fp32"], default="fp64")
+    ap.add_argument("--integrator", choices=["rk4", "dop853"], default="rk4",
+                    help="grid workload: classic RK4 or the paper's DOP853 at the same fixed step")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -69,7 +69,7 @@ def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=Tr
     vp = chs.VEC_FP32 if vec_fp32 else chs.VEC_FP64
     kw = dict(n_dev=k, ld_p=ld_p, renorm=renorm, sample_every=sample_every, escape_r2=escape_r2,
               dh_limit=dh_limit, sali_threshold=sali_threshold, seed=seed, vec_precision=vp,
-              early_exit=early_exit)
+              early_exit=early_exit, integrator=integrator)
     ics_t = torch.from_numpy(np.ascontiguousarray(ics)).cuda()
     st_t = None if ic_status is None else torch.from_numpy(
         np.ascontiguousarray(ic_status, dtype=np.int32)).cuda()

@@ -213,11 +213,43 @@ def test_adaptive_hh_grid_matches_oracle(tol, k):
     assert same.sum() >= 0.99 * v.sum()
     assert state_rel_err(g["x"][:, same], r.x[:, same]).max() < STATE_RTOL
     assert np.abs(g["w"][:, same] - r.w[:, same]).max() < 1e-9
-    assert ind_err(g["ld"][same], r.ld[same]).max() < IND_TOL
+    # The LD is not in the error norm and its integrand sum_i |f_i|^(1/2) is not
+    # smooth, so its quadrature error follows the step sequence closely: in the
+    # oracle alone, moving the tolerance by 1e-7 relative (the step sizes by
+    # ~1e-8) moves the LD by up to 4e-6 relative while the states move by 3e-14.
+    # Step sizes here agree to ~1e-8, so the LD is held to 1e-5.
+    assert (np.abs(g["ld"][same] - r.ld[same]) / r.ld[same]).max() < 1e-5
     np.testing.assert_allclose(g["err_last"][same], r.err_last[same], rtol=1e-6, atol=0)
     np.testing.assert_allclose(g["err_max"][same], r.err_max[same], rtol=1e-6, atol=0)
     np.testing.assert_allclose(g["h"][same], r.h[same], rtol=1e-6, atol=0)
     assert np.all(g["err_last"][v] < 1.0)
+
+
+def test_adaptive_with_step_cap_matches_oracle_ld():
+    """With h_max small and a loose tolerance every step is h_max (the last one
+    clipped to t_final): both sides take the same step sequence, and the LD
+    agrees to the fixed-step bar."""
+    ics, st = O.grid_ics(*_grid(1 / 8, 16, 16))
+    n = ics.shape[1]
+    S = chs.System(HH, 2)
+    ens = chs.DeviceEnsemble.empty(n, 4, 2)
+    abi = ens.abi()
+    kw = dict(n_dev=2, ld_p=0.5, escape_r2=4.0, integrator=DP)
+    chs.chs_ensemble_init(S.h, chs.params(0.05, 1, **kw), abi, torch.from_numpy(ics).cuda(),
+                          torch.from_numpy(st).cuda())
+    t = torch.zeros(n, dtype=torch.float64, device="cuda")
+    h = torch.full((n,), 0.05, dtype=torch.float64, device="cuda")
+    chs.chs_integrate_adaptive(S.h, chs.params(0.05, 10**6, **kw), chs.Adaptive(20.01, 1e-3, 1e-3, 0.05),
+                               abi, t, h)
+    torch.cuda.synchronize()
+    prm = O.params(0.05, 10**6, n_dev=2, ld_p=0.5, escape_r2=4.0, integrator=O.DOP853)
+    e = O.Ensemble(O.henon_heiles(), prm, ics, st)
+    e.integrate_adaptive(prm, 20.01, 1e-3, 1e-3, h_max=0.05)
+    v = st == 0
+    np.testing.assert_array_equal(ens.n_exec.cpu().numpy(), e.n_exec)
+    assert np.all(e.n_exec[v] == 401)
+    assert state_rel_err(ens.x.cpu().numpy()[:, v], e.x[:, v]).max() < STATE_RTOL
+    assert ind_err(ens.ld.cpu().numpy()[v], e.ld[v]).max() < IND_TOL
 
 
 def test_adaptive_resumed_in_calls_is_bit_identical():
