@@ -431,6 +431,16 @@ def fput_flops_per_orbit_step(N: int, qr_every: int = 10) -> int:
     return 72 * N * N + 60 * N + 50 * N + (2 * d * d * (d + 1)) // qr_every
 
 
+def fput_dp_flops_per_orbit_step(N: int, qr_every: int = 10) -> int:
+    """Algorithmic FP64 flops of one DOP853 step of the FPUT Lyapunov run (FMA = 2):
+    per column of W and row pair (q_i, p_i), stage inputs 2 x (2 per nonzero a_sj
+    + 2) = 244, the tridiagonal J_s w 5 per stage (60), the 8 weighted sums 32 and
+    the update 4: 340 per (column, row pair), 680 N^2 in all; the orbit's stages
+    ~120 per component (240 N); modified Gram-Schmidt as for RK4."""
+    d = 2 * N
+    return 680 * N * N + 240 * N + (2 * d * d * (d + 1)) // qr_every
+
+
 def run_fput(args):
     """FPUT-beta Lyapunov spectra (k = 1, beta = 1, h = 0.05, QR every 10 steps):
     4096 normal-mode orbits at energy density 0.1 per chain length; one bench
@@ -459,10 +469,13 @@ def run_fput(args):
     for N in Ns:
         if args.qr_every == "auto":
             from paper_2507_00622_gb300 import autotune
-            qr[N] = autotune.tune_fput_qr(N)["qr_every"]
+            qr[N] = autotune.tune_fput_qr(N, integrator=args.integrator)["qr_every"]
         else:
             qr[N] = int(args.qr_every)
-    prms = {N: chs.params(0.05, args.chunk, qr_every=qr[N], sample_every=100) for N in Ns}
+    dop = args.integrator == "dop853"
+    prms = {N: chs.params(0.05, args.chunk, qr_every=qr[N], sample_every=100,
+                          integrator=chs.DOP853 if dop else chs.RK4) for N in Ns}
+    flops = fput_dp_flops_per_orbit_step if dop else fput_flops_per_orbit_step
     stream = torch.cuda.current_stream()
 
     def step(evs=None):
@@ -496,7 +509,7 @@ def run_fput(args):
             continue
         ms = float(np.mean([evs[i][j][0].elapsed_time(evs[i][j][1]) for i in range(args.steps)]))
         os_ = n * args.chunk / (ms / 1e3)
-        tf = fput_flops_per_orbit_step(N, qr[N]) * os_ / 1e12
+        tf = flops(N, qr[N]) * os_ / 1e12
         per_n[str(N)] = {"orbit_steps_per_s": os_, "kernel_ms": ms, "fp64_tflops": tf,
                          "frac_of_fp64_peak": tf / fp64_peak_tflops(2070.0), "qr_every": qr[N]}
     value = len(runs) * n * args.chunk * args.steps / (total_ms / 1e3)
@@ -504,8 +517,9 @@ def run_fput(args):
                       "steps": args.steps, "warmup": args.warmup,
                       "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": "fput_beta_lyapunov_h0.05", "N": Ns,
-                                 "orbits_per_N": n, "rk4_steps_per_bench_step": args.chunk,
+                      "config": {"workload": "fput_beta_lyapunov_h0.05" + ("_dop853" if dop else ""),
+                                 "N": Ns, "integrator": "DOP853 (fixed step)" if dop else "RK4",
+                                 "orbits_per_N": n, "steps_per_bench_step": args.chunk,
                                  "qr_every": args.qr_every,
                                  "launch": "one CUDA graph, concurrent branches" if args.fput_batch
                                            else "one launch per N"},

@@ -323,15 +323,15 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
 /* Lyapunov spectrum by periodic QR (Sec. Functionalities, Lyapunov item;
  * FPU example of Sec. Examples).  d deviation vectors start as the identity
  * and follow the variational equations with the orbit under p->integrator
- * (RK4 for every supported system; DOP853 for HENON_HEILES, HARMONIC and
- * INVERTED); every
+ * (RK4 or DOP853, fixed step); every
  * p->qr_every steps and at the last step the vector matrix W is factorised
  * W = QR with R_ii > 0, S_i += ln R_ii and W <- Q.  lambda_out [d][n] gets
  * S_i / (n_steps * dt) in column order; status_out [n] gets the orbit status
  * (a non-finite state at a health check gives NONFINITE and NaN exponents).
  * ic_status may be NULL.  Supported: FPUT with N in {4, 8, 16, 32, 64} (the
- * vectors live in shared memory, propagated by the exact one-step RK4
- * propagator), and HENON_HEILES, HARMONIC, INVERTED.  FP64 throughout. */
+ * vectors live in shared memory; RK4 propagates them by its exact one-step
+ * propagator, DOP853 column by column with the stages in registers), and
+ * HENON_HEILES, HARMONIC, INVERTED.  FP64 throughout. */
 chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n,
                                  const double* ics, const int32_t* ic_status,
                                  double* lambda_out, int32_t* status_out, void* stream);

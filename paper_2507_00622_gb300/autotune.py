@@ -55,9 +55,14 @@ def _gpu() -> str:
 
 
 def tune_fput_qr(N: int, candidates=(10, 20, 50, 100, 200, 500), reference: int = 10, tol: float = 1e-10,
-                 n_orbits: int = 1216, steps: int = 2000, dt: float = 0.05, refresh: bool = False) -> dict:
-    """Pick qr_every for the FPUT-beta chain of N sites (energy density 0.1)."""
+                 n_orbits: int = 1216, steps: int = 2000, dt: float = 0.05, refresh: bool = False,
+                 integrator: str = "rk4") -> dict:
+    """Pick qr_every for the FPUT-beta chain of N sites (energy density 0.1) under
+    the given integrator ("rk4" or "dop853")."""
     key = f"fput_qr|{_gpu()}|N={N}|ref={reference}|cand={','.join(map(str, candidates))}|tol={tol}"
+    if integrator != "rk4":
+        key += f"|{integrator}"
+    integ = chs.DOP853 if integrator == "dop853" else chs.RK4
     if not refresh:
         hit = _load().get(key)
         if hit:
@@ -71,7 +76,7 @@ def tune_fput_qr(N: int, candidates=(10, 20, 50, 100, 200, 500), reference: int 
     st = torch.empty(n_orbits, dtype=torch.int32, device="cuda")
     times = {}
     for q in candidates:
-        prm = chs.params(dt, steps, qr_every=q, sample_every=100)
+        prm = chs.params(dt, steps, qr_every=q, sample_every=100, integrator=integ)
         chs.chs_lyapunov_spectrum(S.h, prm, n_orbits, ics, None, lam[q], st)  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()

@@ -460,6 +460,9 @@ static chs_status lyap_launch(chs_system s, const chs_params* p, int64_t n, cons
                               cudaStream_t st)
 {
     const chs::StepArgs a = step_args(p);
+    if (p->integrator == CHS_DOP853 && s->sp.model == CHS_FPUT)
+        return cuda_status(chs::launch_fput_lyap_dp(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
+                           "FPUT Lyapunov launch");
     if (p->integrator == CHS_DOP853)
         return cuda_status(chs::launch_lyap_small_dp(s->sp, a, n, ics, ic_status, lambda_out, status_out, st),
                            "Lyapunov launch");
@@ -496,7 +499,9 @@ chs_status chs_lyapunov_batch(const chs_lyap_job* jobs, int32_t n_jobs, void* st
     // kernel attributes are set before recording (no such calls inside a capture)
     for (int i = 0; i < n_jobs; ++i)
         if (jobs[i].sys->sp.model == CHS_FPUT) {
-            cudaError_t pe = chs::prepare_fput_lyap(jobs[i].sys->sp.n_dof);
+            cudaError_t pe = jobs[i].params.integrator == CHS_DOP853
+                                 ? chs::prepare_fput_lyap_dp(jobs[i].sys->sp.n_dof)
+                                 : chs::prepare_fput_lyap(jobs[i].sys->sp.n_dof);
             if (pe != cudaSuccess) return cuda_status(pe, "FPUT kernel attributes");
         }
     cudaStream_t root = lanes[kMaxJobs];
@@ -542,8 +547,6 @@ static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const
     if (p->vec_precision != CHS_VEC_FP64) return fail(CHS_E_UNSUPPORTED, "the Lyapunov path is FP64 only");
     if (p->integrator != CHS_RK4 && p->integrator != CHS_DOP853)
         return fail(CHS_E_INVALID, "integrator must be CHS_RK4 or CHS_DOP853");
-    if (p->integrator == CHS_DOP853 && s->sp.model == CHS_FPUT)
-        return fail(CHS_E_UNSUPPORTED, "the FPUT Lyapunov path integrates with RK4 only");
     if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
     if (n > ((int64_t)1 << 31)) return fail(CHS_E_SIZE, "n exceeds 2^31");
     if (n > 0 && (!ics || !lambda_out || !status_out)) return fail(CHS_E_INVALID, "pointers must be non-NULL");

@@ -36,4 +36,11 @@ cudaError_t launch_lyap_small_dp(const SysPar& sp, const StepArgs& a, int64_t n,
                                  const int32_t* ic_status, double* lambda, int32_t* status,
                                  cudaStream_t st);
 
+// FPUT Lyapunov spectrum with fixed-step DOP853 (k_fput_dp.cu); the shared-memory
+// attribute is set once by prepare_fput_lyap_dp (before any stream capture).
+cudaError_t launch_fput_lyap_dp(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
+                                const int32_t* ic_status, double* lambda, int32_t* status,
+                                cudaStream_t st);
+cudaError_t prepare_fput_lyap_dp(int n_dof);
+
 }  // namespace chs

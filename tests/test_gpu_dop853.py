@@ -128,6 +128,54 @@ def test_lyapunov_small_dop853_matches_oracle():
     assert np.abs(lam.cpu().numpy()[:, ok] - r[:, ok]).max() < 1e-8
 
 
+@pytest.mark.parametrize("N,n,steps", [(4, 37, 120), (8, 13, 120), (16, 9, 100), (32, 5, 60),
+                                       (64, 3, 40)])
+def test_fput_lyapunov_dop853_matches_oracle(N, n, steps):
+    """FPUT chains with DOP853 (ragged orbit groups: n is not a multiple of the
+    orbits per block), one orbit with a non-OK initial status."""
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+    Q, P = normal_mode_draws(77 + N, N, n)
+    ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))
+    st = np.zeros(n, dtype=np.int32)
+    st[n // 2] = chs.ORBIT_FORBIDDEN
+    prm = dict(qr_every=10, sample_every=20)
+    S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
+    lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+    sto = torch.empty(n, dtype=torch.int32, device="cuda")
+    chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, steps, integrator=DP, **prm), n,
+                              torch.from_numpy(ics).cuda(), torch.from_numpy(st).cuda(), lam, sto)
+    torch.cuda.synchronize()
+    r, rs = O.lyapunov(O.fput(N), O.params(0.05, steps, integrator=O.DOP853, **prm), ics, st)
+    np.testing.assert_array_equal(sto.cpu().numpy(), rs)
+    ok = rs == 0
+    g = lam.cpu().numpy()
+    assert np.abs(g[:, ok] - r[:, ok]).max() < 1e-8
+    assert np.all(np.isnan(g[:, ~ok]))
+
+
+def test_fput_lyapunov_batch_dop853_equals_separate_calls():
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+    jobs, outs, keep = [], [], []
+    for N, integ in ((8, DP), (16, chs.RK4), (32, DP)):
+        n = 40
+        Q, P = normal_mode_draws(5 + N, N, n)
+        ics = torch.from_numpy(O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))).cuda()
+        S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
+        prm = chs.params(0.05, 100, integrator=integ, qr_every=20)
+        lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+        sto = torch.empty(n, dtype=torch.int32, device="cuda")
+        lam1 = torch.empty_like(lam)
+        sto1 = torch.empty_like(sto)
+        chs.chs_lyapunov_spectrum(S.h, prm, n, ics, None, lam1, sto1)
+        jobs.append((S.h, prm, n, ics, None, lam, sto))
+        outs.append((lam, sto, lam1, sto1))
+        keep.append(S)
+    chs.chs_lyapunov_batch(jobs)
+    torch.cuda.synchronize()
+    for lam, sto, lam1, sto1 in outs:
+        assert torch.equal(lam, lam1) and torch.equal(sto, sto1)
+
+
 def test_dop853_argument_checks():
     S = chs.System(HH, 2)
     ens = chs.DeviceEnsemble.empty(4, 4, 2, vec_fp32=True)
@@ -138,13 +186,6 @@ def test_dop853_argument_checks():
     with pytest.raises(chs.ChsError) as e:
         chs.chs_integrate_batch(S.h, chs.params(0.05, 10, n_dev=2, integrator=1), ens.abi())
     assert e.value.code == chs.CHS_E_INVALID
-    F = chs.System(chs.FPUT, 8, (1.0, 0.0, 1.0))
-    lam = torch.empty((16, 4), dtype=torch.float64, device="cuda")
-    sto = torch.empty(4, dtype=torch.int32, device="cuda")
-    ics = torch.zeros((16, 4), dtype=torch.float64, device="cuda")
-    with pytest.raises(chs.ChsError) as e:
-        chs.chs_lyapunov_spectrum(F.h, chs.params(0.05, 10, integrator=DP), 4, ics, None, lam, sto)
-    assert e.value.code == chs.CHS_E_UNSUPPORTED
     e64 = chs.DeviceEnsemble.empty(4, 4, 2)
     t = torch.zeros(4, dtype=torch.float64, device="cuda")
     h = torch.full((4,), 0.1, dtype=torch.float64, device="cuda")
