@@ -316,3 +316,22 @@ def test_dop853_adaptive_step_fail():
     assert e.status[0] == O.STEP_FAIL
     assert e.n_exec[0] == 0 and e.t[0] == 0.0 and e.n_rej[0] > 400
     np.testing.assert_array_equal(e.x, x0)
+
+
+def test_dop853_lyapunov_sum_vanishes_to_eighth_order():
+    """For a Hamiltonian flow the exponents sum to 0 (Liouville).  A one-step map
+    with stability function R has determinant prod R(h mu) R(-h mu) over the
+    eigenvalue pairs, 1 + O(h^9) for DOP853 (R(z) = e^z + O(z^9)) against
+    1 + O(h^5) for RK4: on FPUT chains at h = 0.05 the DOP853 sum is at the
+    rounding level while RK4's is ~1e-6."""
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+    N, n = 8, 3
+    Q, P = normal_mode_draws(3, N, n)
+    ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))
+    sums = {}
+    for integ in (O.RK4, O.DOP853):
+        lam, st = O.lyapunov(O.fput(N), O.params(0.05, 400, integrator=integ, qr_every=10), ics)
+        assert np.all(st == O.OK)
+        sums[integ] = np.abs(lam.sum(axis=0)).max()
+    assert sums[O.DOP853] < 1e-11
+    assert sums[O.RK4] > 1e-7
