@@ -206,8 +206,9 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
  * of the integrator p->integrator (classic RK4, or DOP853, the paper's DOP 8)
  * on the joint system (x, w_1..w_k, M_p):
  *   x' = f(x) (Hamilton's equations), w_j' = J(x) w_j (variational equations,
- *   Sec. Statement of need), M_p' = sum_i |f_i(x)|^p (the LD, Sec. Statement
- *   of need),
+ *   Sec. Statement of need), dM_p/d|t| = sum_i |f_i(x)|^p (the LD, Sec.
+ *   Statement of need; it grows with |t|, so a run with dt < 0 accumulates the
+ *   backward LD as a positive number),
  * the fixed-step integrators of Sec. Functionalities.
  * After each step: vectors are renormalised when p->renorm is set (the
  * fixed-step solver variant with vector normalisation, Sec. Functionalities);
@@ -256,7 +257,8 @@ typedef struct {
  * read and updated), n_rejected (running count of rejected trials, read and
  * updated).  The deviation vectors and the LD do not enter the error (their
  * stages are computed only for accepted trials).  p->dt, p->step0 and e->t_end
- * are not used (t_end must be NULL).  Supported: HENON_HEILES, HARMONIC,
+ * are not used (t_end must be NULL).  Forward in time only (t_final > t).
+ * Supported: HENON_HEILES, HARMONIC,
  * INVERTED (k <= 4), QUARTIC3 (k <= 6); FP64 vectors. */
 chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_adaptive* a,
                                   const chs_ensemble* e, double* t, double* h, double* err_last,

@@ -247,10 +247,12 @@ typedef struct {
     int d, k, ld;
     double ld_p;
     double* Hm;   /* N*N scratch */
+    double ld_sign; /* sign of the step: the LD grows with |t| */
 } o_joint;
 
 /* F(z): z = [x | w_1 | ... | w_k | L].  Variational equations: for w = (dq, dp),
- * d(dq)/dt = dp and d(dp)/dt = -Hess V(q) dq.  LD integrand: sum_i |f_i(x)|^p. */
+ * d(dq)/dt = dp and d(dp)/dt = -Hess V(q) dq.  LD: dL/dt = sgn(h) sum_i |f_i(x)|^p,
+ * so that L = int sum_i |f_i|^p d|t| grows in backward runs (h < 0) too. */
 static void o_joint_f(const o_joint* J, const double* z, double* dz)
 {
     int d = J->d, N = d / 2;
@@ -269,7 +271,7 @@ static void o_joint_f(const o_joint* J, const double* z, double* dz)
     if (J->ld) {
         double acc = 0.0;
         for (int i = 0; i < d; ++i) acc += pow(fabs(dz[i]), J->ld_p);
-        dz[d + J->k * d] = acc;
+        dz[d + J->k * d] = J->ld_sign * acc;
     }
 }
 
@@ -751,7 +753,7 @@ void o_integrate(const o_system* s, const o_params* prm, int64_t n, double* x, d
         if (status[o] != OS_OK) continue;
         o_work W = o_work_alloc(D, N);
         double* z = W.z;
-        o_joint J = {s, d, k, use_ld, prm->ld_p, W.Hm};
+        o_joint J = {s, d, k, use_ld, prm->ld_p, W.Hm, prm->dt < 0.0 ? -1.0 : 1.0};
         for (int c = 0; c < d; ++c) z[c] = x[c * n + o];
         for (int j = 0; j < k; ++j)
             for (int c = 0; c < d; ++c) z[d + j * d + c] = w[((int64_t)j * d + c) * n + o];
@@ -819,7 +821,7 @@ void o_integrate_adaptive(const o_system* s, const o_params* prm, const o_adapti
         if (status[o] != OS_OK) continue;
         o_work W = o_work_alloc(D, N);
         double* z = W.z;
-        o_joint J = {s, d, k, use_ld, prm->ld_p, W.Hm};
+        o_joint J = {s, d, k, use_ld, prm->ld_p, W.Hm, 1.0};
         for (int c = 0; c < d; ++c) z[c] = x[c * n + o];
         for (int j = 0; j < k; ++j)
             for (int c = 0; c < d; ++c) z[d + j * d + c] = w[((int64_t)j * d + c) * n + o];
@@ -1044,7 +1046,7 @@ void o_lyapunov(const o_system* s, const o_params* prm, int64_t n, const double*
         o_work Wk = o_work_alloc(D, N);
         double* z = Wk.z;
         double* S = (double*)calloc((size_t)d, sizeof(double));
-        o_joint J = {s, d, d, 0, 0.0, Wk.Hm};
+        o_joint J = {s, d, d, 0, 0.0, Wk.Hm, 1.0};
         for (int c = 0; c < d; ++c) z[c] = ics[(int64_t)c * n + o];
         for (int j = 0; j < d; ++j)
             for (int c = 0; c < d; ++c) z[d + j * d + c] = (c == j) ? 1.0 : 0.0;

@@ -145,7 +145,7 @@ __device__ __forceinline__ double stage_sum(const Slab<Sys>& sl, const int i)
 
 // Phase 1, the orbit's twelve stages from x with step h:
 //   K_s = f(x + h sum_{j<s} a_sj K_j),   xn = x + h sum_s b_s K_s,
-//   dL = h sum_s b_s g(K_s)  (g the LD integrand),
+//   dL = |h| sum_s b_s g(K_s)  (g the LD integrand; the LD grows with |t|),
 // the stage Hessians into the slab, and with ERR the error sums
 // err5_i = sum_s e5_s K_s,i and err3_i = sum_s (b_s - b3_s) K_s,i.
 template <class Sys, bool LD, bool ERR>
@@ -193,7 +193,7 @@ __device__ __forceinline__ void orbit_step(const Slab<Sys>& sl, const double* x,
             e3[i] = s3[i];
         }
     }
-    if constexpr (LD) dL = h * sL;
+    if constexpr (LD) dL = fabs(h) * sL;
 }
 
 // Phase 2, one deviation vector w = (dq, dp) through the twelve stages of

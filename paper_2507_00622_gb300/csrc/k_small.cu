@@ -173,7 +173,8 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
 #pragma unroll
         for (int c = 0; c < D; ++c) w[j][c] = fma(h6v, aw[j][c] + dw[c], w[j][c]);
     }
-    if (LD) L = fma(h6, aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
+    // the LD grows with |t|: a backward run (h < 0) accumulates a positive M_p
+    if (LD) L = fma(fabs(h6), aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
 }
 
 // The same RK4 step with the vectors advanced by the exact one-step propagator

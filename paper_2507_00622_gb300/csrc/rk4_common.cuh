@@ -53,7 +53,7 @@ __device__ __forceinline__ double ld_term(const double* f, int ld_sqrt, double p
 
 // One classic RK4 step of the orbit x and its LD accumulator L,
 //   k1 = f(x), k2 = f(x + h/2 k1), k3 = f(x + h/2 k2), k4 = f(x + h k3),
-//   x <- x + h/6 (k1 + 2 k2 + 2 k3 + k4),
+//   x <- x + h/6 (k1 + 2 k2 + 2 k3 + k4),  L <- L + |h|/6 (g1 + 2 g2 + 2 g3 + g4),
 // recording Hess V at the four stage states in H[s] (packed upper triangle).
 // LD32: the LD integrand is summed in FP32 (ld_integrand_f32).
 template <class Sys, bool LD, bool LD32 = false>
@@ -86,7 +86,8 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
     Sys::eval(xs, f, H[3], sp);
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = fma(h6, ax[c] + f[c], x[c]);
-    if (LD) L = fma(h6, aL + ld_term<D, LD32>(f, ld_sqrt, ld_p), L);
+    // the LD grows with |t|: a backward run (h < 0) accumulates a positive M_p
+    if (LD) L = fma(fabs(h6), aL + ld_term<D, LD32>(f, ld_sqrt, ld_p), L);
 }
 
 // Exact one-step propagator of RK4 on the linear variational equation

@@ -502,3 +502,21 @@ def test_quartic_bench_size_sampled_against_oracle():
     big = np.abs(r["gali"]) > 1e-6
     rel = np.abs(g[big] - r["gali"][big]) / r["gali"][big]
     assert np.median(rel) < 1e-3 and rel.max() < 5e-2
+
+
+# --------------------------------------------------------------------------
+# backward runs (h < 0): the LD grows with |t|
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("vec_fp32,integrator", [(False, chs.RK4), (True, chs.RK4), (False, chs.DOP853)])
+def test_backward_run_matches_oracle(vec_fp32, integrator):
+    g0 = _grid(1 / 8, 16, 16)
+    ics, st = O.grid_ics(*g0)
+    kw = dict(dt=-0.02, n_steps=500, k=2, ld_p=0.5, escape_r2=4.0, integrator=integrator)
+    g = gpu_run(HH, 2, ics, st, vec_fp32=vec_fp32, **kw)
+    r = oracle_run(HH, 2, ics, st, **kw)
+    ok = (st == 0) & (r["status"] == 0)
+    np.testing.assert_array_equal(g["status"], r["status"])
+    assert state_rel_err(g["x"][:, ok], r["x"][:, ok]).max() < STATE_RTOL
+    assert np.all(g["ld"][ok] > 0)
+    assert ind_err(g["ld"][ok], r["ld"][ok]).max() < (1e-6 if vec_fp32 else IND_TOL)

@@ -483,6 +483,31 @@ def test_ld_harmonic_closed_form_and_convergence():
     assert 6.0 < errs[0] / errs[1] < 10.0
 
 
+def test_backward_ld_retraces_the_orbit():
+    """A backward run (h < 0) integrates the same integrand over |t|: from
+    q = A cos t at t = 0 back to t = -2 pi the LD is the same closed form, and
+    running forward to T then backward to 0 returns to the initial state with
+    twice the forward LD (the orbit retraces itself to O(T h^4); the two LD
+    quadratures agree to the RK4 error of the non-smooth integrand)."""
+    from scipy.special import gamma
+    I = np.sqrt(np.pi) / 2 * gamma(0.75) / gamma(1.25)
+    A = 2.0
+    S = O.system(O.HARMONIC, 1)
+    n = 16000
+    prm = O.params(-2 * np.pi / n, n, n_dev=0, ld_p=0.5, sample_every=0)
+    e = O.Ensemble(S, prm, np.array([[A], [0.0]]))
+    e.integrate(prm)
+    assert abs(e.ld[0] - 8 * I * np.sqrt(A)) < 5e-6
+    H = O.henon_heiles()
+    x0 = np.array([[0.0], [0.1], [np.sqrt(0.25 - 0.01 - 0.01 + 2 * 0.001 / 3)], [0.1]])
+    f = O.Ensemble(H, O.params(0.01, 1, n_dev=1, ld_p=0.5), x0)
+    f.integrate(O.params(0.01, 2000, n_dev=1, ld_p=0.5))
+    ld_f = f.ld[0]
+    f.integrate(O.params(-0.01, 2000, n_dev=1, ld_p=0.5))
+    assert np.abs(f.x - x0).max() < 1e-9
+    assert abs(f.ld[0] - 2 * ld_f) < 1e-6 * ld_f
+
+
 def test_ld_indicators_on_synthetic_fields():
     ny, npy = 7, 9
     iy, ip = np.meshgrid(np.arange(ny), np.arange(npy), indexing="ij")
