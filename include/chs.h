@@ -338,6 +338,24 @@ chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n,
                                  const double* ics, const int32_t* ic_status,
                                  double* lambda_out, int32_t* status_out, void* stream);
 
+/* Lyapunov spectrum by periodic QR with adaptive DOP 8(5) (Sec. Functionalities:
+ * the adaptive solver with vector normalisation and the Lyapunov spectrum by
+ * QR).  As chs_lyapunov_spectrum, with every orbit and its d vectors advanced
+ * from t = 0 to a->t_final by the DOP853 pair under the step-size control of
+ * chs_integrate_adaptive (error over the d orbit components; p->dt is the first
+ * step size; p->integrator must be CHS_DOP853), the QR every p->qr_every
+ * accepted steps and at t_final, and lambda_out [d][n] = S_i / t_final.  An
+ * orbit still short of t_final after p->n_steps accepted steps, or whose step
+ * size fails (a trial whose orbit is not finite is always rejected), freezes as
+ * STEP_FAIL; non-finite exponent sums at the end give NONFINITE; both get NaN
+ * exponents.  n_steps_out and n_rejected_out [n] (nullable) receive each
+ * orbit's accepted steps and rejected trials.  Supported: FPUT (N in
+ * {4, 8, 16, 32, 64}), HENON_HEILES, HARMONIC, INVERTED. */
+chs_status chs_lyapunov_adaptive(chs_system s, const chs_params* p, const chs_adaptive* a, int64_t n,
+                                 const double* ics, const int32_t* ic_status, double* lambda_out,
+                                 int32_t* status_out, int64_t* n_steps_out, int64_t* n_rejected_out,
+                                 void* stream);
+
 /* ------------------------------------------------------------------------
  * Early-stop surrogate (a learned classifier of the final label; the method's
  * indicators stay the judge).  A 12 -> 128 -> 128 -> 128 -> 2 ReLU perceptron

@@ -104,6 +104,9 @@ def lib():
                                            C.POINTER(Adaptive), C.c_int64, P, P, P, P, P, P, P,
                                            P, P, P, P, P, C.c_int]
         L.o_dop853_tableau.argtypes = [P, P, P, P]
+        L.o_lyapunov_adaptive.argtypes = [C.POINTER(System), C.POINTER(Params),
+                                          C.POINTER(Adaptive), C.c_int64, P, P, P, P, P, P,
+                                          C.c_int]
         L.o_shell_ics.restype = C.c_int
         L.o_shell_ics.argtypes = [C.POINTER(System), C.c_int64, P, P, P]
         L.o_jacobi_sv.argtypes = [C.c_int, C.c_int, P, P]
@@ -306,3 +309,22 @@ def lyapunov(sysd: System, prm: Params, ics, ic_status=None, nthreads: int = 0):
     lib().o_lyapunov(C.byref(sysd), C.byref(prm), n, _p(ics), _p(ic_status), _p(lam), _p(st),
                      nthreads)
     return lam, st
+
+
+def lyapunov_adaptive(sysd: System, prm: Params, ics, t_final: float, rtol: float, atol: float,
+                      ic_status=None, h_max: float = 0.0, nthreads: int = 0):
+    """Lyapunov spectrum with adaptive DOP 8(5) from t = 0 to t_final (first
+    step prm.dt, at most prm.n_steps accepted steps): (lambda, status,
+    accepted steps, rejected trials)."""
+    ics = _f64(ics)
+    d = 2 * sysd.n_dof
+    n = ics.shape[1]
+    lam = np.empty((d, n))
+    st = np.empty(n, dtype=np.int32)
+    acc = np.empty(n, dtype=np.int64)
+    rej = np.empty(n, dtype=np.int64)
+    ic_status = None if ic_status is None else np.ascontiguousarray(ic_status, dtype=np.int32)
+    ad = Adaptive(t_final, rtol, atol, h_max)
+    lib().o_lyapunov_adaptive(C.byref(sysd), C.byref(prm), C.byref(ad), n, _p(ics), _p(ic_status),
+                              _p(lam), _p(st), _p(acc), _p(rej), nthreads)
+    return lam, st, acc, rej

@@ -806,6 +806,43 @@ typedef struct {
     double h_max;
 } o_adaptive;
 
+/* One accepted DOP 8(5) step of the joint state W->z (length D; the error norm
+ * over its first d components), with the controller described above.  On
+ * return *tt and *h are the new time and next step size, *err the accepted
+ * step's error; rejections are counted in *rej.  Returns OS_OK, or
+ * OS_STEP_FAIL with z and *tt unchanged. */
+static int32_t o_adaptive_step(const o_joint* J, o_work* W, int D, int d, const o_adaptive* ad,
+                               double* tt, double* h, double* err, int64_t* rej)
+{
+    double min_step = 10.0 * (nextafter(*tt, INFINITY) - *tt);
+    if (ad->h_max > 0.0 && *h > ad->h_max) *h = ad->h_max;
+    if (*h < min_step) *h = min_step;
+    int rejected = 0;
+    for (;;) {
+        if (*h < min_step) return OS_STEP_FAIL;
+        double tn = *tt + *h;
+        if (tn > ad->t_final) tn = ad->t_final;
+        double hh = tn - *tt;
+        o_dop853_step(J, W->z, W->zn, D, hh, W->K, W->zt, W->e5, W->e3);
+        double e = o_dop853_err(W->z, W->zn, W->e5, W->e3, d, hh, ad->atol, ad->rtol);
+        if (e < 1.0) {
+            double fac = (e == 0.0) ? 10.0 : 0.9 * pow(e, -1.0 / 8.0);
+            if (fac > 10.0) fac = 10.0;
+            if (rejected && fac > 1.0) fac = 1.0;
+            *h = hh * fac;
+            memcpy(W->z, W->zn, sizeof(double) * (size_t)D);
+            *tt = tn;
+            *err = e;
+            return OS_OK;
+        }
+        double fac = 0.9 * pow(e, -1.0 / 8.0);
+        if (!(fac >= 0.2)) fac = 0.2;   /* also for a non-finite err */
+        *h = hh * fac;
+        rejected = 1;
+        ++*rej;
+    }
+}
+
 void o_integrate_adaptive(const o_system* s, const o_params* prm, const o_adaptive* ad, int64_t n,
                           double* x, double* w, double* ld, const double* h0, double* dh_max,
                           int64_t* n_exec, int32_t* status, double* t, double* hs,
@@ -833,38 +870,11 @@ void o_integrate_adaptive(const o_system* s, const o_params* prm, const o_adapti
         int32_t st = OS_OK;
         int64_t done = 0;
         while (done < prm->n_steps && tt < ad->t_final) {
-            double min_step = 10.0 * (nextafter(tt, INFINITY) - tt);
-            if (ad->h_max > 0.0 && h > ad->h_max) h = ad->h_max;
-            if (h < min_step) h = min_step;
-            int rejected = 0;
-            for (;;) {
-                if (h < min_step) {
-                    st = OS_STEP_FAIL;
-                    break;
-                }
-                double tn = tt + h;
-                if (tn > ad->t_final) tn = ad->t_final;
-                double hh = tn - tt;
-                o_dop853_step(&J, z, W.zn, D, hh, W.K, W.zt, W.e5, W.e3);
-                double err = o_dop853_err(z, W.zn, W.e5, W.e3, d, hh, ad->atol, ad->rtol);
-                if (err < 1.0) {
-                    double fac = (err == 0.0) ? 10.0 : 0.9 * pow(err, -1.0 / 8.0);
-                    if (fac > 10.0) fac = 10.0;
-                    if (rejected && fac > 1.0) fac = 1.0;
-                    h = hh * fac;
-                    memcpy(z, W.zn, sizeof(double) * (size_t)D);
-                    tt = tn;
-                    el = err;
-                    if (err > em) em = err;
-                    break;
-                }
-                double fac = 0.9 * pow(err, -1.0 / 8.0);
-                if (!(fac >= 0.2)) fac = 0.2;   /* also for a non-finite err */
-                h = hh * fac;
-                rejected = 1;
-                ++rej;
-            }
+            double err = 0.0;
+            st = o_adaptive_step(&J, &W, D, d, ad, &tt, &h, &err, &rej);
             if (st != OS_OK) break;
+            el = err;
+            if (err > em) em = err;
             ++done;
             int64_t cnt = n_exec[o] + done;
             int check = prm->sample_every > 0 && cnt % prm->sample_every == 0;
@@ -1022,6 +1032,24 @@ void o_ld_indicators(int ny, int npy, const double* ld, const int32_t* status, d
 /* Lyapunov spectrum by periodic QR                                          */
 /* ------------------------------------------------------------------------ */
 
+/* Modified Gram-Schmidt on the d columns w_j of W (column j at W + j*d):
+ * W = QR with R_jj > 0, S_j += ln R_jj, W <- Q. */
+static void o_qr_accumulate(double* W, int d, double* S)
+{
+    for (int j = 0; j < d; ++j) {
+        double* wj = W + j * d;
+        for (int i = 0; i < j; ++i) {
+            double* qi = W + i * d;
+            double r = 0.0;
+            for (int c = 0; c < d; ++c) r += qi[c] * wj[c];
+            for (int c = 0; c < d; ++c) wj[c] = wj[c] - r * qi[c];
+        }
+        double rjj = o_norm(wj, d);
+        for (int c = 0; c < d; ++c) wj[c] = wj[c] / rjj;
+        S[j] += log(rjj);
+    }
+}
+
 /* d deviation vectors start as the identity basis and follow the variational
  * equations under RK4 together with the orbit.  At every step divisible by
  * qr_every, and at the last step, the matrix W of vectors (columns) is
@@ -1052,20 +1080,8 @@ void o_lyapunov(const o_system* s, const o_params* prm, int64_t n, const double*
             for (int c = 0; c < d; ++c) z[d + j * d + c] = (c == j) ? 1.0 : 0.0;
         for (int64_t sidx = 1; sidx <= prm->n_steps; ++sidx) {
             o_fixed_step(&J, prm, &Wk, D);
-            if ((prm->qr_every > 0 && sidx % prm->qr_every == 0) || sidx == prm->n_steps) {
-                for (int j = 0; j < d; ++j) {
-                    double* wj = z + d + j * d;
-                    for (int i = 0; i < j; ++i) {
-                        double* qi = z + d + i * d;
-                        double r = 0.0;
-                        for (int c = 0; c < d; ++c) r += qi[c] * wj[c];
-                        for (int c = 0; c < d; ++c) wj[c] = wj[c] - r * qi[c];
-                    }
-                    double rjj = o_norm(wj, d);
-                    for (int c = 0; c < d; ++c) wj[c] = wj[c] / rjj;
-                    S[j] += log(rjj);
-                }
-            }
+            if ((prm->qr_every > 0 && sidx % prm->qr_every == 0) || sidx == prm->n_steps)
+                o_qr_accumulate(z + d, d, S);
             if (prm->sample_every > 0 && sidx % prm->sample_every == 0 && !o_all_finite(z, D)) {
                 st = OS_NONFINITE;
                 break;
@@ -1074,6 +1090,64 @@ void o_lyapunov(const o_system* s, const o_params* prm, int64_t n, const double*
         double T = (double)prm->n_steps * prm->dt;
         for (int i = 0; i < d; ++i) lambda[(int64_t)i * n + o] = (st == OS_OK) ? S[i] / T : NAN;
         status[o] = st;
+        free(S);
+        o_work_free(&Wk);
+    }
+}
+
+/* Lyapunov spectrum by periodic QR with adaptive DOP 8(5) (Sec. Functionalities,
+ * the adaptive solver with vector normalisation and QR): as o_lyapunov, with
+ * the orbit and its d vectors advanced by o_adaptive_step from t = 0 to
+ * ad->t_final (error over the orbit components), the QR every qr_every
+ * accepted steps and at t_final, and lambda_i = S_i / t_final.  The first
+ * step guess is prm->dt.  An orbit still short of t_final after prm->n_steps
+ * accepted steps, or whose step size fails (a trial whose orbit is not finite
+ * is always rejected), freezes as STEP_FAIL; non-finite exponent sums at the
+ * end give NONFINITE; both get NaN exponents.  n_acc (optional) receives the
+ * accepted steps and n_rej (optional) the rejected trials. */
+void o_lyapunov_adaptive(const o_system* s, const o_params* prm, const o_adaptive* ad, int64_t n,
+                         const double* ics, const int32_t* ic_status, double* lambda,
+                         int32_t* status, int64_t* n_acc, int64_t* n_rej, int nthreads)
+{
+    int d = 2 * s->n_dof, N = s->n_dof;
+    int D = d + d * d;
+    int nt = o_threads(nthreads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int64_t o = 0; o < n; ++o) {
+        int32_t st = ic_status ? ic_status[o] : OS_OK;
+        int64_t done = 0, rej = 0;
+        if (st != OS_OK) {
+            status[o] = st;
+            for (int i = 0; i < d; ++i) lambda[(int64_t)i * n + o] = NAN;
+            if (n_acc) n_acc[o] = 0;
+            if (n_rej) n_rej[o] = 0;
+            continue;
+        }
+        o_work Wk = o_work_alloc(D, N);
+        double* z = Wk.z;
+        double* S = (double*)calloc((size_t)d, sizeof(double));
+        o_joint J = {s, d, d, 0, 0.0, Wk.Hm, 1.0};
+        for (int c = 0; c < d; ++c) z[c] = ics[(int64_t)c * n + o];
+        for (int j = 0; j < d; ++j)
+            for (int c = 0; c < d; ++c) z[d + j * d + c] = (c == j) ? 1.0 : 0.0;
+        double tt = 0.0, h = prm->dt, err = 0.0;
+        while (tt < ad->t_final) {
+            if (done >= prm->n_steps) {
+                st = OS_STEP_FAIL;
+                break;
+            }
+            st = o_adaptive_step(&J, &Wk, D, d, ad, &tt, &h, &err, &rej);
+            if (st != OS_OK) break;
+            ++done;
+            if ((prm->qr_every > 0 && done % prm->qr_every == 0) || tt >= ad->t_final)
+                o_qr_accumulate(z + d, d, S);
+        }
+        if (st == OS_OK && !o_all_finite(S, d)) st = OS_NONFINITE;
+        for (int i = 0; i < d; ++i) lambda[(int64_t)i * n + o] = (st == OS_OK) ? S[i] / ad->t_final : NAN;
+        status[o] = st;
+        if (n_acc) n_acc[o] = done;
+        if (n_rej) n_rej[o] = rej;
         free(S);
         o_work_free(&Wk);
     }

@@ -26,7 +26,7 @@ RK4, DOP853 = 0, 2
 
 EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_section_grid_ics",
            "chs_fput_mode_ics", "chs_shell_ics", "chs_ensemble_init", "chs_integrate_batch",
-           "chs_integrate_adaptive",
+           "chs_integrate_adaptive", "chs_lyapunov_adaptive",
            "chs_compact_work_size", "chs_integrate_compacted", "chs_integrate_compacted_static",
            "chs_indicators",
            "chs_lyapunov_spectrum", "chs_lyapunov_batch", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
@@ -98,6 +98,8 @@ def load(path: str | None = None):
                                      P, P, P]),
         "chs_lyapunov_spectrum": (C.c_int, [P, C.POINTER(Params), I64, P, P, P, P, P]),
         "chs_lyapunov_batch": (C.c_int, [C.POINTER(LyapJob), I32, P]),
+        "chs_lyapunov_adaptive": (C.c_int, [P, C.POINTER(Params), C.POINTER(Adaptive), I64, P, P, P, P,
+                                            P, P, P]),
         "chs_mlp_param_count": (C.c_size_t, []),
         "chs_mlp_features": (C.c_int, [P, I32, P, D, P, I64, P, P]),
         "chs_mlp_forward": (C.c_int, [P, P, I64, P, P, P]),
@@ -221,6 +223,13 @@ def chs_indicators(h, prm: Params, ens: Ensemble, grid_ny=0, grid_npy=0, sali=No
 def chs_lyapunov_spectrum(h, prm: Params, n, ics, ic_status, lam, status, stream=None):
     _check(load().chs_lyapunov_spectrum(h, C.byref(prm), n, _ptr(ics), _ptr(ic_status), _ptr(lam),
                                         _ptr(status), _stream(stream)))
+
+
+def chs_lyapunov_adaptive(h, prm: Params, ad: Adaptive, n, ics, ic_status, lam, status,
+                          n_steps=None, n_rejected=None, stream=None):
+    _check(load().chs_lyapunov_adaptive(h, C.byref(prm), C.byref(ad), n, _ptr(ics), _ptr(ic_status),
+                                        _ptr(lam), _ptr(status), _ptr(n_steps), _ptr(n_rejected),
+                                        _stream(stream)))
 
 
 def chs_lyapunov_batch(jobs, stream=None):

@@ -569,6 +569,33 @@ chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n, c
     return lyap_launch(s, p, n, ics, ic_status, lambda_out, status_out, as_stream(stream));
 }
 
+chs_status chs_lyapunov_adaptive(chs_system s, const chs_params* p, const chs_adaptive* a, int64_t n,
+                                 const double* ics, const int32_t* ic_status, double* lambda_out,
+                                 int32_t* status_out, int64_t* n_steps_out, int64_t* n_rejected_out,
+                                 void* stream)
+{
+    chs_status r = lyap_check(s, p, n, ics, lambda_out, status_out);
+    if (r != CHS_OK) return r;
+    if (p->integrator != CHS_DOP853) return fail(CHS_E_INVALID, "adaptive runs need integrator = CHS_DOP853");
+    if (!(p->dt > 0.0)) return fail(CHS_E_INVALID, "dt (the first step size) must be > 0");
+    if (!a) return fail(CHS_E_INVALID, "adaptive controls are NULL");
+    if (!(a->t_final > 0.0) || !isfinite(a->t_final)) return fail(CHS_E_INVALID, "t_final must be finite and > 0");
+    if (!(a->rtol >= 0.0) || !(a->atol >= 0.0) || !isfinite(a->rtol) || !isfinite(a->atol))
+        return fail(CHS_E_INVALID, "rtol and atol must be finite and >= 0");
+    if (isnan(a->h_max)) return fail(CHS_E_INVALID, "h_max must not be NaN");
+    if (n == 0) return ok();
+    const chs::StepArgs sa = step_args(p);
+    const chs::AdaptArgs ad{a->t_final, a->rtol, a->atol, a->h_max};
+    cudaStream_t st = as_stream(stream);
+    if (s->sp.model == CHS_FPUT)
+        return cuda_status(chs::launch_fput_lyap_adapt(s->sp, sa, ad, n, ics, ic_status, lambda_out, status_out,
+                                                       n_steps_out, n_rejected_out, st),
+                           "adaptive FPUT Lyapunov launch");
+    return cuda_status(chs::launch_lyap_small_adapt(s->sp, sa, ad, n, ics, ic_status, lambda_out, status_out,
+                                                    n_steps_out, n_rejected_out, st),
+                       "adaptive Lyapunov launch");
+}
+
 size_t chs_mlp_param_count(void) { return chs::mlp_param_count(); }
 
 chs_status chs_mlp_features(const double* sali_series, int32_t n_samples, const double* ld,

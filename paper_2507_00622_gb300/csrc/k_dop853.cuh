@@ -43,4 +43,14 @@ cudaError_t launch_fput_lyap_dp(const SysPar& sp, const StepArgs& a, int64_t n, 
                                 cudaStream_t st);
 cudaError_t prepare_fput_lyap_dp(int n_dof);
 
+// Lyapunov spectra with adaptive DOP 8(5) from t = 0 to ad.t_final
+// (k_fput_dp.cu for FPUT, k_dop853_adapt.cu for the 2-DOF systems); n_acc and
+// n_rej (accepted steps, rejected trials) may be null.
+cudaError_t launch_fput_lyap_adapt(const SysPar& sp, const StepArgs& a, const AdaptArgs& ad, int64_t n,
+                                   const double* ics, const int32_t* ic_status, double* lambda,
+                                   int32_t* status, int64_t* n_acc, int64_t* n_rej, cudaStream_t st);
+cudaError_t launch_lyap_small_adapt(const SysPar& sp, const StepArgs& a, const AdaptArgs& ad, int64_t n,
+                                    const double* ics, const int32_t* ic_status, double* lambda,
+                                    int32_t* status, int64_t* n_acc, int64_t* n_rej, cudaStream_t st);
+
 }  // namespace chs

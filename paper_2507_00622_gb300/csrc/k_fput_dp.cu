@@ -1,6 +1,7 @@
 // k_fput_dp.cu -- Lyapunov spectrum of the FPUT chain by periodic QR with the
-// paper's own 8th-order solver (DOP 8 with vector normalisation and QR, Sec.
-// Functionalities; FPU example of Sec. Examples), fixed step.
+// paper's own 8th-order solver (Sec. Functionalities: DOP 8 and DOP 8(5) with
+// vector normalisation and QR; FPU example of Sec. Examples), fixed step and
+// adaptive.
 //
 // RK4 has a cheap one-step propagator for the chain (k_fput.cu); DOP853 has
 // none (its propagator is a degree-12 polynomial in the stage Jacobians), and
@@ -22,6 +23,11 @@
 // that both a warp reading down a column and the QR's thread-per-column sweeps
 // are free of bank conflicts.  The QR is the modified Gram-Schmidt of the RK4
 // kernel ("dot products first"); S_j += ln R_jj, lambda_j = S_j / T.
+//
+// Adaptive runs give every orbit its own time and step size.  The error norm
+// of a trial is a sum over the orbit's 2N components, formed by every thread of
+// the orbit from a shared array in the same order; the columns of W advance
+// only for accepted trials.  A block loops until all of its orbits are done.
 #include "dop853.cuh"
 
 namespace chs {
@@ -36,11 +42,23 @@ struct FputDpCfg {
     static constexpr int R = N / L;                    // row pairs per lane
     static constexpr int CPW = 32 / L;                 // columns per warp at a time
     static constexpr int WS = D + 1;                   // padded column stride
-    // doubles per orbit: W, two stage-state buffers, 12 stage stiffness rows, scratch
-    static constexpr int PER = D * WS + 2 * D + 12 * (N + 1) + 2;
+    // doubles per orbit: W, two stage-state buffers, 12 stage stiffness rows,
+    // two error-sum rows, control words
+    static constexpr int PER = D * WS + 2 * D + 12 * (N + 1) + 2 * D + 4;
     static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
     static_assert(THREADS == 128, "one 128-thread block per orbit group");
     static_assert((G * D) % (4 * CPW) == 0, "every warp takes the same number of columns");
+};
+
+// Offsets inside an orbit's shared slab.
+template <int N>
+struct FputDpSlab {
+    using Cfg = FputDpCfg<N>;
+    static constexpr int W = 0;
+    static constexpr int XB = Cfg::D * Cfg::WS;     // [2][D]
+    static constexpr int CS = XB + 2 * Cfg::D;      // [12][N + 1]
+    static constexpr int ER = CS + 12 * (N + 1);    // [2][D] error sums
+    static constexpr int CTL = ER + 2 * Cfg::D;     // [0] red, [1] any, [2] step of phase 2, [3] advance
 };
 
 struct FputDpCoef {
@@ -58,6 +76,196 @@ __device__ __forceinline__ double fd2v(const FputDpCoef& fc, double r)
     return fma(r, fma(fc.b3, r, fc.a2), fc.k);  // V''(r)
 }
 
+// Phase 1 for component l of one orbit (every thread of the block calls it;
+// it has one barrier per stage).  Returns x_l + h sum_s b_s F_s; with ERR the
+// error sums err5 = sum_s e5_s F_s and err3 = sum_s (b_s - b3_s) F_s.
+template <int N, bool ERR>
+__device__ __forceinline__ double orbit_stages(const double xi, const double h, const int l,
+                                               double* slab, const FputDpCoef& fc, double& e5,
+                                               double& e3)
+{
+    using Sl = FputDpSlab<N>;
+    constexpr int D = 2 * N;
+    double* xb = slab + Sl::XB;
+    double* cs = slab + Sl::CS;
+    double F[12] = {};
+    double acc = 0.0, a5 = 0.0, a3 = 0.0;
+    dp::static_for<0, 12>([&](auto sc) {
+        constexpr int s = decltype(sc)::value;
+        double sum = 0.0;
+        dp::static_for<0, s>([&](auto jc) {
+            constexpr int j = decltype(jc)::value;
+            constexpr double c = dp::kA[s][j];
+            if constexpr (c != 0.0) sum = fma(c, F[j], sum);
+        });
+        double* xs = xb + (s & 1) * D;
+        xs[l] = (s == 0) ? xi : fma(h, sum, xi);
+        __syncthreads();
+        double f;
+        if (l < N) {
+            f = xs[N + l];
+        } else {
+            const int i = l - N;
+            const double qm = i > 0 ? xs[i - 1] : 0.0;
+            const double q0 = xs[i];
+            const double qp = i < N - 1 ? xs[i + 1] : 0.0;
+            f = fdv(fc, qp - q0) - fdv(fc, q0 - qm);
+        }
+        if (l <= N) {
+            const double qa = l < N ? xs[l] : 0.0;
+            const double qb = l > 0 ? xs[l - 1] : 0.0;
+            cs[s * (N + 1) + l] = fd2v(fc, qa - qb);
+        }
+        F[s] = f;
+        constexpr double cb = dp::kB[s], c5 = dp::kE5[s], c3 = dp::kB[s] - dp::kB3[s];
+        if constexpr (s == 0) {
+            acc = cb * f;
+            if constexpr (ERR) {
+                a5 = c5 * f;
+                a3 = c3 * f;
+            }
+        } else {
+            if constexpr (cb != 0.0) acc = fma(cb, f, acc);
+            if constexpr (ERR && c5 != 0.0) a5 = fma(c5, f, a5);
+            if constexpr (ERR && c3 != 0.0) a3 = fma(c3, f, a3);
+        }
+    });
+    if constexpr (ERR) {
+        e5 = a5;
+        e3 = a3;
+    }
+    return fma(h, acc, xi);
+}
+
+// Phase 2: every column of every orbit g of the block with step(g) > 0 advances
+// through the twelve stages of w' = J_s w with that step.
+template <int N, class StepOf>
+__device__ __forceinline__ void columns(double* smem, StepOf step_of)
+{
+    using Cfg = FputDpCfg<N>;
+    using Sl = FputDpSlab<N>;
+    constexpr int D = Cfg::D, G = Cfg::G, PER = Cfg::PER, L = Cfg::L, R = Cfg::R, CPW = Cfg::CPW,
+                  WS = Cfg::WS;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int seg = lane / L, r0 = lane % L;
+    for (int task = warp * CPW + seg; task < G * D; task += 4 * CPW) {
+        const int og = task / D, col = task % D;
+        double* slab = smem + og * PER;
+        const double h = step_of(og, slab);
+        // the whole warp takes part in the shuffles; columns of orbits that do
+        // not advance compute with h = 0 and are not written back
+        double* Wc = slab + col * WS;
+        const double* c_s = slab + Sl::CS;
+        double q[R], p[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            q[k] = Wc[r0 + k * L];
+            p[k] = Wc[N + r0 + k * L];
+        }
+        double Mq[12][R], Mp[12][R], aq[R], ap[R];
+        dp::static_for<0, 12>([&](auto sc) {
+            constexpr int s = decltype(sc)::value;
+            double wq[R], wp[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                double sq = 0.0, sp_ = 0.0;
+                dp::static_for<0, s>([&](auto jc) {
+                    constexpr int j = decltype(jc)::value;
+                    constexpr double c = dp::kA[s][j];
+                    if constexpr (c != 0.0) {
+                        sq = fma(c, Mq[j][k], sq);
+                        sp_ = fma(c, Mp[j][k], sp_);
+                    }
+                });
+                wq[k] = (s == 0) ? q[k] : fma(h, sq, q[k]);
+                wp[k] = (s == 0) ? p[k] : fma(h, sp_, p[k]);
+            }
+            // neighbours of row r = r0 + k L in the column (walls: 0)
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                double left = __shfl_up_sync(0xffffffffu, wq[k], 1, L);
+                double right = __shfl_down_sync(0xffffffffu, wq[k], 1, L);
+                if constexpr (R > 1) {
+                    // row blocks wrap from lane L-1 of block k-1 / lane 0 of block k+1
+                    const double prev_last = __shfl_sync(0xffffffffu, wq[k > 0 ? k - 1 : 0], L - 1, L);
+                    const double next_first = __shfl_sync(0xffffffffu, wq[k < R - 1 ? k + 1 : 0], 0, L);
+                    if (r0 == 0) left = k > 0 ? prev_last : 0.0;
+                    if (r0 == L - 1) right = k < R - 1 ? next_first : 0.0;
+                } else {
+                    if (r0 == 0) left = 0.0;
+                    if (r0 == L - 1) right = 0.0;
+                }
+                const int r = r0 + k * L;
+                const double cl = c_s[s * (N + 1) + r], cr = c_s[s * (N + 1) + r + 1];
+                Mq[s][k] = wp[k];
+                Mp[s][k] = fma(cr, right - wq[k], -cl * (wq[k] - left));
+            }
+            constexpr double cb = dp::kB[s];
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                if constexpr (s == 0) {
+                    aq[k] = cb * Mq[0][k];
+                    ap[k] = cb * Mp[0][k];
+                } else if constexpr (cb != 0.0) {
+                    aq[k] = fma(cb, Mq[s][k], aq[k]);
+                    ap[k] = fma(cb, Mp[s][k], ap[k]);
+                }
+            }
+        });
+        if (h > 0.0 || h < 0.0) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                Wc[r0 + k * L] = fma(h, aq[k], q[k]);
+                Wc[N + r0 + k * L] = fma(h, ap[k], p[k]);
+            }
+        }
+    }
+}
+
+// Modified Gram-Schmidt of the orbit's W (thread l owns column l), when `mine`
+// is set for the orbit; every thread takes part in the barriers.  S += ln R_ll.
+template <int N>
+__device__ __forceinline__ void qr_step(double* slab, const int l, const bool mine, double& S)
+{
+    using Cfg = FputDpCfg<N>;
+    using Sl = FputDpSlab<N>;
+    constexpr int D = Cfg::D, WS = Cfg::WS;
+    double* W = slab + Sl::W;
+    double* red = slab + Sl::CTL;
+    double* wl = W + l * WS;
+    double inv = 1.0;
+    for (int j = 0; j < D; ++j) {
+        const double* wj = W + j * WS;
+        double r = 0.0;
+        if (mine && l >= j) {
+            double r0a = 0.0, r1a = 0.0;
+#pragma unroll 4
+            for (int i = 0; i < D; i += 2) {
+                r0a = fma(wj[i], wl[i], r0a);
+                r1a = fma(wj[i + 1], wl[i + 1], r1a);
+            }
+            r = r0a + r1a;
+        }
+        if (mine && l == j) red[0] = r;
+        __syncthreads();
+        const double nj = red[0];
+        if (mine && l > j) {
+            const double cfac = -r / nj;
+#pragma unroll 4
+            for (int i = 0; i < D; ++i) wl[i] = fma(cfac, wj[i], wl[i]);
+        } else if (mine && l == j) {
+            S += 0.5 * log(nj);
+            inv = rsqrt(nj);
+        }
+        __syncthreads();
+    }
+    if (mine) {
+#pragma unroll 4
+        for (int i = 0; i < D; ++i) wl[i] *= inv;
+    }
+    __syncthreads();
+}
+
 template <int N>
 __global__ void __launch_bounds__(128)
 k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double* __restrict__ ics,
@@ -65,16 +273,14 @@ k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double*
                int32_t* __restrict__ status_out)
 {
     using Cfg = FputDpCfg<N>;
-    constexpr int D = Cfg::D, G = Cfg::G, PER = Cfg::PER, L = Cfg::L, R = Cfg::R, CPW = Cfg::CPW,
-                  WS = Cfg::WS;
+    using Sl = FputDpSlab<N>;
+    constexpr int D = Cfg::D, G = Cfg::G, PER = Cfg::PER, WS = Cfg::WS;
     extern __shared__ double smem[];
     const int g = threadIdx.x / D, l = threadIdx.x % D;
     const int64_t o = (int64_t)blockIdx.x * G + g;
     const bool valid = o < n;
-    double* W = smem + g * PER;
-    double* xb = W + D * WS;           // [2][D] stage states
-    double* cs = xb + 2 * D;           // [12][N + 1] stage stiffnesses
-    double* red = cs + 12 * (N + 1);   // [2] scratch
+    double* slab = smem + g * PER;
+    double* red = slab + Sl::CTL;
 
     const FputDpCoef fc = {sp.kk, 2.0 * sp.alpha, 3.0 * sp.beta, sp.alpha, sp.beta};
     int32_t st = valid ? (ic_status ? ic_status[o] : CHS_ORBIT_OK) : CHS_ORBIT_FORBIDDEN;
@@ -94,156 +300,22 @@ k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double*
     if (st != CHS_ORBIT_OK) xi = 0.0;
 
 #pragma unroll 4
-    for (int i = 0; i < D; ++i) W[l * WS + i] = (i == l) ? 1.0 : 0.0;
+    for (int i = 0; i < D; ++i) slab[Sl::W + l * WS + i] = (i == l) ? 1.0 : 0.0;
     double S = 0.0;
     __syncthreads();
 
     const double h = a.dt;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int seg = lane / L, r0 = lane % L;
     int64_t until_qr = a.qr_every;
     int64_t until = a.sample_every > 0 ? a.sample_every : -1;
     for (int64_t step = 1; step <= a.n_steps; ++step) {
-        // ---- phase 1: the orbit's twelve stages
-        double F[12];
-        double acc = 0.0;
-        dp::static_for<0, 12>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            double sum = 0.0;
-            dp::static_for<0, s>([&](auto jc) {
-                constexpr int j = decltype(jc)::value;
-                constexpr double c = dp::kA[s][j];
-                if constexpr (c != 0.0) sum = fma(c, F[j], sum);
-            });
-            double* xs = xb + (s & 1) * D;
-            xs[l] = (s == 0) ? xi : fma(h, sum, xi);
-            __syncthreads();
-            double f;
-            if (l < N) {
-                f = xs[N + l];
-            } else {
-                const int i = l - N;
-                const double qm = i > 0 ? xs[i - 1] : 0.0;
-                const double q0 = xs[i];
-                const double qp = i < N - 1 ? xs[i + 1] : 0.0;
-                f = fdv(fc, qp - q0) - fdv(fc, q0 - qm);
-            }
-            if (l <= N) {
-                const double qa = l < N ? xs[l] : 0.0;
-                const double qb = l > 0 ? xs[l - 1] : 0.0;
-                cs[s * (N + 1) + l] = fd2v(fc, qa - qb);
-            }
-            F[s] = f;
-            constexpr double cb = dp::kB[s];
-            if constexpr (s == 0)
-                acc = cb * f;
-            else if constexpr (cb != 0.0)
-                acc = fma(cb, f, acc);
-        });
-        xi = fma(h, acc, xi);
+        double e5, e3;
+        xi = orbit_stages<N, false>(xi, h, l, slab, fc, e5, e3);
         __syncthreads();  // every stage stiffness is written
-
-        // ---- phase 2: the columns of W through the twelve stages of w' = J_s w
-        for (int task = warp * CPW + seg; task < G * D; task += 4 * CPW) {
-            const int og = task / D, col = task % D;
-            double* Wc = smem + og * PER + col * WS;
-            const double* c_s = smem + og * PER + D * WS + 2 * D;
-            double q[R], p[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                q[k] = Wc[r0 + k * L];
-                p[k] = Wc[N + r0 + k * L];
-            }
-            double Mq[12][R], Mp[12][R], aq[R], ap[R];
-            dp::static_for<0, 12>([&](auto sc) {
-                constexpr int s = decltype(sc)::value;
-                double wq[R], wp[R];
-#pragma unroll
-                for (int k = 0; k < R; ++k) {
-                    double sq = 0.0, sp_ = 0.0;
-                    dp::static_for<0, s>([&](auto jc) {
-                        constexpr int j = decltype(jc)::value;
-                        constexpr double c = dp::kA[s][j];
-                        if constexpr (c != 0.0) {
-                            sq = fma(c, Mq[j][k], sq);
-                            sp_ = fma(c, Mp[j][k], sp_);
-                        }
-                    });
-                    wq[k] = (s == 0) ? q[k] : fma(h, sq, q[k]);
-                    wp[k] = (s == 0) ? p[k] : fma(h, sp_, p[k]);
-                }
-                // neighbours of row r = r0 + k L in the column (walls: 0)
-#pragma unroll
-                for (int k = 0; k < R; ++k) {
-                    double left = __shfl_up_sync(0xffffffffu, wq[k], 1, L);
-                    double right = __shfl_down_sync(0xffffffffu, wq[k], 1, L);
-                    if constexpr (R > 1) {
-                        // row blocks wrap from lane L-1 of block k-1 / lane 0 of block k+1
-                        const double prev_last = __shfl_sync(0xffffffffu, wq[k > 0 ? k - 1 : 0], L - 1, L);
-                        const double next_first = __shfl_sync(0xffffffffu, wq[k < R - 1 ? k + 1 : 0], 0, L);
-                        if (r0 == 0) left = k > 0 ? prev_last : 0.0;
-                        if (r0 == L - 1) right = k < R - 1 ? next_first : 0.0;
-                    } else {
-                        if (r0 == 0) left = 0.0;
-                        if (r0 == L - 1) right = 0.0;
-                    }
-                    const int r = r0 + k * L;
-                    const double cl = c_s[s * (N + 1) + r], cr = c_s[s * (N + 1) + r + 1];
-                    Mq[s][k] = wp[k];
-                    Mp[s][k] = fma(cr, right - wq[k], -cl * (wq[k] - left));
-                }
-                constexpr double cb = dp::kB[s];
-#pragma unroll
-                for (int k = 0; k < R; ++k) {
-                    if constexpr (s == 0) {
-                        aq[k] = cb * Mq[0][k];
-                        ap[k] = cb * Mp[0][k];
-                    } else if constexpr (cb != 0.0) {
-                        aq[k] = fma(cb, Mq[s][k], aq[k]);
-                        ap[k] = fma(cb, Mp[s][k], ap[k]);
-                    }
-                }
-            });
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                Wc[r0 + k * L] = fma(h, aq[k], q[k]);
-                Wc[N + r0 + k * L] = fma(h, ap[k], p[k]);
-            }
-        }
+        columns<N>(smem, [&](int, const double*) { return h; });
         __syncthreads();  // W complete; stage stiffnesses free
-
         if (--until_qr == 0 || step == a.n_steps) {
             until_qr = a.qr_every;
-            double* wl = W + l * WS;
-            double inv = 1.0;
-            for (int j = 0; j < D; ++j) {
-                const double* wj = W + j * WS;
-                double r = 0.0;
-                if (l >= j) {
-                    double r0a = 0.0, r1a = 0.0;
-#pragma unroll 4
-                    for (int i = 0; i < D; i += 2) {
-                        r0a = fma(wj[i], wl[i], r0a);
-                        r1a = fma(wj[i + 1], wl[i + 1], r1a);
-                    }
-                    r = r0a + r1a;
-                }
-                if (l == j) red[0] = r;
-                __syncthreads();
-                const double nj = red[0];
-                if (l > j) {
-                    const double cfac = -r / nj;
-#pragma unroll 4
-                    for (int i = 0; i < D; ++i) wl[i] = fma(cfac, wj[i], wl[i]);
-                } else if (l == j) {
-                    S += 0.5 * log(nj);
-                    inv = rsqrt(nj);
-                }
-                __syncthreads();
-            }
-#pragma unroll 4
-            for (int i = 0; i < D; ++i) wl[i] *= inv;
-            __syncthreads();
+            qr_step<N>(slab, l, true, S);
         }
         if (--until == 0) {
             until = a.sample_every;
@@ -258,13 +330,139 @@ k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double*
     }
 }
 
+// Adaptive DOP 8(5): every orbit from t = 0 to ad.t_final with its own steps.
+template <int N>
+__global__ void __launch_bounds__(128)
+k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const int64_t n,
+                  const double* __restrict__ ics, const int32_t* __restrict__ ic_status,
+                  double* __restrict__ lambda, int32_t* __restrict__ status_out,
+                  int64_t* __restrict__ n_acc, int64_t* __restrict__ n_rej)
+{
+    using Cfg = FputDpCfg<N>;
+    using Sl = FputDpSlab<N>;
+    constexpr int D = Cfg::D, G = Cfg::G, PER = Cfg::PER, WS = Cfg::WS;
+    extern __shared__ double smem[];
+    const int g = threadIdx.x / D, l = threadIdx.x % D;
+    const int64_t o = (int64_t)blockIdx.x * G + g;
+    const bool valid = o < n;
+    double* slab = smem + g * PER;
+    double* ctl = slab + Sl::CTL;
+    double* er = slab + Sl::ER;
+
+    const FputDpCoef fc = {sp.kk, 2.0 * sp.alpha, 3.0 * sp.beta, sp.alpha, sp.beta};
+    int32_t st = valid ? (ic_status ? ic_status[o] : CHS_ORBIT_OK) : CHS_ORBIT_FORBIDDEN;
+    double xi = valid ? ics[(int64_t)l * n + o] : 0.0;
+    // a non-finite initial state is never accepted: it ends as STEP_FAIL
+    if (st != CHS_ORBIT_OK) xi = 0.0;
+
+#pragma unroll 4
+    for (int i = 0; i < D; ++i) slab[Sl::W + l * WS + i] = (i == l) ? 1.0 : 0.0;
+    double S = 0.0;
+    // per-orbit control, identical in every thread of the orbit
+    double tt = 0.0, hnext = a.dt;
+    int64_t done = 0, rej = 0;
+    bool rejected = false;
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    __syncthreads();
+
+    // Every iteration is one trial of every active orbit.  An orbit's trials end
+    // once it reaches t_final, exhausts n_steps accepted steps or fails: each
+    // rejection shrinks its step by at least 0.9 until it drops below
+    // 10 ulp(t), so every orbit leaves after finitely many iterations.
+    for (;;) {
+        bool active = st == CHS_ORBIT_OK && tt < ad.t_final;
+        if (active && done >= a.n_steps) {
+            st = CHS_ORBIT_STEP_FAIL;
+            active = false;
+        }
+        double hh = 0.0, tn = tt;
+        if (active) {
+            const double min_step = 10.0 * (nextafter(tt, inf) - tt);
+            if (!rejected) {
+                if (ad.h_max > 0.0 && hnext > ad.h_max) hnext = ad.h_max;
+                if (hnext < min_step) hnext = min_step;
+            }
+            if (hnext < min_step) {
+                st = CHS_ORBIT_STEP_FAIL;
+                active = false;
+            } else {
+                tn = tt + hnext;
+                if (tn > ad.t_final) tn = ad.t_final;
+                hh = tn - tt;
+            }
+        }
+        if (!__syncthreads_or(active)) break;
+
+        double e5 = 0.0, e3 = 0.0;
+        const double xn = orbit_stages<N, true>(xi, hh, l, slab, fc, e5, e3);
+        // error norm over the orbit's components, summed in index order by
+        // every thread of the orbit
+        const double sc = ad.atol + ad.rtol * fmax(fabs(xi), fabs(xn));
+        const double q5 = e5 / sc, q3 = e3 / sc;
+        er[l] = q5 * q5;
+        er[D + l] = q3 * q3;
+        __syncthreads();
+        double E5 = 0.0, E3 = 0.0;
+        for (int i = 0; i < D; ++i) {
+            E5 += er[i];
+            E3 += er[D + i];
+        }
+        const double err = (E5 == 0.0 && E3 == 0.0) ? 0.0 : fabs(hh) * E5 / sqrt((double)D * (E5 + 0.01 * E3));
+        const bool accept = active && err < 1.0;
+        if (l == 0) ctl[2] = accept ? hh : 0.0;
+        __syncthreads();  // stage stiffnesses and phase-2 steps are in place
+
+        columns<N>(smem, [&](int, const double* sl) { return sl[Sl::CTL + 2]; });
+        if (active) {
+            const double r8 = (err > 0.0) ? 1.0 / sqrt(sqrt(sqrt(err))) : 0.0;
+            if (accept) {
+                double fac = (err == 0.0) ? 10.0 : fmin(10.0, 0.9 * r8);
+                if (rejected) fac = fmin(fac, 1.0);
+                hnext = hh * fac;
+                xi = xn;
+                tt = tn;
+                ++done;
+                rejected = false;
+            } else {
+                double fac = 0.9 * r8;
+                if (!(fac >= 0.2)) fac = 0.2;
+                hnext = hh * fac;
+                rejected = true;
+                ++rej;
+            }
+        }
+        __syncthreads();  // W complete; stage stiffnesses free
+        const bool want_qr = accept && ((a.qr_every > 0 && done % a.qr_every == 0) || tt >= ad.t_final);
+        if (__syncthreads_or(want_qr)) qr_step<N>(slab, l, want_qr, S);
+    }
+    // non-finite exponent sums give NONFINITE for the whole orbit
+    const bool bad = valid && st == CHS_ORBIT_OK && !isfinite(S);
+    if (l == 0) ctl[3] = 0.0;
+    __syncthreads();
+    if (bad) ctl[3] = 1.0;
+    __syncthreads();
+    if (valid) {
+        if (st == CHS_ORBIT_OK && ctl[3] != 0.0) st = CHS_ORBIT_NONFINITE;
+        lambda[(int64_t)l * n + o] =
+            (st == CHS_ORBIT_OK) ? S / ad.t_final : __longlong_as_double(0x7ff8000000000000LL);
+        if (l == 0) {
+            status_out[o] = st;
+            if (n_acc) n_acc[o] = done;
+            if (n_rej) n_rej[o] = rej;
+        }
+    }
+}
+
 template <int N>
 cudaError_t prepare_dp_n()
 {
     static bool done = false;  // idempotent; set before any stream capture
     if (done) return cudaSuccess;
-    const cudaError_t err = cudaFuncSetAttribute(k_fput_lyap_dp<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)FputDpCfg<N>::SMEM);
+    cudaError_t err = cudaFuncSetAttribute(k_fput_lyap_dp<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)FputDpCfg<N>::SMEM);
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(k_fput_lyap_adapt<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)FputDpCfg<N>::SMEM);
     if (err == cudaSuccess) done = true;
     return err;
 }
@@ -278,6 +476,19 @@ cudaError_t fput_dp_n(const SysPar& sp, const StepArgs& a, int64_t n, const doub
     if (err != cudaSuccess) return err;
     k_fput_lyap_dp<N><<<blocks_for(n, Cfg::G), Cfg::THREADS, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status,
                                                                              lambda, status);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t fput_adapt_n(const SysPar& sp, const StepArgs& a, const AdaptArgs& ad, int64_t n,
+                         const double* ics, const int32_t* ic_status, double* lambda,
+                         int32_t* status, int64_t* n_acc, int64_t* n_rej, cudaStream_t st)
+{
+    using Cfg = FputDpCfg<N>;
+    const cudaError_t err = prepare_dp_n<N>();
+    if (err != cudaSuccess) return err;
+    k_fput_lyap_adapt<N><<<blocks_for(n, Cfg::G), Cfg::THREADS, Cfg::SMEM, st>>>(
+        a, ad, sp, n, ics, ic_status, lambda, status, n_acc, n_rej);
     return cudaGetLastError();
 }
 
@@ -306,6 +517,21 @@ cudaError_t launch_fput_lyap_dp(const SysPar& sp, const StepArgs& a, int64_t n, 
     case 16: return fput_dp_n<16>(sp, a, n, ics, ic_status, lambda, status, st);
     case 32: return fput_dp_n<32>(sp, a, n, ics, ic_status, lambda, status, st);
     case 64: return fput_dp_n<64>(sp, a, n, ics, ic_status, lambda, status, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fput_lyap_adapt(const SysPar& sp, const StepArgs& a, const AdaptArgs& ad, int64_t n,
+                                   const double* ics, const int32_t* ic_status, double* lambda,
+                                   int32_t* status, int64_t* n_acc, int64_t* n_rej, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    switch (sp.n_dof) {
+    case 4: return fput_adapt_n<4>(sp, a, ad, n, ics, ic_status, lambda, status, n_acc, n_rej, st);
+    case 8: return fput_adapt_n<8>(sp, a, ad, n, ics, ic_status, lambda, status, n_acc, n_rej, st);
+    case 16: return fput_adapt_n<16>(sp, a, ad, n, ics, ic_status, lambda, status, n_acc, n_rej, st);
+    case 32: return fput_adapt_n<32>(sp, a, ad, n, ics, ic_status, lambda, status, n_acc, n_rej, st);
+    case 64: return fput_adapt_n<64>(sp, a, ad, n, ics, ic_status, lambda, status, n_acc, n_rej, st);
     }
     return cudaErrorInvalidValue;
 }

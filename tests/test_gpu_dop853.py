@@ -328,3 +328,60 @@ def test_adaptive_quartic_and_step_fail():
     assert np.all(f["status"][bad] == chs.ORBIT_STEP_FAIL)
     np.testing.assert_array_equal(f["x"][:, bad], ics[:, bad])
     assert np.all(f["n_exec"][bad] == 0) and np.all(f["n_rej"][bad] >= 1)
+
+
+# --------------------------------------------------------------------------
+# Lyapunov spectra with adaptive DOP 8(5)
+# --------------------------------------------------------------------------
+
+def _gpu_lyap_adaptive(model, N, ics, st, params, T, tol, sys_params=()):
+    S = chs.System(model, N, sys_params)
+    n = ics.shape[1]
+    lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+    sto = torch.empty(n, dtype=torch.int32, device="cuda")
+    acc = torch.empty(n, dtype=torch.int64, device="cuda")
+    rej = torch.empty(n, dtype=torch.int64, device="cuda")
+    chs.chs_lyapunov_adaptive(S.h, params, chs.Adaptive(T, tol, tol, 0.0), n,
+                              torch.from_numpy(np.ascontiguousarray(ics)).cuda(),
+                              None if st is None else torch.from_numpy(st).cuda(), lam, sto, acc, rej)
+    torch.cuda.synchronize()
+    return lam.cpu().numpy(), sto.cpu().numpy(), acc.cpu().numpy(), rej.cpu().numpy()
+
+
+def test_adaptive_lyapunov_hh_matches_oracle():
+    ics, st = O.grid_ics(*_grid(1 / 8, 12, 12))
+    prm = chs.params(0.01, 10**6, qr_every=10, integrator=DP)
+    g, gs, ga, gr = _gpu_lyap_adaptive(HH, 2, ics, st, prm, 20.0, 1e-10)
+    r, rs, ra, rr = O.lyapunov_adaptive(O.henon_heiles(), O.params(0.01, 10**6, qr_every=10), ics,
+                                        20.0, 1e-10, 1e-10, ic_status=st)
+    np.testing.assert_array_equal(gs, rs)
+    ok = rs == 0
+    same = ok & (ga == ra) & (gr == rr)
+    assert same.sum() >= 0.99 * ok.sum()
+    assert np.abs(g[:, same] - r[:, same]).max() < 1e-8
+    assert np.all(np.isnan(g[:, ~ok]))
+
+
+@pytest.mark.parametrize("N,n", [(4, 37), (8, 13), (16, 9), (32, 5), (64, 3)])
+def test_adaptive_lyapunov_fput_matches_oracle(N, n):
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+    Q, P = normal_mode_draws(91 + N, N, n)
+    ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))
+    st = np.zeros(n, dtype=np.int32)
+    st[-1] = chs.ORBIT_FORBIDDEN
+    T = 6.0 if N == 64 else 10.0
+    prm = chs.params(0.05, 10**6, qr_every=10, integrator=DP)
+    g, gs, ga, gr = _gpu_lyap_adaptive(chs.FPUT, N, ics, st, prm, T, 1e-9, (1.0, 0.0, 1.0))
+    r, rs, ra, rr = O.lyapunov_adaptive(O.fput(N), O.params(0.05, 10**6, qr_every=10), ics, T,
+                                        1e-9, 1e-9, ic_status=st)
+    np.testing.assert_array_equal(gs, rs)
+    ok = rs == 0
+    same = ok & (ga == ra) & (gr == rr)
+    assert same.sum() >= ok.sum() - 1
+    assert np.abs(g[:, same] - r[:, same]).max() < 1e-8
+    assert np.all(np.isnan(g[:, ~ok]))
+    # a step budget shorter than the run: STEP_FAIL with NaN exponents
+    g2, gs2, ga2, _ = _gpu_lyap_adaptive(chs.FPUT, N, ics, None,
+                                         chs.params(0.05, 3, qr_every=10, integrator=DP), T, 1e-9,
+                                         (1.0, 0.0, 1.0))
+    assert np.all(gs2 == chs.ORBIT_STEP_FAIL) and np.all(ga2 == 3) and np.all(np.isnan(g2))

@@ -335,3 +335,38 @@ def test_dop853_lyapunov_sum_vanishes_to_eighth_order():
         sums[integ] = np.abs(lam.sum(axis=0)).max()
     assert sums[O.DOP853] < 1e-11
     assert sums[O.RK4] > 1e-7
+
+
+# --------------------------------------------------------------------------
+# Lyapunov spectrum with adaptive DOP 8(5)
+# --------------------------------------------------------------------------
+
+def test_adaptive_lyapunov_inverted_oscillator_flow_spectrum():
+    """With a tight tolerance the spectrum is that of the exact flow: for
+    H = (p1^2 - q1^2)/2 + (p2^2 + q2^2)/2 and W(T) = exp(A T), the QR of W gives
+    R_11 = sqrt(cosh 2T) = 1 / R_33 and R_22 = R_44 = 1, so
+    lambda = (ln cosh 2T / 2T, 0, -ln cosh 2T / 2T, 0) in column order."""
+    S = O.system(O.INVERTED, 2)
+    T = 20.0
+    lam, st, acc, rej = O.lyapunov_adaptive(S, O.params(0.01, 10**6, qr_every=10),
+                                            np.array([[0.1], [0.2], [0.3], [-0.1]]), T, 1e-12, 1e-12)
+    l1 = (2 * T + np.log1p(np.exp(-4 * T)) - np.log(2.0)) / (2 * T)
+    np.testing.assert_allclose(lam[:, 0], [l1, 0.0, -l1, 0.0], rtol=0, atol=1e-9)
+    assert st[0] == O.OK and acc[0] > 10
+
+
+def test_adaptive_lyapunov_fput_liouville_and_fixed_step_agreement():
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+    N, n = 8, 3
+    Q, P = normal_mode_draws(3, N, n)
+    ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))
+    lam, st, acc, rej = O.lyapunov_adaptive(O.fput(N), O.params(0.05, 10**6, qr_every=10), ics,
+                                            20.0, 1e-10, 1e-10)
+    assert np.all(st == O.OK)
+    assert np.abs(lam.sum(axis=0)).max() < 1e-8
+    lf, _ = O.lyapunov(O.fput(N), O.params(0.02, 1000, qr_every=10, integrator=O.DOP853), ics)
+    assert np.abs(lam - lf).max() < 1e-8
+    # a step budget shorter than the run freezes the orbit
+    lam, st, acc, rej = O.lyapunov_adaptive(O.fput(N), O.params(0.05, 5, qr_every=10), ics,
+                                            20.0, 1e-10, 1e-10)
+    assert np.all(st == O.STEP_FAIL) and np.all(np.isnan(lam)) and np.all(acc == 5)
