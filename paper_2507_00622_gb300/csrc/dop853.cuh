@@ -183,7 +183,11 @@ __device__ __forceinline__ void orbit_step(const Slab<Sys>& sl, const double* x,
                 if constexpr (ERR && c3 != 0.0) s3[i] = fma(c3, f[i], s3[i]);
             }
         }
-        if constexpr (LD && cb != 0.0) sL = fma(cb, ld_integrand<D>(f, ld_sqrt, ld_p), sL);
+        if constexpr (LD && cb != 0.0) {
+            // p = 1/2: the stage's sum of square roots in double-float, widened once
+            const double g = ld_sqrt ? ff_to_f64(ff_sum_sqrt_abs<D>(f)) : ld_integrand<D>(f, ld_sqrt, ld_p);
+            sL = fma(cb, g, sL);
+        }
     });
 #pragma unroll
     for (int i = 0; i < D; ++i) {
@@ -293,7 +297,7 @@ __device__ __forceinline__ int32_t post_step(const double* x, double (*w)[2 * Sy
             double n2 = w[j][0] * w[j][0];
 #pragma unroll
             for (int c = 1; c < D; ++c) n2 = fma(w[j][c], w[j][c], n2);
-            const double inv = rsqrt_nr(n2);
+            const double inv = rsqrt_ff(n2);
 #pragma unroll
             for (int c = 0; c < D; ++c) w[j][c] *= inv;
         }

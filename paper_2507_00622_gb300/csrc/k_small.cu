@@ -115,6 +115,7 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
     double ax[D], xs[D], f[D], H[NH];
     VT aw[KK][D], ws[KK][D], dw[D], Hc[NH];
     double aL = 0.0;
+    FF fL{0.0f, 0.0f};  // p = 1/2: the LD sum in double-float (rk4_common.cuh)
 
     // stage 1 at (x, w)
     Sys::eval(x, f, H, sp);
@@ -134,7 +135,12 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
             ws[j][c] = fma(hhv, dw[c], w[j][c]);
         }
     }
-    if (LD) aL = ld_integrand<D>(f, ld_sqrt, ld_p);
+    if (LD) {
+        if (ld_sqrt)
+            ld_acc_sqrt<D>(fL, f, 1.0f);
+        else
+            aL = ld_integrand<D>(f, ld_sqrt, ld_p);
+    }
 
     // stages 2 and 3 at (xs, ws); the next stage input uses h/2 then h
 #pragma unroll
@@ -158,7 +164,12 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
                 ws[j][c] = fma(csv, dw[c], w[j][c]);
             }
         }
-        if (LD) aL = fma(2.0, ld_integrand<D>(f, ld_sqrt, ld_p), aL);
+        if (LD) {
+            if (ld_sqrt)
+                ld_acc_sqrt<D>(fL, f, 2.0f);
+            else
+                aL = fma(2.0, ld_integrand<D>(f, ld_sqrt, ld_p), aL);
+        }
     }
 
     // stage 4 at (xs, ws)
@@ -174,7 +185,14 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
         for (int c = 0; c < D; ++c) w[j][c] = fma(h6v, aw[j][c] + dw[c], w[j][c]);
     }
     // the LD grows with |t|: a backward run (h < 0) accumulates a positive M_p
-    if (LD) L = fma(fabs(h6), aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
+    if (LD) {
+        if (ld_sqrt) {
+            ld_acc_sqrt<D>(fL, f, 1.0f);
+            L = fma(fabs(h6), ff_to_f64(fL), L);
+        } else {
+            L = fma(fabs(h6), aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
+        }
+    }
 }
 
 // The same RK4 step with the vectors advanced by the exact one-step propagator
@@ -272,7 +290,7 @@ k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList 
                 double n2 = w[j][0] * w[j][0];
 #pragma unroll
                 for (int c = 1; c < D; ++c) n2 = fma(w[j][c], w[j][c], n2);
-                const double inv = rsqrt_nr(n2);
+                const double inv = rsqrt_ff(n2);
 #pragma unroll
                 for (int c = 0; c < D; ++c) w[j][c] *= inv;
             }

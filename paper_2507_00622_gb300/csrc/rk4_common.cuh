@@ -51,11 +51,21 @@ __device__ __forceinline__ double ld_term(const double* f, int ld_sqrt, double p
         return ld_integrand<D>(f, ld_sqrt, p);
 }
 
+// acc += w sum_i sqrt|f_i| in double-float (p = 1/2; w a power of two).
+template <int D>
+__device__ __forceinline__ void ld_acc_sqrt(FF& acc, const double* f, const float w)
+{
+#pragma unroll
+    for (int i = 0; i < D; ++i) ff_acc(acc, ff_sqrt(ff_split(fabs(f[i]))), w);
+}
+
 // One classic RK4 step of the orbit x and its LD accumulator L,
 //   k1 = f(x), k2 = f(x + h/2 k1), k3 = f(x + h/2 k2), k4 = f(x + h k3),
 //   x <- x + h/6 (k1 + 2 k2 + 2 k3 + k4),  L <- L + |h|/6 (g1 + 2 g2 + 2 g3 + g4),
 // recording Hess V at the four stage states in H[s] (packed upper triangle).
-// LD32: the LD integrand is summed in FP32 (ld_integrand_f32).
+// For p = 1/2 the weighted sum of the sixteen square roots is formed in
+// double-float arithmetic (relative error ~1e-13, off the FP64 pipe) and added
+// to L with one FP64 FMA; other exponents use pow in FP64 (LD32: in FP32).
 template <class Sys, bool LD, bool LD32 = false>
 __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const double h,
                                                   const int ld_sqrt, const double ld_p,
@@ -65,13 +75,19 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
     const double hh = 0.5 * h, h6 = h / 6.0;
     double ax[D], xs[D], f[D];
     double aL = 0.0;
+    FF fL{0.0f, 0.0f};
     Sys::eval(x, f, H[0], sp);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
         ax[c] = f[c];
         xs[c] = fma(hh, f[c], x[c]);
     }
-    if (LD) aL = ld_term<D, LD32>(f, ld_sqrt, ld_p);
+    if (LD) {
+        if (ld_sqrt)
+            ld_acc_sqrt<D>(fL, f, 1.0f);
+        else
+            aL = ld_term<D, LD32>(f, ld_sqrt, ld_p);
+    }
 #pragma unroll
     for (int s = 1; s < 3; ++s) {
         const double cs = (s == 1) ? hh : h;
@@ -81,13 +97,25 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
             ax[c] = fma(2.0, f[c], ax[c]);
             xs[c] = fma(cs, f[c], x[c]);
         }
-        if (LD) aL = fma(2.0, ld_term<D, LD32>(f, ld_sqrt, ld_p), aL);
+        if (LD) {
+            if (ld_sqrt)
+                ld_acc_sqrt<D>(fL, f, 2.0f);
+            else
+                aL = fma(2.0, ld_term<D, LD32>(f, ld_sqrt, ld_p), aL);
+        }
     }
     Sys::eval(xs, f, H[3], sp);
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = fma(h6, ax[c] + f[c], x[c]);
     // the LD grows with |t|: a backward run (h < 0) accumulates a positive M_p
-    if (LD) L = fma(fabs(h6), aL + ld_term<D, LD32>(f, ld_sqrt, ld_p), L);
+    if (LD) {
+        if (ld_sqrt) {
+            ld_acc_sqrt<D>(fL, f, 1.0f);
+            L = fma(fabs(h6), ff_to_f64(fL), L);
+        } else {
+            L = fma(fabs(h6), aL + ld_term<D, LD32>(f, ld_sqrt, ld_p), L);
+        }
+    }
 }
 
 // Exact one-step propagator of RK4 on the linear variational equation
