@@ -63,9 +63,11 @@ __device__ __forceinline__ void ld_acc_sqrt(FF& acc, const double* f, const floa
 //   k1 = f(x), k2 = f(x + h/2 k1), k3 = f(x + h/2 k2), k4 = f(x + h k3),
 //   x <- x + h/6 (k1 + 2 k2 + 2 k3 + k4),  L <- L + |h|/6 (g1 + 2 g2 + 2 g3 + g4),
 // recording Hess V at the four stage states in H[s] (packed upper triangle).
-// For p = 1/2 the weighted sum of the sixteen square roots is formed in
-// double-float arithmetic (relative error ~1e-13, off the FP64 pipe) and added
-// to L with one FP64 FMA; other exponents use pow in FP64 (LD32: in FP32).
+// FP64 vectors, p = 1/2: the weighted sum of the sixteen square roots is formed
+// in double-float arithmetic (relative error ~1e-13, off the FP64 pipe) and
+// added to L with one FP64 FMA.  LD32 (the FP32-frame mode, bound by
+// instruction issue rather than by the FP64 pipe): the integrand is summed in
+// FP32 (ld_integrand_f32).  Other exponents use pow.
 template <class Sys, bool LD, bool LD32 = false>
 __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const double h,
                                                   const int ld_sqrt, const double ld_p,
@@ -82,8 +84,9 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
         ax[c] = f[c];
         xs[c] = fma(hh, f[c], x[c]);
     }
+    const bool ff = !LD32 && ld_sqrt;
     if (LD) {
-        if (ld_sqrt)
+        if (ff)
             ld_acc_sqrt<D>(fL, f, 1.0f);
         else
             aL = ld_term<D, LD32>(f, ld_sqrt, ld_p);
@@ -98,7 +101,7 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
             xs[c] = fma(cs, f[c], x[c]);
         }
         if (LD) {
-            if (ld_sqrt)
+            if (ff)
                 ld_acc_sqrt<D>(fL, f, 2.0f);
             else
                 aL = fma(2.0, ld_term<D, LD32>(f, ld_sqrt, ld_p), aL);
@@ -109,7 +112,7 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
     for (int c = 0; c < D; ++c) x[c] = fma(h6, ax[c] + f[c], x[c]);
     // the LD grows with |t|: a backward run (h < 0) accumulates a positive M_p
     if (LD) {
-        if (ld_sqrt) {
+        if (ff) {
             ld_acc_sqrt<D>(fL, f, 1.0f);
             L = fma(fabs(h6), ff_to_f64(fL), L);
         } else {
