@@ -180,50 +180,21 @@ __device__ __forceinline__ FF ff_sum_sqrt_abs(const double* f)
     return acc;
 }
 
-// 1 / sqrt(hi + lo) for 1e-30 <= hi <= 1e30, relative error ~2^-43, with one
-// FP64 addition: y ~ 1/sqrt(hi) from the SFU, e = 1 - (hi + lo) y^2 in
-// double-float (hi y = p + p_lo exactly by an FMA), result y + y e / 2.
-__device__ __forceinline__ double rsqrt_ff(FF a)
+// 1 / sqrt(a) for a > 0 in the FP32 exponent range, relative error ~2^-43, with
+// one FP64 addition: y ~ 1/sqrt(hi) from the SFU, e = 1 - a y^2 in double-float
+// (hi y = p + p_lo exactly by an FMA), result y + y e / 2.  Falls back to the
+// library rsqrt outside that range.
+__device__ __forceinline__ double rsqrt_ff(double a)
 {
-    const float y = rsqrt_approx_f32(a.hi);
-    const float p = a.hi * y;
-    const float p_lo = fmaf(a.hi, y, -p);
+    const int hi32 = __double2hiint(a);
+    if (!in_f32_range(hi32) || hi32 >= ((1023 + 126) << 20)) return rsqrt(a);
+    const FF x = ff_split(a);
+    const float y = rsqrt_approx_f32(x.hi);
+    const float p = x.hi * y;
+    const float p_lo = fmaf(x.hi, y, -p);
     const float q = fmaf(-p, y, 1.0f);
-    const float e = fmaf(-fmaf(a.lo, y, p_lo), y, q);
+    const float e = fmaf(-fmaf(x.lo, y, p_lo), y, q);
     return f32_to_f64_bits(y) + f32_to_f64_signed(0.5f * y * e);
-}
-
-// sum_c w_c^2 in double-float: each |w_c| split into hi + lo, hi^2 formed
-// exactly as p + e by an FMA, plus 2 hi lo; the terms summed by two-sum.
-template <int D>
-__device__ __forceinline__ FF ff_sumsq(const double* w)
-{
-    FF acc{0.0f, 0.0f};
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-        const FF x = ff_split(fabs(w[c]));
-        const float p = x.hi * x.hi;
-        const float e = fmaf(x.hi, x.hi, -p);
-        ff_acc(acc, FF{p, fmaf(2.0f * x.hi, x.lo, e)}, 1.0f);
-    }
-    return acc;
-}
-
-// 1 / sqrt(|w|^2) of a vector for its renormalisation: the squared norm in
-// double-float and rsqrt_ff, one FP64 addition in all.  Only the scale factor
-// is approximate (~2^-43): the scaled vector keeps its direction exactly as an
-// FP64 scaling would.  Squared norms outside [1e-30, 1e30] take the FP64 route.
-template <int D>
-__device__ __forceinline__ double inv_norm_ff(const double* w)
-{
-    const FF a = ff_sumsq<D>(w);
-    if (!(a.hi >= 1e-30f && a.hi <= 1e30f)) {
-        double n2 = w[0] * w[0];
-#pragma unroll
-        for (int c = 1; c < D; ++c) n2 = fma(w[c], w[c], n2);
-        return rsqrt(n2);
-    }
-    return rsqrt_ff(a);
 }
 
 }  // namespace chs

@@ -287,7 +287,10 @@ k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList 
         if (a.renorm) {
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                const double inv = inv_norm_ff<D>(w[j]);
+                double n2 = w[j][0] * w[j][0];
+#pragma unroll
+                for (int c = 1; c < D; ++c) n2 = fma(w[j][c], w[j][c], n2);
+                const double inv = rsqrt_ff(n2);
 #pragma unroll
                 for (int c = 0; c < D; ++c) w[j][c] *= inv;
             }
