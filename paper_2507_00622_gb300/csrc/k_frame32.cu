@@ -113,6 +113,57 @@ k_init_f32(const SysPar sp, const uint64_t seed, const double* __restrict__ ics,
     for (int p = 0; p < K * (K + 1) / 2; ++p) wg[(K * D + p) * n + o] = (float)R[p];
 }
 
+// Hess V of each system (as in systems.cuh) in FP32 from the FP32-rounded stage
+// positions: the frame is propagated in FP32 anyway, so forming the Hessian in
+// FP64 and rounding it would spend FP64 instructions for the same FP32 accuracy.
+template <class Sys>
+struct Hess32;
+
+template <>
+struct Hess32<SysHenonHeiles> {
+    __device__ __forceinline__ static void eval(const float* q, float* H, const SysPar&)
+    {
+        H[0] = fmaf(2.0f, q[1], 1.0f);
+        H[1] = 2.0f * q[0];
+        H[2] = fmaf(-2.0f, q[1], 1.0f);
+    }
+};
+
+template <>
+struct Hess32<SysHarmonic> {
+    __device__ __forceinline__ static void eval(const float*, float* H, const SysPar&)
+    {
+        H[0] = 1.0f;
+        H[1] = 0.0f;
+        H[2] = 1.0f;
+    }
+};
+
+template <>
+struct Hess32<SysInverted> {
+    __device__ __forceinline__ static void eval(const float*, float* H, const SysPar&)
+    {
+        H[0] = -1.0f;
+        H[1] = 0.0f;
+        H[2] = 1.0f;
+    }
+};
+
+template <>
+struct Hess32<SysQuartic3> {
+    __device__ __forceinline__ static void eval(const float* q, float* H, const SysPar& sp)
+    {
+        const float e2 = (float)(2.0 * sp.eps), e4 = (float)(4.0 * sp.eps);
+        const float s0 = q[0] * q[0], s1 = q[1] * q[1], s2 = q[2] * q[2];
+        H[hidx<3>(0, 0)] = fmaf(e2, s1 + s2, 1.0f);
+        H[hidx<3>(1, 1)] = fmaf(e2, s0 + s2, 1.0f);
+        H[hidx<3>(2, 2)] = fmaf(e2, s0 + s1, 1.0f);
+        H[hidx<3>(0, 1)] = e4 * q[0] * q[1];
+        H[hidx<3>(0, 2)] = e4 * q[0] * q[2];
+        H[hidx<3>(1, 2)] = e4 * q[1] * q[2];
+    }
+};
+
 template <class Sys, int K, bool LD, bool LIST>
 __global__ void __launch_bounds__(kSmallBlock)
 k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
@@ -151,13 +202,10 @@ k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitL
     int64_t s = 0;
     while (s < todo) {
         ++s;
-        double H[4][NH];
-        rk4_state_capture<Sys, LD, true>(x, L, a.dt, a.ld_sqrt, a.ld_p, sp, H);
-        float Hf[4][NH];
+        float qf[4][N], Hf[4][NH];
+        rk4_state_positions<Sys, LD, true>(x, L, a.dt, a.ld_sqrt, a.ld_p, sp, qf);
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-            for (int i = 0; i < NH; ++i) Hf[q][i] = f32_from_f64(H[q][i]);
+        for (int q = 0; q < 4; ++q) Hess32<Sys>::eval(qf[q], Hf[q], sp);
         PhiBlocks<N, float> P;
         phi_build<N, NH, float>(Hf, a.dt, P);
 #pragma unroll

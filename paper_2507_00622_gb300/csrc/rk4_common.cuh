@@ -62,23 +62,24 @@ __device__ __forceinline__ void ld_acc_sqrt(FF& acc, const double* f, const floa
 // One classic RK4 step of the orbit x and its LD accumulator L,
 //   k1 = f(x), k2 = f(x + h/2 k1), k3 = f(x + h/2 k2), k4 = f(x + h k3),
 //   x <- x + h/6 (k1 + 2 k2 + 2 k3 + k4),  L <- L + |h|/6 (g1 + 2 g2 + 2 g3 + g4),
-// recording Hess V at the four stage states in H[s] (packed upper triangle).
+// handing each stage s its state xs and Hess V(xs) (packed upper triangle) as
+// rec(s, xs, H); a recorder that ignores H leaves its arithmetic unused.
 // FP64 vectors, p = 1/2: the weighted sum of the sixteen square roots is formed
 // in double-float arithmetic (relative error ~1e-13, off the FP64 pipe) and
 // added to L with one FP64 FMA.  LD32 (the FP32-frame mode, bound by
 // instruction issue rather than by the FP64 pipe): the integrand is summed in
 // FP32 (ld_integrand_f32).  Other exponents use pow.
-template <class Sys, bool LD, bool LD32 = false>
-__device__ __forceinline__ void rk4_state_capture(double* x, double& L, const double h,
-                                                  const int ld_sqrt, const double ld_p,
-                                                  const SysPar& sp, double (*H)[Sys::NH])
+template <class Sys, bool LD, bool LD32, class Rec>
+__device__ __forceinline__ void rk4_stages(double* x, double& L, const double h, const int ld_sqrt,
+                                           const double ld_p, const SysPar& sp, Rec&& rec)
 {
     constexpr int D = 2 * Sys::N;
     const double hh = 0.5 * h, h6 = h / 6.0;
-    double ax[D], xs[D], f[D];
+    double ax[D], xs[D], f[D], Hs[Sys::NH];
     double aL = 0.0;
     FF fL{0.0f, 0.0f};
-    Sys::eval(x, f, H[0], sp);
+    Sys::eval(x, f, Hs, sp);
+    rec(0, x, Hs);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
         ax[c] = f[c];
@@ -94,7 +95,8 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
 #pragma unroll
     for (int s = 1; s < 3; ++s) {
         const double cs = (s == 1) ? hh : h;
-        Sys::eval(xs, f, H[s], sp);
+        Sys::eval(xs, f, Hs, sp);
+        rec(s, xs, Hs);
 #pragma unroll
         for (int c = 0; c < D; ++c) {
             ax[c] = fma(2.0, f[c], ax[c]);
@@ -107,7 +109,8 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
                 aL = fma(2.0, ld_term<D, LD32>(f, ld_sqrt, ld_p), aL);
         }
     }
-    Sys::eval(xs, f, H[3], sp);
+    Sys::eval(xs, f, Hs, sp);
+    rec(3, xs, Hs);
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = fma(h6, ax[c] + f[c], x[c]);
     // the LD grows with |t|: a backward run (h < 0) accumulates a positive M_p
@@ -119,6 +122,31 @@ __device__ __forceinline__ void rk4_state_capture(double* x, double& L, const do
             L = fma(fabs(h6), aL + ld_term<D, LD32>(f, ld_sqrt, ld_p), L);
         }
     }
+}
+
+// The RK4 step recording Hess V at the four stage states in H[s].
+template <class Sys, bool LD, bool LD32 = false>
+__device__ __forceinline__ void rk4_state_capture(double* x, double& L, const double h,
+                                                  const int ld_sqrt, const double ld_p,
+                                                  const SysPar& sp, double (*H)[Sys::NH])
+{
+    rk4_stages<Sys, LD, LD32>(x, L, h, ld_sqrt, ld_p, sp, [&](int s, const double*, const double* Hs) {
+#pragma unroll
+        for (int i = 0; i < Sys::NH; ++i) H[s][i] = Hs[i];
+    });
+}
+
+// The RK4 step recording the stage positions q rounded to FP32 (integer pipe)
+// in qf[s]; the FP64 Hessians are not formed.
+template <class Sys, bool LD, bool LD32 = false>
+__device__ __forceinline__ void rk4_state_positions(double* x, double& L, const double h,
+                                                    const int ld_sqrt, const double ld_p,
+                                                    const SysPar& sp, float (*qf)[Sys::N])
+{
+    rk4_stages<Sys, LD, LD32>(x, L, h, ld_sqrt, ld_p, sp, [&](int s, const double* xs, const double*) {
+#pragma unroll
+        for (int i = 0; i < Sys::N; ++i) qf[s][i] = f32_from_f64(xs[i]);
+    });
 }
 
 // Exact one-step propagator of RK4 on the linear variational equation
