@@ -613,9 +613,14 @@ def run_quartic(args):
     step = 0
     stream = torch.cuda.current_stream()
 
+    queue = torch.empty(1, dtype=torch.int64, device="cuda")
+
     def one():
         nonlocal step
-        chs.chs_integrate_compacted(S.h, chs.params(0.01, args.chunk, step0=step, **kw), abi, 500, work)
+        if args.persistent:
+            chs.chs_integrate_persistent(S.h, chs.params(0.01, args.chunk, step0=step, **kw), abi, queue)
+        else:
+            chs.chs_integrate_compacted(S.h, chs.params(0.01, args.chunk, step0=step, **kw), abi, 500, work)
         chs.chs_indicators(S.h, chs.params(0.01, 0, **kw), abi, sali=sali, gali=gali)
         step += args.chunk
 
@@ -638,6 +643,8 @@ def run_quartic(args):
                       "dtype": "f64 orbit + f32 frame", "data": "synthetic",
                       "config": {"workload": "quartic3_eps0.1_shellE1-10_k6_fp32frame_gali2-6",
                                  "n_orbits": n, "rk4_steps_per_bench_step": args.chunk,
+                                 "launch": "persistent work queue" if args.persistent
+                                           else "compacted 500-step chunks (CUDA graph)",
                                  "t_window": [args.warmup * args.chunk * 0.01, step * 0.01],
                                  "early_exited": int((st == chs.ORBIT_EARLY_CHAOTIC).sum())}}))
     return 0
@@ -660,6 +667,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--workload", choices=["grid", "fput", "classify", "quartic"], default="grid")
     ap.add_argument("--quartic-orbits", type=int, default=4_194_304)
+    ap.add_argument("--persistent", action="store_true",
+                    help="quartic workload: one persistent work-queue launch per bench step")
     ap.add_argument("--final-steps", type=int, default=1_000_000)
     ap.add_argument("--confidence", type=float, default=None)
     ap.add_argument("--classify-side", type=int, default=256,

@@ -264,6 +264,18 @@ chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_a
                                   const chs_ensemble* e, double* t, double* h, double* err_last,
                                   double* err_max, int64_t* n_rejected, void* stream);
 
+/* The same integration as chs_integrate_batch (identical results, bit for bit),
+ * run by a persistent grid (every SM filled to the kernel's occupancy) whose
+ * threads take orbit indices from a work queue, one orbit after another: a
+ * thread whose orbit stops early -- its t_end, early exit, escape or any other
+ * freeze -- takes the next orbit at once, so orbits of uneven length leave no
+ * lane idle until the queue runs dry, in one launch.  `work` is caller-owned
+ * device scratch of at least 8 bytes, 8-byte aligned (the queue counter; reset
+ * by the call).  Calls that share a work buffer and overlap on the GPU race.
+ * Supported: as chs_integrate_batch, both vector precisions and integrators. */
+chs_status chs_integrate_persistent(chs_system s, const chs_params* p, const chs_ensemble* e,
+                                    void* work, size_t work_bytes, void* stream);
+
 /* Bytes of device scratch that chs_integrate_compacted needs for n orbits. */
 size_t chs_compact_work_size(int64_t n_orbits);
 

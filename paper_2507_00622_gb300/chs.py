@@ -26,7 +26,7 @@ RK4, DOP853 = 0, 2
 
 EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_section_grid_ics",
            "chs_fput_mode_ics", "chs_shell_ics", "chs_ensemble_init", "chs_integrate_batch",
-           "chs_integrate_adaptive", "chs_lyapunov_adaptive",
+           "chs_integrate_adaptive", "chs_lyapunov_adaptive", "chs_integrate_persistent",
            "chs_compact_work_size", "chs_integrate_compacted", "chs_integrate_compacted_static",
            "chs_indicators",
            "chs_lyapunov_spectrum", "chs_lyapunov_batch", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
@@ -90,6 +90,8 @@ def load(path: str | None = None):
                                               C.c_size_t, P]),
         "chs_integrate_compacted_static": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble),
                                                      I32, P]),
+        "chs_integrate_persistent": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), P,
+                                               C.c_size_t, P]),
         "chs_ensemble_init": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), P, P, P, P]),
         "chs_integrate_batch": (C.c_int, [P, C.POINTER(Params), C.POINTER(Ensemble), P]),
         "chs_integrate_adaptive": (C.c_int, [P, C.POINTER(Params), C.POINTER(Adaptive),
@@ -196,6 +198,11 @@ def chs_integrate_compacted_static(h, prm: Params, ens: Ensemble, chunk_steps: i
     device scratch (see include/chs.h); at most 1,048,576 orbits."""
     _check(load().chs_integrate_compacted_static(h, C.byref(prm), C.byref(ens), chunk_steps,
                                                  _stream(stream)))
+
+
+def chs_integrate_persistent(h, prm: Params, ens: Ensemble, work, stream=None):
+    _check(load().chs_integrate_persistent(h, C.byref(prm), C.byref(ens), _ptr(work),
+                                           work.numel() * work.element_size(), _stream(stream)))
 
 
 def chs_ensemble_init(h, prm: Params, ens: Ensemble, ics, ic_status=None, w_in=None, stream=None):

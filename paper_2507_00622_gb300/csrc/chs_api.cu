@@ -339,6 +339,25 @@ chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_a
                        "adaptive integrate launch");
 }
 
+chs_status chs_integrate_persistent(chs_system s, const chs_params* p, const chs_ensemble* e, void* work,
+                                    size_t work_bytes, void* stream)
+{
+    chs_status r = check_handle(s);
+    if (r != CHS_OK) return r;
+    if (!chs::small_model(s->sp.model))
+        return fail(CHS_E_UNSUPPORTED, "integration is implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
+    if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ensemble(e, p)) != CHS_OK) return r;
+    if (!work || ((uintptr_t)work & 7u)) return fail(CHS_E_INVALID, "work must be an 8-byte aligned device buffer");
+    if (work_bytes < 8) return fail(CHS_E_SIZE, "work must hold at least 8 bytes");
+    if (e->n_orbits == 0 || p->n_steps == 0) return ok();
+    cudaStream_t st = as_stream(stream);
+    cudaError_t ce = cudaMemsetAsync(work, 0, sizeof(unsigned long long), st);
+    if (ce != cudaSuccess) return cuda_status(ce, "queue reset");
+    const chs::OrbitList ol{nullptr, nullptr, nullptr, nullptr, static_cast<unsigned long long*>(work)};
+    return cuda_status(launch_selected(s->sp, p, step_args(p), ens_ptrs(e), &ol, st), "persistent integrate launch");
+}
+
 size_t chs_compact_work_size(int64_t n_orbits)
 {
     if (n_orbits < 0) return 0;

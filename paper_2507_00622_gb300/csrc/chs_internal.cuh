@@ -31,14 +31,25 @@ struct EnsPtrs {
     const int64_t* t_end;  // optional per-orbit end step
 };
 
-// Optional orbit list for compacted runs: thread t integrates orbit list[t] for
-// t < *count and appends the orbits still running to next / *next_count.
+// How the one-orbit-per-thread integrate kernels pick their orbits.
+//   compacted list (list set): thread t integrates orbit list[t] for
+//     t < *count and appends the orbits still running to next / *next_count;
+//   work queue (queue set): a persistent grid whose threads take orbit indices
+//     from the counter *queue (starting at 0) until they run past n.
 struct OrbitList {
     const int32_t* list;
     const int32_t* count;
     int32_t* next;
     int32_t* next_count;
+    unsigned long long* queue;
 };
+
+enum { kModeAll = 0, kModeList = 1, kModeQueue = 2 };
+
+__device__ __forceinline__ int integ_mode(const OrbitList& ol)
+{
+    return ol.queue ? kModeQueue : (ol.list ? kModeList : kModeAll);
+}
 
 // Integration controls, validated on the host.
 struct StepArgs {
@@ -67,6 +78,8 @@ cudaError_t launch_init(const SysPar& sp, int k, int vec_fp32, int renorm, uint6
 cudaError_t launch_integrate(const SysPar& sp, int k, int vec_fp32, bool ld, const StepArgs& a,
                              const EnsPtrs& e, const OrbitList* ol, cudaStream_t st);
 cudaError_t launch_list_init(const EnsPtrs& e, int32_t* list, int32_t* count, cudaStream_t st);
+// The integrate launch of the persistent work-queue mode (ol->queue set) runs
+// a grid of persistent_blocks(); the caller zeroes *ol->queue first.
 cudaError_t launch_shell_ics(const SysPar& sp, int64_t n, const double* dirs, const double* E,
                              double* ics, cudaStream_t st);
 cudaError_t launch_indicators(const SysPar& sp, int k, int vec_fp32, double sali_threshold,
@@ -127,6 +140,32 @@ __device__ __forceinline__ void list_append(const OrbitList& ol, bool keep, int3
 inline unsigned blocks_for(int64_t n, int per_block)
 {
     return (unsigned)((n + per_block - 1) / per_block);
+}
+
+// Next orbit index from a work-queue counter, one atomic per group of converged
+// lanes.
+__device__ __forceinline__ int64_t queue_next(unsigned long long* q)
+{
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(q, (unsigned long long)__popc(act));
+    base = __shfl_sync(act, base, leader);
+    return (int64_t)(base + (unsigned long long)__popc(act & ((1u << lane) - 1u)));
+}
+
+// Blocks of a persistent launch: every SM filled to the kernel's occupancy.
+template <class Kernel>
+inline cudaError_t persistent_blocks(Kernel kernel, int threads, size_t smem, unsigned* blocks)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    *blocks = (unsigned)(sms * (per_sm > 0 ? per_sm : 1));
+    return cudaSuccess;
 }
 
 }  // namespace chs

@@ -10,26 +10,16 @@ namespace {
 
 using dp::kBlock;
 
-// One orbit per thread.  With ol.list set, thread t takes orbit list[t]
-// (t < *count) and appends the orbit to the next list when it is still running
-// after the call.
+// Advances orbit o (status OK) by the call's steps; returns true when it is
+// still running afterwards.
 template <class Sys, int K, bool LD>
-__global__ void __launch_bounds__(kBlock)
-k_integrate_dp(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
+__device__ __forceinline__ bool integrate_orbit_dp(const int64_t o, const StepArgs& a,
+                                                   const SysPar& sp, const EnsPtrs& e,
+                                                   const dp::Slab<Sys>& sl)
 {
     constexpr int N = Sys::N, D = 2 * N;
     constexpr int KK = K > 0 ? K : 1;
-    const dp::Slab<Sys> sl = dp::my_slab<Sys>();
     const int64_t n = e.n;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool listed = ol.list != nullptr;
-    int64_t o = t;
-    if (listed) {
-        if (t >= *ol.count) return;
-        o = ol.list[t];
-    }
-    if (o >= n) return;
-    if (e.status[o] != CHS_ORBIT_OK) return;
 
     double* wg = static_cast<double*>(e.w);
     double x[D], w[KK][D];
@@ -77,7 +67,34 @@ k_integrate_dp(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitLi
     e.dh_max[o] = dhm;
     e.n_exec[o] = exec0 + s;
     e.status[o] = st;
-    if (listed) list_append(ol, st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]), (int32_t)o);
+    return st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]);
+}
+
+// One orbit per thread, with the orbit-selection modes of k_integrate
+// (k_small.cu) chosen at run time from ol.
+template <class Sys, int K, bool LD>
+__global__ void __launch_bounds__(kBlock)
+k_integrate_dp(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
+{
+    const dp::Slab<Sys> sl = dp::my_slab<Sys>();
+    const int mode = integ_mode(ol);
+    if (mode == kModeQueue) {
+        for (;;) {
+            const int64_t o = queue_next(ol.queue);
+            if (o >= e.n) return;
+            if (e.status[o] == CHS_ORBIT_OK) integrate_orbit_dp<Sys, K, LD>(o, a, sp, e, sl);
+        }
+    }
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t o = t;
+    if (mode == kModeList) {
+        if (t >= *ol.count) return;
+        o = ol.list[t];
+    }
+    if (o >= e.n) return;
+    if (e.status[o] != CHS_ORBIT_OK) return;
+    const bool keep = integrate_orbit_dp<Sys, K, LD>(o, a, sp, e, sl);
+    if (mode == kModeList) list_append(ol, keep, (int32_t)o);
 }
 
 // Lyapunov spectrum of the 2-DOF systems: W (4 x 4) in registers.
@@ -163,10 +180,15 @@ cudaError_t fixed_sys(int k, bool ld, const StepArgs& a, const SysPar& sp, const
     constexpr size_t sm = dp::slab_bytes<Sys>();
     return dp::with_k<Sys>(k, [&](auto kc) {
         constexpr int K = decltype(kc)::value;
-        if (ld)
-            k_integrate_dp<Sys, K, true><<<g, kBlock, sm, st>>>(a, sp, e, l);
-        else
-            k_integrate_dp<Sys, K, false><<<g, kBlock, sm, st>>>(a, sp, e, l);
+        auto kern = ld ? k_integrate_dp<Sys, K, true> : k_integrate_dp<Sys, K, false>;
+        unsigned grid = g;
+        if (l.queue) {
+            static unsigned pg[2] = {0, 0};  // persistent grid per LD variant, found once
+            unsigned& p = pg[ld ? 1 : 0];
+            if (!p && persistent_blocks(kern, kBlock, sm, &p) != cudaSuccess) p = 0;
+            if (p) grid = p;
+        }
+        kern<<<grid, kBlock, sm, st>>>(a, sp, e, l);
     });
 }
 

@@ -164,20 +164,14 @@ struct Hess32<SysQuartic3> {
     }
 };
 
-template <class Sys, int K, bool LD, bool LIST>
-__global__ void __launch_bounds__(kSmallBlock)
-k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
+// Advances orbit o (status OK) by the call's steps; returns true when it is
+// still running afterwards.
+template <class Sys, int K, bool LD>
+__device__ __forceinline__ bool integrate_orbit_f32(const int64_t o, const StepArgs& a,
+                                                    const SysPar& sp, const EnsPtrs& e)
 {
     constexpr int N = Sys::N, D = 2 * N, NH = Sys::NH, NR = K * (K + 1) / 2;
     const int64_t n = e.n;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t o = t;
-    if (LIST) {
-        if (t >= *ol.count) return;
-        o = ol.list[t];
-    }
-    if (o >= n) return;
-    if (e.status[o] != CHS_ORBIT_OK) return;
 
     float* wg = static_cast<float*>(e.w);
     double x[D];
@@ -298,7 +292,32 @@ k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitL
     e.dh_max[o] = dhm;
     e.n_exec[o] = exec0 + s;
     e.status[o] = st;
-    if (LIST) list_append(ol, st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]), (int32_t)o);
+    return st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]);
+}
+
+// One thread per orbit; the orbit-selection modes of k_integrate (k_small.cu).
+template <class Sys, int K, bool LD, int MODE>
+__global__ void __launch_bounds__(kSmallBlock)
+k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
+{
+    if constexpr (MODE == kModeQueue) {
+        for (;;) {
+            const int64_t o = queue_next(ol.queue);
+            if (o >= e.n) return;
+            if (e.status[o] == CHS_ORBIT_OK) integrate_orbit_f32<Sys, K, LD>(o, a, sp, e);
+        }
+    } else {
+        const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        int64_t o = t;
+        if (MODE == kModeList) {
+            if (t >= *ol.count) return;
+            o = ol.list[t];
+        }
+        if (o >= e.n) return;
+        if (e.status[o] != CHS_ORBIT_OK) return;
+        const bool keep = integrate_orbit_f32<Sys, K, LD>(o, a, sp, e);
+        if (MODE == kModeList) list_append(ol, keep, (int32_t)o);
+    }
 }
 
 // SALI, GALI_m and labels from the triangular factor (see the file comment).
@@ -402,10 +421,16 @@ template <class Sys, int K, bool LD>
 static void integ_one(const unsigned g, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
                       const OrbitList* ol, cudaStream_t st)
 {
-    if (ol)
-        k_integrate_f32<Sys, K, LD, true><<<g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
-    else
-        k_integrate_f32<Sys, K, LD, false><<<g, kSmallBlock, 0, st>>>(a, sp, e, OrbitList{});
+    if (ol && ol->queue) {
+        static unsigned pg = 0;  // blocks of the persistent grid, found once
+        if (!pg && persistent_blocks(k_integrate_f32<Sys, K, LD, kModeQueue>, kSmallBlock, 0, &pg) != cudaSuccess)
+            pg = 0;
+        k_integrate_f32<Sys, K, LD, kModeQueue><<<pg ? pg : g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+    } else if (ol) {
+        k_integrate_f32<Sys, K, LD, kModeList><<<g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+    } else {
+        k_integrate_f32<Sys, K, LD, kModeAll><<<g, kSmallBlock, 0, st>>>(a, sp, e, OrbitList{});
+    }
 }
 
 template <class Sys, bool LD>

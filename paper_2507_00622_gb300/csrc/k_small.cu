@@ -244,23 +244,15 @@ __device__ __forceinline__ double sali_of(const double* a, const double* b)
     return sqrt(fmin(sp, sm));
 }
 
-// One thread per orbit.  LIST: thread t takes orbit list[t] (t < *count) and
-// appends the orbit to the next list when it is still running after the call.
-template <class Sys, int K, bool LD, bool LIST>
-__global__ void __launch_bounds__(kSmallBlock)
-k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
+// Advances orbit o (status OK) by the call's steps; returns true when it is
+// still running afterwards (status OK and below its end step).
+template <class Sys, int K, bool LD>
+__device__ __forceinline__ bool integrate_orbit(const int64_t o, const StepArgs& a, const SysPar& sp,
+                                                const EnsPtrs& e)
 {
     constexpr int N = Sys::N, D = 2 * N;
     constexpr int KK = K > 0 ? K : 1;
     const int64_t n = e.n;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t o = t;
-    if (LIST) {
-        if (t >= *ol.count) return;
-        o = ol.list[t];
-    }
-    if (o >= n) return;
-    if (e.status[o] != CHS_ORBIT_OK) return;
 
     double* wg = static_cast<double*>(e.w);
     double x[D];
@@ -342,7 +334,36 @@ k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList 
     e.dh_max[o] = dhm;
     e.n_exec[o] = exec0 + s;
     e.status[o] = st;
-    if (LIST) list_append(ol, st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]), (int32_t)o);
+    return st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]);
+}
+
+// One thread per orbit.  MODE kModeAll: thread t takes orbit t; kModeList:
+// orbit list[t] for t < *count, appended to the next list while it is still
+// running; kModeQueue: a persistent grid, every thread taking orbit after orbit
+// from the work queue, so that an orbit that ends early (end step, early exit,
+// escape) frees its lane at once.
+template <class Sys, int K, bool LD, int MODE>
+__global__ void __launch_bounds__(kSmallBlock)
+k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
+{
+    if constexpr (MODE == kModeQueue) {
+        for (;;) {
+            const int64_t o = queue_next(ol.queue);
+            if (o >= e.n) return;
+            if (e.status[o] == CHS_ORBIT_OK) integrate_orbit<Sys, K, LD>(o, a, sp, e);
+        }
+    } else {
+        const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        int64_t o = t;
+        if (MODE == kModeList) {
+            if (t >= *ol.count) return;
+            o = ol.list[t];
+        }
+        if (o >= e.n) return;
+        if (e.status[o] != CHS_ORBIT_OK) return;
+        const bool keep = integrate_orbit<Sys, K, LD>(o, a, sp, e);
+        if (MODE == kModeList) list_append(ol, keep, (int32_t)o);
+    }
 }
 
 // Orbits that can still advance: status OK and below their end step.
@@ -352,7 +373,7 @@ __global__ void k_list_init(const EnsPtrs e, int32_t* __restrict__ list, int32_t
     if (o >= e.n) return;
     bool keep = e.status[o] == CHS_ORBIT_OK;
     if (keep && e.t_end) keep = e.n_exec[o] < e.t_end[o];
-    OrbitList ol{nullptr, nullptr, list, count};
+    OrbitList ol{nullptr, nullptr, list, count, nullptr};
     list_append(ol, keep, (int32_t)o);
 }
 
@@ -576,10 +597,16 @@ template <class Sys, int K, bool LD>
 static void integ_one(const unsigned g, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
                       const OrbitList* ol, cudaStream_t st)
 {
-    if (ol)
-        k_integrate<Sys, K, LD, true><<<g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
-    else
-        k_integrate<Sys, K, LD, false><<<g, kSmallBlock, 0, st>>>(a, sp, e, OrbitList{});
+    if (ol && ol->queue) {
+        static unsigned pg = 0;  // blocks of the persistent grid, found once
+        if (!pg && persistent_blocks(k_integrate<Sys, K, LD, kModeQueue>, kSmallBlock, 0, &pg) != cudaSuccess)
+            pg = 0;
+        k_integrate<Sys, K, LD, kModeQueue><<<pg ? pg : g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+    } else if (ol) {
+        k_integrate<Sys, K, LD, kModeList><<<g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+    } else {
+        k_integrate<Sys, K, LD, kModeAll><<<g, kSmallBlock, 0, st>>>(a, sp, e, OrbitList{});
+    }
 }
 
 template <class Sys, bool LD>

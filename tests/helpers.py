@@ -58,7 +58,7 @@ def oracle_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm
 def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=True,
             sample_every=100, escape_r2=0.0, dh_limit=0.0, seed=1, w_in=None,
             sali_threshold=1e-8, chunks=None, grid=None, vec_fp32=False, sys_params=(),
-            early_exit=False, t_end=None, compact_chunk=None, integrator=0):
+            early_exit=False, t_end=None, compact_chunk=None, integrator=0, persistent=False):
     import torch
 
     from paper_2507_00622_gb300 import chs
@@ -82,9 +82,12 @@ def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=Tr
     chs.chs_ensemble_init(S.h, chs.params(dt, 1, **kw), abi, ics_t, st_t, w_t)
     step = 0
     work = chs.compact_work(n) if compact_chunk else None
+    queue = torch.empty(1, dtype=torch.int64, device="cuda") if persistent else None
     for c in (chunks or [n_steps]):
         if compact_chunk:
             chs.chs_integrate_compacted(S.h, chs.params(dt, c, step0=step, **kw), abi, compact_chunk, work)
+        elif persistent:
+            chs.chs_integrate_persistent(S.h, chs.params(dt, c, step0=step, **kw), abi, queue)
         else:
             chs.chs_integrate_batch(S.h, chs.params(dt, c, step0=step, **kw), abi)
         step += c

@@ -409,6 +409,31 @@ def test_compacted_graph_run_is_bit_identical_to_plain(vec_fp32):
                                   np.minimum(t_end, 5000)[ok & (a["status"] == 0)])
 
 
+@pytest.mark.parametrize("vec_fp32,integrator", [(False, chs.RK4), (True, chs.RK4), (False, chs.DOP853)])
+def test_persistent_queue_run_is_bit_identical_to_plain(vec_fp32, integrator):
+    """The work-queue launch (threads take orbit after orbit) changes which thread
+    integrates which orbit, never the arithmetic: identical results, with uneven
+    end steps and early exits, resumed in two calls."""
+    g0 = _grid(1 / 6, 40, 40)
+    ics, st = O.grid_ics(*g0)
+    rng = np.random.default_rng(4)
+    t_end = rng.integers(0, 6000, ics.shape[1]).astype(np.int64)
+    kw = dict(dt=0.01, k=3, ld_p=0.5, escape_r2=4.0, early_exit=True, t_end=t_end,
+              vec_fp32=vec_fp32, seed=5, integrator=integrator)
+    a = gpu_run(HH, 2, ics, st, n_steps=5000, **kw)
+    b = gpu_run(HH, 2, ics, st, n_steps=5000, chunks=[2300, 2700], persistent=True, **kw)
+    for key in ("x", "w", "ld", "dh_max", "n_exec", "status", "sali", "gali", "label"):
+        np.testing.assert_array_equal(a[key], b[key])
+    # an empty queue run and a queue of one orbit
+    S = chs.System(HH, 2)
+    q = torch.empty(1, dtype=torch.int64, device="cuda")
+    ens = chs.DeviceEnsemble.empty(0, 4, 2)
+    chs.chs_integrate_persistent(S.h, chs.params(0.01, 10, n_dev=2), ens.abi(), q)
+    one = gpu_run(HH, 2, ics[:, 700:701], st[700:701], n_steps=300, persistent=True, dt=0.01, k=2)
+    ref = gpu_run(HH, 2, ics[:, 700:701], st[700:701], n_steps=300, dt=0.01, k=2)
+    np.testing.assert_array_equal(one["x"], ref["x"])
+
+
 def test_uneven_end_steps_match_oracle():
     g0 = _grid(1 / 8, 20, 20)
     ics, st = O.grid_ics(*g0)
