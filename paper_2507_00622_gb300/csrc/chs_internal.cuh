@@ -155,6 +155,42 @@ __device__ __forceinline__ int64_t queue_next(unsigned long long* q)
     return (int64_t)(base + (unsigned long long)__popc(act & ((1u << lane) - 1u)));
 }
 
+// Work-queue loop of a persistent grid, shared by the one-orbit-per-thread
+// kernels.  Every lane holds one orbit in a Run (load / step / store, with the
+// step loop of a plain launch), and the warp steps in lockstep: a lane whose
+// orbit ends stores it and takes the next orbit with work from the queue inside
+// a short divergent branch, and the warp-wide vote at the top of every
+// iteration brings the lanes back together, so they never drift into groups
+// that execute the step separately.  Orbits without work (status not OK, or at
+// their end step) are left as they are, as a plain launch leaves them
+// unchanged.  Every lane of the warp must call this.
+template <class Run, class StepArgs_, class SysPar_, class EnsPtrs_, class... Extra>
+__device__ __forceinline__ void queue_worker(const StepArgs_& a, const SysPar_& sp, const EnsPtrs_& e,
+                                             unsigned long long* queue, Extra&... extra)
+{
+    Run r;
+    int64_t o = 0;
+    auto fetch = [&]() -> bool {
+        for (;;) {
+            o = queue_next(queue);
+            if (o >= e.n) return false;
+            if (e.status[o] != CHS_ORBIT_OK) continue;
+            r.load(o, a, e, extra...);
+            if (r.todo > 0) return true;
+        }
+    };
+    bool have = fetch();
+    while (__any_sync(0xffffffffu, have)) {
+        if (have) {
+            const bool running = r.step(a, sp, extra...);
+            if (!running || r.s >= r.todo) {
+                r.store(o, e, extra...);
+                have = fetch();
+            }
+        }
+    }
+}
+
 // Blocks of a persistent launch: every SM filled to the kernel's occupancy.
 template <class Kernel>
 inline cudaError_t persistent_blocks(Kernel kernel, int threads, size_t smem, unsigned* blocks)

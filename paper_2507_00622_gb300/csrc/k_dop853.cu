@@ -10,36 +10,41 @@ namespace {
 
 using dp::kBlock;
 
-// Advances orbit o (status OK) by the call's steps; returns true when it is
-// still running afterwards.
+// The state of one orbit during a call: loaded, advanced by fixed DOP853
+// steps with the checks of the chs_integrate_batch contract, stored back.
 template <class Sys, int K, bool LD>
-__device__ __forceinline__ bool integrate_orbit_dp(const int64_t o, const StepArgs& a,
-                                                   const SysPar& sp, const EnsPtrs& e,
-                                                   const dp::Slab<Sys>& sl)
-{
-    constexpr int N = Sys::N, D = 2 * N;
-    constexpr int KK = K > 0 ? K : 1;
-    const int64_t n = e.n;
-
-    double* wg = static_cast<double*>(e.w);
+struct DpRun {
+    static constexpr int N = Sys::N, D = 2 * N, KK = K > 0 ? K : 1;
     double x[D], w[KK][D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-#pragma unroll
-        for (int c = 0; c < D; ++c) w[j][c] = wg[(j * D + c) * n + o];
-    double L = LD ? e.ld[o] : 0.0;
-    const double h0 = e.h0[o];
-    double dhm = e.dh_max[o];
-    const int64_t exec0 = e.n_exec[o];
-    int64_t todo = a.n_steps;
-    if (e.t_end) todo = min(todo, max(e.t_end[o] - exec0, (int64_t)0));
+    double L, h0, dhm;
+    int64_t exec0, todo, s, until;
+    int32_t st;
 
-    int32_t st = CHS_ORBIT_OK;
-    int64_t until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
-    int64_t s = 0;
-    while (s < todo) {
+    __device__ __forceinline__ void load(const int64_t o, const StepArgs& a, const EnsPtrs& e,
+                                         const dp::Slab<Sys>&)
+    {
+        const int64_t n = e.n;
+        const double* wg = static_cast<const double*>(e.w);
+#pragma unroll
+        for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+#pragma unroll
+            for (int c = 0; c < D; ++c) w[j][c] = wg[(j * D + c) * n + o];
+        L = LD ? e.ld[o] : 0.0;
+        h0 = e.h0[o];
+        dhm = e.dh_max[o];
+        exec0 = e.n_exec[o];
+        todo = a.n_steps;
+        if (e.t_end) todo = min(todo, max(e.t_end[o] - exec0, (int64_t)0));
+        st = CHS_ORBIT_OK;
+        until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
+        s = 0;
+    }
+
+    // One step and its checks; false once the orbit froze (st says why).
+    __device__ __forceinline__ bool step(const StepArgs& a, const SysPar& sp, const dp::Slab<Sys>& sl)
+    {
         ++s;
         double xn[D], dL = 0.0;
         dp::orbit_step<Sys, LD, false>(sl, x, a.dt, a.ld_sqrt, a.ld_p, sp, xn, dL, nullptr, nullptr);
@@ -54,20 +59,40 @@ __device__ __forceinline__ bool integrate_orbit_dp(const int64_t o, const StepAr
             check = true;
         }
         st = dp::post_step<Sys, K>(x, w, L, a, sp, check, h0, dhm);
-        if (st != CHS_ORBIT_OK) break;
+        return st == CHS_ORBIT_OK;
     }
 
+    // Writes the orbit back; true when it is still running.
+    __device__ __forceinline__ bool store(const int64_t o, const EnsPtrs& e, const dp::Slab<Sys>&) const
+    {
+        const int64_t n = e.n;
+        double* wg = static_cast<double*>(e.w);
 #pragma unroll
-    for (int c = 0; c < D; ++c) e.x[c * n + o] = x[c];
+        for (int c = 0; c < D; ++c) e.x[c * n + o] = x[c];
 #pragma unroll
-    for (int j = 0; j < K; ++j)
+        for (int j = 0; j < K; ++j)
 #pragma unroll
-        for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = w[j][c];
-    if (LD) e.ld[o] = L;
-    e.dh_max[o] = dhm;
-    e.n_exec[o] = exec0 + s;
-    e.status[o] = st;
-    return st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]);
+            for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = w[j][c];
+        if (LD) e.ld[o] = L;
+        e.dh_max[o] = dhm;
+        e.n_exec[o] = exec0 + s;
+        e.status[o] = st;
+        return st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]);
+    }
+};
+
+// Advances orbit o (status OK) by the call's steps; returns true when it is
+// still running afterwards.
+template <class Sys, int K, bool LD>
+__device__ __forceinline__ bool integrate_orbit_dp(const int64_t o, const StepArgs& a,
+                                                   const SysPar& sp, const EnsPtrs& e,
+                                                   const dp::Slab<Sys>& sl)
+{
+    DpRun<Sys, K, LD> r;
+    r.load(o, a, e, sl);
+    while (r.s < r.todo)
+        if (!r.step(a, sp, sl)) break;
+    return r.store(o, e, sl);
 }
 
 // One orbit per thread, with the orbit-selection modes of k_integrate
@@ -79,11 +104,8 @@ k_integrate_dp(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitLi
     const dp::Slab<Sys> sl = dp::my_slab<Sys>();
     const int mode = integ_mode(ol);
     if (mode == kModeQueue) {
-        for (;;) {
-            const int64_t o = queue_next(ol.queue);
-            if (o >= e.n) return;
-            if (e.status[o] == CHS_ORBIT_OK) integrate_orbit_dp<Sys, K, LD>(o, a, sp, e, sl);
-        }
+        queue_worker<DpRun<Sys, K, LD>>(a, sp, e, ol.queue, sl);
+        return;
     }
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t o = t;

@@ -164,37 +164,44 @@ struct Hess32<SysQuartic3> {
     }
 };
 
-// Advances orbit o (status OK) by the call's steps; returns true when it is
-// still running afterwards.
+// The state of one orbit during a call (FP64 orbit and LD, FP32 frame Q and
+// triangle R): loaded, advanced step by step with the checks of the
+// chs_integrate_batch contract, stored back.
 template <class Sys, int K, bool LD>
-__device__ __forceinline__ bool integrate_orbit_f32(const int64_t o, const StepArgs& a,
-                                                    const SysPar& sp, const EnsPtrs& e)
-{
-    constexpr int N = Sys::N, D = 2 * N, NH = Sys::NH, NR = K * (K + 1) / 2;
-    const int64_t n = e.n;
-
-    float* wg = static_cast<float*>(e.w);
+struct FrameRun {
+    static constexpr int N = Sys::N, D = 2 * N, NH = Sys::NH, NR = K * (K + 1) / 2;
     double x[D];
     float Q[K][D], R[NR];
-#pragma unroll
-    for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-#pragma unroll
-        for (int c = 0; c < D; ++c) Q[j][c] = wg[(j * D + c) * n + o];
-#pragma unroll
-    for (int p = 0; p < NR; ++p) R[p] = wg[(K * D + p) * n + o];
-    double L = LD ? e.ld[o] : 0.0;
-    const double h0 = e.h0[o];
-    double dhm = e.dh_max[o];
-    const int64_t exec0 = e.n_exec[o];
-    int64_t todo = a.n_steps;
-    if (e.t_end) todo = min(todo, max(e.t_end[o] - exec0, (int64_t)0));
+    double L, h0, dhm;
+    int64_t exec0, todo, s, until;
+    int32_t st;
 
-    int32_t st = CHS_ORBIT_OK;
-    int64_t until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
-    int64_t s = 0;
-    while (s < todo) {
+    __device__ __forceinline__ void load(const int64_t o, const StepArgs& a, const EnsPtrs& e)
+    {
+        const int64_t n = e.n;
+        const float* wg = static_cast<const float*>(e.w);
+#pragma unroll
+        for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+#pragma unroll
+            for (int c = 0; c < D; ++c) Q[j][c] = wg[(j * D + c) * n + o];
+#pragma unroll
+        for (int p = 0; p < NR; ++p) R[p] = wg[(K * D + p) * n + o];
+        L = LD ? e.ld[o] : 0.0;
+        h0 = e.h0[o];
+        dhm = e.dh_max[o];
+        exec0 = e.n_exec[o];
+        todo = a.n_steps;
+        if (e.t_end) todo = min(todo, max(e.t_end[o] - exec0, (int64_t)0));
+        st = CHS_ORBIT_OK;
+        until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
+        s = 0;
+    }
+
+    // One step and its checks; false once the orbit froze (st says why).
+    __device__ __forceinline__ bool step(const StepArgs& a, const SysPar& sp)
+    {
         ++s;
         float qf[4][N], Hf[4][NH];
         rk4_state_positions<Sys, LD, true>(x, L, a.dt, a.ld_sqrt, a.ld_p, sp, qf);
@@ -247,7 +254,7 @@ __device__ __forceinline__ bool integrate_orbit_f32(const int64_t o, const StepA
             for (int i = 1; i < N; ++i) r2 = fma(x[i], x[i], r2);
             if (r2 > a.escape_r2) {
                 st = CHS_ORBIT_ESCAPED;
-                break;
+                return false;
             }
         }
         if (--until == 0) {
@@ -261,38 +268,58 @@ __device__ __forceinline__ bool integrate_orbit_f32(const int64_t o, const StepA
                 for (int c = 0; c < D; ++c) fin = fin && isfinite(Q[j][c]);
             if (!fin) {
                 st = CHS_ORBIT_NONFINITE;
-                break;
+                return false;
             }
             const double dH = fabs(Sys::energy(x, sp) - h0);
             dhm = fmax(dhm, dH);
             if (a.dh_limit > 0.0 && dH > a.dh_limit) {
                 st = CHS_ORBIT_ENERGY_DRIFT;
-                break;
+                return false;
             }
             if constexpr (K >= 2) {
                 const double sv = fabs((double)R[tri(1, 1)]) *
                                   sqrt(2.0 / (1.0 + fmin(fabs((double)R[tri(0, 1)]), 1.0)));
                 if (a.early_exit && sv < a.sali_threshold) {
                     st = CHS_ORBIT_EARLY_CHAOTIC;
-                    break;
+                    return false;
                 }
             }
         }
+        return true;
     }
 
+    // Writes the orbit back; true when it is still running.
+    __device__ __forceinline__ bool store(const int64_t o, const EnsPtrs& e) const
+    {
+        const int64_t n = e.n;
+        float* wg = static_cast<float*>(e.w);
 #pragma unroll
-    for (int c = 0; c < D; ++c) e.x[c * n + o] = x[c];
+        for (int c = 0; c < D; ++c) e.x[c * n + o] = x[c];
 #pragma unroll
-    for (int j = 0; j < K; ++j)
+        for (int j = 0; j < K; ++j)
 #pragma unroll
-        for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = Q[j][c];
+            for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = Q[j][c];
 #pragma unroll
-    for (int p = 0; p < NR; ++p) wg[(K * D + p) * n + o] = R[p];
-    if (LD) e.ld[o] = L;
-    e.dh_max[o] = dhm;
-    e.n_exec[o] = exec0 + s;
-    e.status[o] = st;
-    return st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]);
+        for (int p = 0; p < NR; ++p) wg[(K * D + p) * n + o] = R[p];
+        if (LD) e.ld[o] = L;
+        e.dh_max[o] = dhm;
+        e.n_exec[o] = exec0 + s;
+        e.status[o] = st;
+        return st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]);
+    }
+};
+
+// Advances orbit o (status OK) by the call's steps; returns true when it is
+// still running afterwards.
+template <class Sys, int K, bool LD>
+__device__ __forceinline__ bool integrate_orbit_f32(const int64_t o, const StepArgs& a,
+                                                    const SysPar& sp, const EnsPtrs& e)
+{
+    FrameRun<Sys, K, LD> r;
+    r.load(o, a, e);
+    while (r.s < r.todo)
+        if (!r.step(a, sp)) break;
+    return r.store(o, e);
 }
 
 // One thread per orbit; the orbit-selection modes of k_integrate (k_small.cu).
@@ -301,11 +328,7 @@ __global__ void __launch_bounds__(kSmallBlock)
 k_integrate_f32(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
 {
     if constexpr (MODE == kModeQueue) {
-        for (;;) {
-            const int64_t o = queue_next(ol.queue);
-            if (o >= e.n) return;
-            if (e.status[o] == CHS_ORBIT_OK) integrate_orbit_f32<Sys, K, LD>(o, a, sp, e);
-        }
+        queue_worker<FrameRun<Sys, K, LD>>(a, sp, e, ol.queue);
     } else {
         const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         int64_t o = t;

@@ -244,36 +244,41 @@ __device__ __forceinline__ double sali_of(const double* a, const double* b)
     return sqrt(fmin(sp, sm));
 }
 
-// Advances orbit o (status OK) by the call's steps; returns true when it is
-// still running afterwards (status OK and below its end step).
+// The state of one orbit during a call: loaded from the ensemble, advanced
+// step by step with the checks of the chs_integrate_batch contract, stored back.
 template <class Sys, int K, bool LD>
-__device__ __forceinline__ bool integrate_orbit(const int64_t o, const StepArgs& a, const SysPar& sp,
-                                                const EnsPtrs& e)
-{
-    constexpr int N = Sys::N, D = 2 * N;
-    constexpr int KK = K > 0 ? K : 1;
-    const int64_t n = e.n;
-
-    double* wg = static_cast<double*>(e.w);
+struct OrbitRun {
+    static constexpr int N = Sys::N, D = 2 * N, KK = K > 0 ? K : 1;
     double x[D];
     double w[KK][D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-#pragma unroll
-        for (int c = 0; c < D; ++c) w[j][c] = wg[(j * D + c) * n + o];
-    double L = LD ? e.ld[o] : 0.0;
-    const double h0 = e.h0[o];
-    double dhm = e.dh_max[o];
-    const int64_t exec0 = e.n_exec[o];
-    int64_t todo = a.n_steps;
-    if (e.t_end) todo = min(todo, max(e.t_end[o] - exec0, (int64_t)0));
+    double L, h0, dhm;
+    int64_t exec0, todo, s, until;
+    int32_t st;
 
-    int32_t st = CHS_ORBIT_OK;
-    int64_t until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
-    int64_t s = 0;
-    while (s < todo) {
+    __device__ __forceinline__ void load(const int64_t o, const StepArgs& a, const EnsPtrs& e)
+    {
+        const int64_t n = e.n;
+        const double* wg = static_cast<const double*>(e.w);
+#pragma unroll
+        for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+#pragma unroll
+            for (int c = 0; c < D; ++c) w[j][c] = wg[(j * D + c) * n + o];
+        L = LD ? e.ld[o] : 0.0;
+        h0 = e.h0[o];
+        dhm = e.dh_max[o];
+        exec0 = e.n_exec[o];
+        todo = a.n_steps;
+        if (e.t_end) todo = min(todo, max(e.t_end[o] - exec0, (int64_t)0));
+        st = CHS_ORBIT_OK;
+        until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
+        s = 0;
+    }
+
+    // One step and its checks; false once the orbit froze (st says why).
+    __device__ __forceinline__ bool step(const StepArgs& a, const SysPar& sp)
+    {
         ++s;
         rk4_step<Sys, K, LD>(x, w, L, a.dt, a.ld_sqrt, a.ld_p, sp);
         if (a.renorm) {
@@ -293,7 +298,7 @@ __device__ __forceinline__ bool integrate_orbit(const int64_t o, const StepArgs&
             for (int i = 1; i < N; ++i) r2 = fma(x[i], x[i], r2);
             if (r2 > a.escape_r2) {
                 st = CHS_ORBIT_ESCAPED;
-                break;
+                return false;
             }
         }
         if (--until == 0) {
@@ -307,51 +312,68 @@ __device__ __forceinline__ bool integrate_orbit(const int64_t o, const StepArgs&
                 for (int c = 0; c < D; ++c) fin = fin && isfinite(w[j][c]);
             if (!fin) {
                 st = CHS_ORBIT_NONFINITE;
-                break;
+                return false;
             }
             const double dH = fabs(Sys::energy(x, sp) - h0);
             dhm = fmax(dhm, dH);
             if (a.dh_limit > 0.0 && dH > a.dh_limit) {
                 st = CHS_ORBIT_ENERGY_DRIFT;
-                break;
+                return false;
             }
             if constexpr (K >= 2) {
                 if (a.early_exit && sali_of<D>(w[0], w[1]) < a.sali_threshold) {
                     st = CHS_ORBIT_EARLY_CHAOTIC;
-                    break;
+                    return false;
                 }
             }
         }
+        return true;
     }
 
+    // Writes the orbit back; true when it is still running (status OK and below
+    // its end step).
+    __device__ __forceinline__ bool store(const int64_t o, const EnsPtrs& e) const
+    {
+        const int64_t n = e.n;
+        double* wg = static_cast<double*>(e.w);
 #pragma unroll
-    for (int c = 0; c < D; ++c) e.x[c * n + o] = x[c];
+        for (int c = 0; c < D; ++c) e.x[c * n + o] = x[c];
 #pragma unroll
-    for (int j = 0; j < K; ++j)
+        for (int j = 0; j < K; ++j)
 #pragma unroll
-        for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = w[j][c];
-    if (LD) e.ld[o] = L;
-    e.dh_max[o] = dhm;
-    e.n_exec[o] = exec0 + s;
-    e.status[o] = st;
-    return st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]);
+            for (int c = 0; c < D; ++c) wg[(j * D + c) * n + o] = w[j][c];
+        if (LD) e.ld[o] = L;
+        e.dh_max[o] = dhm;
+        e.n_exec[o] = exec0 + s;
+        e.status[o] = st;
+        return st == CHS_ORBIT_OK && (!e.t_end || exec0 + s < e.t_end[o]);
+    }
+};
+
+// Advances orbit o (status OK) by the call's steps; returns true when it is
+// still running afterwards.
+template <class Sys, int K, bool LD>
+__device__ __forceinline__ bool integrate_orbit(const int64_t o, const StepArgs& a, const SysPar& sp,
+                                                const EnsPtrs& e)
+{
+    OrbitRun<Sys, K, LD> r;
+    r.load(o, a, e);
+    while (r.s < r.todo)
+        if (!r.step(a, sp)) break;
+    return r.store(o, e);
 }
 
 // One thread per orbit.  MODE kModeAll: thread t takes orbit t; kModeList:
 // orbit list[t] for t < *count, appended to the next list while it is still
 // running; kModeQueue: a persistent grid, every thread taking orbit after orbit
-// from the work queue, so that an orbit that ends early (end step, early exit,
-// escape) frees its lane at once.
+// from the work queue (queue_worker), so that an orbit that ends early (end
+// step, early exit, escape) frees its lane at once.
 template <class Sys, int K, bool LD, int MODE>
 __global__ void __launch_bounds__(kSmallBlock)
 k_integrate(const StepArgs a, const SysPar sp, const EnsPtrs e, const OrbitList ol)
 {
     if constexpr (MODE == kModeQueue) {
-        for (;;) {
-            const int64_t o = queue_next(ol.queue);
-            if (o >= e.n) return;
-            if (e.status[o] == CHS_ORBIT_OK) integrate_orbit<Sys, K, LD>(o, a, sp, e);
-        }
+        queue_worker<OrbitRun<Sys, K, LD>>(a, sp, e, ol.queue);
     } else {
         const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
         int64_t o = t;
