@@ -185,7 +185,7 @@ __device__ __forceinline__ void orbit_step(const Slab<Sys>& sl, const double* x,
         }
         if constexpr (LD && cb != 0.0) {
             // p = 1/2: the stage's sum of square roots in double-float, widened once
-            const double g = ld_sqrt ? ff_to_f64(ff_sum_sqrt_abs<D>(f)) : ld_integrand<D>(f, ld_sqrt, ld_p);
+            const double g = ld_sqrt ? ff_to_f64(ff_sum_sqrt_abs<D>(f)) : ld_integrand_pow<D>(f, ld_p);
             sL = fma(cb, g, sL);
         }
     });

@@ -1,17 +1,16 @@
 // fastmath.cuh -- square root and reciprocal square root for the FP64 pipe-bound
 // kernels of GB300, where FP64 runs at 1/64 of the FP32 rate.
 //
-// Both start from the hardware single-precision reciprocal-square-root
-// approximation (PTX rsqrt.approx.ftz.f32, on the SFU), reach it through
-// integer bit manipulation instead of FP64<->FP32 conversions, and finish with
-// one Newton-Raphson step in FP64:
-//   rsqrt:  y1 = y0 + y0 (1 - a y0^2) / 2                          (3 FP64 ops)
-//   sqrt :  s0 = a y0,  s1 = s0 + (a - s0^2) y0 / 2   (Heron step)  (3 FP64 ops)
-// With |y0 sqrt(a) - 1| = e <= ~2^-22 the refined results carry a relative
-// error of O(e^2) ~ 1e-13, against ~10 FP64-pipe instructions for the correctly
-// rounded library routines.  Arguments outside the single-precision exponent
-// range go to the library routines (sqrt of a value below 2^-126 returns 0,
-// an absolute error below 1.1e-19).
+// Every routine starts from the hardware single-precision reciprocal-square-
+// root approximation (PTX rsqrt.approx.ftz.f32, on the SFU), reached through
+// integer bit manipulation instead of FP64<->FP32 conversions.  rsqrt_nr
+// finishes with one Newton-Raphson step in FP64,
+//   y1 = y0 + y0 (1 - a y0^2) / 2                                   (3 FP64 ops)
+// (with |y0 sqrt(a) - 1| = e <= ~2^-22 the result carries a relative error of
+// O(e^2) ~ 1e-13, against ~10 FP64-pipe instructions for the correctly rounded
+// library routine; arguments outside the single-precision exponent range go to
+// the library); the double-float routines below keep even that step off the
+// FP64 pipe.
 #pragma once
 
 #include <stdint.h>
@@ -62,21 +61,6 @@ __device__ __forceinline__ float f32_from_f64(double a)
     fb = ah < ((1023 - 126) << 20) ? 0 : fb;
     fb = ah >= ((1023 + 128) << 20) ? 0x7f800000 : fb;
     return __int_as_float(fb | sgn);
-}
-
-// sqrt(a) for a >= 0, relative error ~1e-13.
-__device__ __forceinline__ double sqrt_nr(double a)
-{
-    const int hi = __double2hiint(a), lo = __double2loint(a);
-    if (in_f32_range(hi)) {
-        const float yf = rsqrt_approx_f32(f64_to_f32_trunc(hi, lo));
-        const double y = f32_to_f64_bits(yf);
-        const double hy = f32_to_f64_bits(0.5f * yf);
-        const double s0 = a * y;
-        const double r = fma(-s0, s0, a);
-        return fma(r, hy, s0);
-    }
-    return hi < ((1023 - 126) << 20) ? 0.0 : sqrt(a);
 }
 
 // 1/sqrt(a) for a > 0, relative error ~1e-13.

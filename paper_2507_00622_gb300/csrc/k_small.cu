@@ -139,7 +139,7 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
         if (ld_sqrt)
             ld_acc_sqrt<D>(fL, f, 1.0f);
         else
-            aL = ld_integrand<D>(f, ld_sqrt, ld_p);
+            aL = ld_integrand_pow<D>(f, ld_p);
     }
 
     // stages 2 and 3 at (xs, ws); the next stage input uses h/2 then h
@@ -168,7 +168,7 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
             if (ld_sqrt)
                 ld_acc_sqrt<D>(fL, f, 2.0f);
             else
-                aL = fma(2.0, ld_integrand<D>(f, ld_sqrt, ld_p), aL);
+                aL = fma(2.0, ld_integrand_pow<D>(f, ld_p), aL);
         }
     }
 
@@ -190,7 +190,7 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
             ld_acc_sqrt<D>(fL, f, 1.0f);
             L = fma(fabs(h6), ff_to_f64(fL), L);
         } else {
-            L = fma(fabs(h6), aL + ld_integrand<D>(f, ld_sqrt, ld_p), L);
+            L = fma(fabs(h6), aL + ld_integrand_pow<D>(f, ld_p), L);
         }
     }
 }

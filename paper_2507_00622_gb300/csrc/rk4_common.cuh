@@ -10,18 +10,14 @@
 
 namespace chs {
 
-// LD integrand sum_i |f_i|^p (p = 1/2: Newton-refined square roots).
+// LD integrand sum_i |f_i|^p in FP64 for a general exponent p (p = 1/2 takes
+// the double-float route, ld_acc_sqrt).
 template <int D>
-__device__ __forceinline__ double ld_integrand(const double* f, int ld_sqrt, double p)
+__device__ __forceinline__ double ld_integrand_pow(const double* f, double p)
 {
     double acc = 0.0;
-    if (ld_sqrt) {
 #pragma unroll
-        for (int i = 0; i < D; ++i) acc += sqrt_nr(fabs(f[i]));
-    } else {
-#pragma unroll
-        for (int i = 0; i < D; ++i) acc += pow(fabs(f[i]), p);
-    }
+    for (int i = 0; i < D; ++i) acc += pow(fabs(f[i]), p);
     return acc;
 }
 
@@ -48,7 +44,7 @@ __device__ __forceinline__ double ld_term(const double* f, int ld_sqrt, double p
     if constexpr (LD32)
         return ld_integrand_f32<D>(f, ld_sqrt, p);
     else
-        return ld_integrand<D>(f, ld_sqrt, p);
+        return ld_integrand_pow<D>(f, p);
 }
 
 // acc += w sum_i sqrt|f_i| in double-float (p = 1/2; w a power of two).
