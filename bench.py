@@ -72,14 +72,15 @@ def flops_per_orbit_step(k: int, ld: bool, vec_fp32: bool) -> tuple[int, int]:
       7 per component, renormalisation 12 per vector.
     FP32 frame: propagator blocks 104, application 32 per vector, Gram-Schmidt
       16 per vector pair and 13 per vector, triangle update and normalisation
-      74 (for k = 4); the LD integrand (7 per stage) is summed in FP32 there."""
+      74 (for k = 4); the LD integrand (7 per stage) is summed in FP32 there, and
+      the stage Hessians (3 of the 10 per stage) are formed in FP32."""
     xs = 4 * (10 + (7 if ld else 0)) + 3 * 2 * 4 + 7 * (4 + (1 if ld else 0)) + 3
     if vec_fp32:
         tri = sum(2 * (j - i + 1) for j in range(k) for i in range(j + 1))
         nr = k * (k + 1) // 2
         vs = 104 + 32 * k + 16 * k * (k - 1) // 2 + 13 * k + tri + 2 * nr + k + nr
-        ldf = 4 * 7 if ld else 0
-        return xs - ldf, vs + ldf
+        moved = (4 * 7 if ld else 0) + 4 * 3
+        return xs - moved, vs + moved
     vs = 4 * 6 * k + 3 * 2 * 4 * k + 7 * 4 * k + 12 * k
     return xs + vs, 0
 
