@@ -651,6 +651,81 @@ def run_quartic(args):
     return 0
 
 
+def run_integrators(args):
+    """Cost of accuracy, RK4 against the paper's DOP853: the 256 x 256 grid at
+    E = 1/6 (k = 4, LD) integrated to t = 100 by classic RK4 at two fixed steps,
+    DOP853 at two fixed steps and adaptive DOP 8(5) at three tolerances; every
+    final state is compared with DOP853 at h = 0.0025 on the orbits that are
+    regular by that reference (SALI > 1e-2; chaotic orbits amplify any
+    difference by exp(lambda t)).  Prints one JSON line: per method the kernel
+    time, orbit-steps, and the median and maximum relative state error."""
+    import torch
+
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+
+    cuda_build.build()
+    chs.load()
+    side, T, k = 256, 100.0, 4
+    n = side * side
+    y0, y1, p0, p1 = grid_box(E_GRID)
+    S = chs.System(chs.HENON_HEILES, 2)
+    ics = torch.empty((4, n), dtype=torch.float64, device="cuda")
+    ic_st = torch.empty(n, dtype=torch.int32, device="cuda")
+    chs.chs_section_grid_ics(S.h, E_GRID, y0, y1, side, p0, p1, side, ics, ic_st)
+    stream = torch.cuda.current_stream()
+
+    def run(integ, h=None, tol=None):
+        kw = dict(n_dev=k, ld_p=0.5, escape_r2=4.0, sample_every=100, integrator=integ)
+        ens = chs.DeviceEnsemble.empty(n, 4, k)
+        abi = ens.abi()
+        chs.chs_ensemble_init(S.h, chs.params(h or 0.01, 1, **kw), abi, ics, ic_st)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if tol is None:
+            steps = int(round(T / h))
+            prm = chs.params(h, steps, **kw)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            chs.chs_integrate_batch(S.h, prm, abi, stream)
+            ev1.record(stream)
+        else:
+            t = torch.zeros(n, dtype=torch.float64, device="cuda")
+            hs = torch.full((n,), 0.01, dtype=torch.float64, device="cuda")
+            rej = torch.zeros(n, dtype=torch.int64, device="cuda")
+            prm = chs.params(0.01, 10**8, **kw)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            chs.chs_integrate_adaptive(S.h, prm, chs.Adaptive(T, tol, tol, 0.0), abi, t, hs, None, None, rej,
+                                       stream)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        sali = torch.empty(n, dtype=torch.float64, device="cuda")
+        chs.chs_indicators(S.h, chs.params(0.01, 0, **kw), abi, sali=sali)
+        torch.cuda.synchronize()
+        return dict(ms=ev0.elapsed_time(ev1), x=ens.x.cpu().numpy(), st=ens.status.cpu().numpy(),
+                    steps=int(ens.n_exec.sum()), sali=sali.cpu().numpy())
+
+    ref = run(chs.DOP853, h=0.0025)
+    keep = (ref["st"] == 0) & (ref["sali"] > 1e-2)
+    scale = np.abs(ref["x"][:, keep]).max(axis=0)
+    out = {}
+    for name, integ, h, tol in (("rk4_h0.01", chs.RK4, 0.01, None), ("rk4_h0.005", chs.RK4, 0.005, None),
+                                ("dop853_h0.1", chs.DOP853, 0.1, None), ("dop853_h0.05", chs.DOP853, 0.05, None),
+                                ("dop853_adaptive_tol1e-8", chs.DOP853, None, 1e-8),
+                                ("dop853_adaptive_tol1e-10", chs.DOP853, None, 1e-10),
+                                ("dop853_adaptive_tol1e-12", chs.DOP853, None, 1e-12)):
+        r = run(integ, h=h, tol=tol)
+        ok = keep & (r["st"] == 0)
+        err = (np.abs(r["x"][:, ok] - ref["x"][:, ok]).max(axis=0) / scale[ok[keep]])
+        out[name] = {"kernel_ms": r["ms"], "orbit_steps": r["steps"],
+                     "median_rel_err": float(np.median(err)), "max_rel_err": float(err.max()),
+                     "orbits_compared": int(ok.sum())}
+    print(json.dumps({"workload": f"henon_heiles_E1/6_grid{side}x{side}_k4_ld_to_t{T:g}",
+                      "reference": "DOP853 h = 0.0025", "regular_orbits": int(keep.sum()),
+                      "methods": out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -666,7 +741,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
-    ap.add_argument("--workload", choices=["grid", "fput", "classify", "quartic"], default="grid")
+    ap.add_argument("--workload", choices=["grid", "fput", "classify", "quartic", "integrators"],
+                    default="grid")
     ap.add_argument("--quartic-orbits", type=int, default=4_194_304)
     ap.add_argument("--persistent", action="store_true",
                     help="quartic workload: one persistent work-queue launch per bench step")
@@ -685,6 +761,8 @@ def main():
         return run_fput(args)
     if args.workload == "classify":
         return run_classify(args)
+    if args.workload == "integrators":
+        return run_integrators(args)
     if args.workload == "quartic":
         return run_quartic(args)
     if args.impl == "reference":

@@ -100,15 +100,17 @@ constexpr bool read_later(int j)
 }
 template <int J>
 constexpr bool kReadLater = read_later(J);
+static_assert(!read_later(11), "the last stage is never read by another stage");
 
 // A thread's column of the block's shared array: H[s][t] (stage Hessians,
-// packed upper triangle) then K[s][i] (stage derivatives), entry e at
-// base[e * kBlock].  Accesses are volatile so that stage values are re-read
-// from shared memory instead of being kept in registers.
+// packed upper triangle, 12 stages) then K[s][i] (stage derivatives of the 11
+// stages a later stage reads), entry e at base[e * kBlock].  Accesses are
+// volatile so that stage values are re-read from shared memory instead of
+// being kept in registers.
 template <class Sys>
 struct Slab {
     static constexpr int D = 2 * Sys::N, NH = Sys::NH;
-    static constexpr int kDoubles = 12 * (NH + D);
+    static constexpr int kDoubles = 12 * NH + 11 * D;
     volatile double* base;
     __device__ __forceinline__ volatile double& H(int s, int t) const { return base[(s * NH + t) * kBlock]; }
     __device__ __forceinline__ volatile double& K(int s, int i) const
