@@ -191,6 +191,15 @@ __device__ __forceinline__ void queue_worker(const StepArgs_& a, const SysPar_& 
     }
 }
 
+// The current device, clamped into [0, kCacheDevices) for per-device launch caches.
+constexpr int kCacheDevices = 64;
+inline int cache_device()
+{
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kCacheDevices) d = 0;
+    return d;
+}
+
 // Blocks of a persistent launch: every SM filled to the kernel's occupancy.
 template <class Kernel>
 inline cudaError_t persistent_blocks(Kernel kernel, int threads, size_t smem, unsigned* blocks)

@@ -205,8 +205,8 @@ cudaError_t fixed_sys(int k, bool ld, const StepArgs& a, const SysPar& sp, const
         auto kern = ld ? k_integrate_dp<Sys, K, true> : k_integrate_dp<Sys, K, false>;
         unsigned grid = g;
         if (l.queue) {
-            static unsigned pg[2] = {0, 0};  // persistent grid per LD variant, found once
-            unsigned& p = pg[ld ? 1 : 0];
+            static unsigned pg[kCacheDevices][2] = {};  // persistent grid per device and LD variant
+            unsigned& p = pg[cache_device()][ld ? 1 : 0];
             if (!p && persistent_blocks(kern, kBlock, sm, &p) != cudaSuccess) p = 0;
             if (p) grid = p;
         }

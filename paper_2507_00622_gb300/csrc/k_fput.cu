@@ -283,11 +283,12 @@ bool fput_lyap_supported(int n_dof)
 template <int N>
 static cudaError_t prepare_n()
 {
-    static bool done = false;  // idempotent; set before any stream capture
-    if (done) return cudaSuccess;
+    static bool done[kCacheDevices] = {};  // per device; set before any stream capture
+    const int dev = cache_device();
+    if (done[dev]) return cudaSuccess;
     cudaError_t err = cudaFuncSetAttribute(k_fput_lyap<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)FputLyapCfg<N>::SMEM);
-    if (err == cudaSuccess) done = true;
+    if (err == cudaSuccess) done[dev] = true;
     return err;
 }
 

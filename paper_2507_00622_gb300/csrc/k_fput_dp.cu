@@ -456,14 +456,15 @@ k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const i
 template <int N>
 cudaError_t prepare_dp_n()
 {
-    static bool done = false;  // idempotent; set before any stream capture
-    if (done) return cudaSuccess;
+    static bool done[kCacheDevices] = {};  // per device; set before any stream capture
+    const int dev = cache_device();
+    if (done[dev]) return cudaSuccess;
     cudaError_t err = cudaFuncSetAttribute(k_fput_lyap_dp<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)FputDpCfg<N>::SMEM);
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_fput_lyap_adapt<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)FputDpCfg<N>::SMEM);
-    if (err == cudaSuccess) done = true;
+    if (err == cudaSuccess) done[dev] = true;
     return err;
 }
 

@@ -445,7 +445,8 @@ static void integ_one(const unsigned g, const StepArgs& a, const SysPar& sp, con
                       const OrbitList* ol, cudaStream_t st)
 {
     if (ol && ol->queue) {
-        static unsigned pg = 0;  // blocks of the persistent grid, found once
+        static unsigned pgs[kCacheDevices] = {};  // blocks of the persistent grid, per device
+        unsigned& pg = pgs[cache_device()];
         if (!pg && persistent_blocks(k_integrate_f32<Sys, K, LD, kModeQueue>, kSmallBlock, 0, &pg) != cudaSuccess)
             pg = 0;
         k_integrate_f32<Sys, K, LD, kModeQueue><<<pg ? pg : g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
