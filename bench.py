@@ -211,6 +211,69 @@ def cpu_oracle_sample(chunk: int, budget_s: float, n_sample: int = 4096, ny: int
                       f"{step} {integrator.upper()} steps from t=0 ({done} orbit-steps in {el:.1f} s)"}
 
 
+def cpu_fput_sample(Ns, chunk: int, qr: dict, budget_s: float, integrator: str = "rk4",
+                    n_sample: int = 64):
+    """The oracle on the host cores for the FPUT Lyapunov workload: n_sample
+    orbits per chain length (the bench's first draws), each chain length given
+    an equal share of budget_s, integrated chunk by chunk (fresh runs of `chunk`
+    steps from the initial conditions) until its share is spent; the rate is
+    that of the bench's mix (equal orbit-steps per chain length)."""
+    import oracle as O
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+
+    inv_rate, parts = 0.0, []
+    for N in Ns:
+        Q, P = normal_mode_draws(1000 + N, N, n_sample)
+        ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(n_sample, 0.1 * N))
+        prm = O.params(0.05, chunk, qr_every=qr[N], sample_every=100,
+                       integrator=O.DOP853 if integrator == "dop853" else O.RK4)
+        t0 = time.perf_counter()
+        runs = 0
+        while True:
+            O.lyapunov(O.fput(N), prm, ics)
+            runs += 1
+            if time.perf_counter() - t0 >= budget_s / len(Ns):
+                break
+        el = time.perf_counter() - t0
+        inv_rate += el / (runs * n_sample * chunk)
+        parts.append(f"N={N}: {runs} x {n_sample} orbits x {chunk} steps in {el:.1f} s")
+    # the bench's mix: the same number of orbit-steps for every chain length
+    return {"value": len(Ns) / inv_rate, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": "; ".join(parts) + " (rate of an equal mix of orbit-steps per N)"}
+
+
+def cpu_quartic_sample(chunk: int, budget_s: float, n_sample: int = 16384):
+    """The oracle on the host cores for the quartic-3 workload: a strided sample of
+    the bench's shell states with FP64 vectors (the oracle's precision), k = 6,
+    early exit, their own end steps, integrated chunk by chunk until budget_s."""
+    import oracle as O
+    from paper_2507_00622_gb300.inputs import strided_sample
+
+    n = 4_194_304
+    rng = np.random.default_rng(5)
+    dirs = rng.standard_normal((6, n))
+    E = rng.uniform(1.0, 10.0, n)
+    t_end = rng.integers(100_000, 1_000_001, n).astype(np.int64)
+    idx = strided_sample(n, n_sample)
+    sysd = O.system(O.QUARTIC3, 3, eps=0.1)
+    ics = O.shell_ics(sysd, dirs[:, idx], E[idx])
+    kw = dict(n_dev=6, ld_p=0.0, sample_every=100, early_exit=True)
+    ens = O.Ensemble(sysd, O.params(0.01, 1, **kw), ics, seed=3)
+    done, step, t0 = 0, 0, time.perf_counter()
+    while True:
+        before = int(ens.n_exec.sum())
+        ens.integrate(O.params(0.01, chunk, step0=step, **kw), t_end=t_end[idx])
+        ens.indicators()
+        done += int(ens.n_exec.sum()) - before
+        step += chunk
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": done / el, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{n_sample} strided shell states, k = 6 FP64 vectors, {step} RK4 steps "
+                      f"({done} orbit-steps in {el:.1f} s)"}
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -524,7 +587,10 @@ def run_fput(args):
                                  "qr_every": args.qr_every,
                                  "launch": "one CUDA graph, concurrent branches" if args.fput_batch
                                            else "one launch per N"},
-                      "per_N": per_n}))
+                      "per_N": per_n,
+                      **({} if args.no_cpu_baseline else
+                         {"cpu_baseline": cpu_fput_sample(Ns, args.chunk, qr, args.cpu_budget,
+                                                          args.integrator)})}))
     return 0
 
 
@@ -647,7 +713,9 @@ def run_quartic(args):
                                  "launch": "persistent work queue" if args.persistent
                                            else "compacted 500-step chunks (CUDA graph)",
                                  "t_window": [args.warmup * args.chunk * 0.01, step * 0.01],
-                                 "early_exited": int((st == chs.ORBIT_EARLY_CHAOTIC).sum())}}))
+                                 "early_exited": int((st == chs.ORBIT_EARLY_CHAOTIC).sum())},
+                      **({} if args.no_cpu_baseline else
+                         {"cpu_baseline": cpu_quartic_sample(100, args.cpu_budget)})}))
     return 0
 
 
