@@ -794,6 +794,57 @@ def run_integrators(args):
     return 0
 
 
+def run_saturation(args):
+    """GPU saturation curve of the paper's Henon-Heiles experiment (Sec. Examples:
+    time per initial condition against the number of initial conditions, SALI
+    with 2 deviation vectors): section grids at E = 1/8 of 2^10 ... 2^20 cells,
+    --chunk steps of the chosen integrator (h = 0.01; DOP853 at the same step)
+    plus SALI, timed with CUDA events; one JSON line with the curve."""
+    import torch
+
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+
+    cuda_build.build()
+    chs.load()
+    from paper_2507_00622_gb300.inputs import hh_section_box
+
+    E = 1.0 / 8.0
+    y0, y1, p0, p1 = hh_section_box(E)
+    S = chs.System(chs.HENON_HEILES, 2)
+    integ = chs.DOP853 if args.integrator == "dop853" else chs.RK4
+    kw = dict(n_dev=2, ld_p=0.5, escape_r2=4.0, sample_every=100, integrator=integ)
+    stream = torch.cuda.current_stream()
+    curve = []
+    for e in range(10, 21, 2):
+        side = 1 << (e // 2)
+        n = side * side
+        ics = torch.empty((4, n), dtype=torch.float64, device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        chs.chs_section_grid_ics(S.h, E, y0, y1, side, p0, p1, side, ics, st)
+        ens = chs.DeviceEnsemble.empty(n, 4, 2)
+        abi = ens.abi()
+        sali = torch.empty(n, dtype=torch.float64, device="cuda")
+        times = []
+        for rep in range(1 + max(1, args.steps)):
+            chs.chs_ensemble_init(S.h, chs.params(0.01, 1, **kw), abi, ics, st)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            chs.chs_integrate_batch(S.h, chs.params(0.01, args.chunk, **kw), abi, stream)
+            chs.chs_indicators(S.h, chs.params(0.01, 0, **kw), abi, sali=sali, stream=stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                times.append(ev0.elapsed_time(ev1))
+        ms = float(np.median(times))
+        valid = int((st == 0).sum())
+        curve.append({"n_ics": n, "valid": valid, "ms": ms, "us_per_ic": 1e3 * ms / valid,
+                      "orbit_steps_per_s": valid * args.chunk / (ms / 1e3)})
+    print(json.dumps({"workload": "henon_heiles_E1/8_saturation_sali_k2_ld",
+                      "integrator": args.integrator, "steps": args.chunk, "dt": 0.01, "curve": curve}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -809,8 +860,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
-    ap.add_argument("--workload", choices=["grid", "fput", "classify", "quartic", "integrators"],
-                    default="grid")
+    ap.add_argument("--workload", choices=["grid", "fput", "classify", "quartic", "integrators",
+                                           "saturation"], default="grid")
     ap.add_argument("--quartic-orbits", type=int, default=4_194_304)
     ap.add_argument("--persistent", action="store_true",
                     help="quartic workload: one persistent work-queue launch per bench step")
@@ -831,6 +882,8 @@ def main():
         return run_classify(args)
     if args.workload == "integrators":
         return run_integrators(args)
+    if args.workload == "saturation":
+        return run_saturation(args)
     if args.workload == "quartic":
         return run_quartic(args)
     if args.impl == "reference":
