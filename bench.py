@@ -594,6 +594,139 @@ def run_fput(args):
     return 0
 
 
+def fput_ens_flops_per_step(N: int, k: int) -> int:
+    """Algorithmic FP64 flops of one accepted DOP853 step of an FPUT ensemble
+    orbit with k deviation vectors (FMA = 2): 340 per (vector, row pair) as in
+    fput_dp_flops_per_orbit_step, the orbit's stages ~240 N, the error norm ~12 N."""
+    return 340 * k * N + 252 * N
+
+
+def cpu_fput_gali_sample(Ns, n_orbits: int, tol: float, budget_s: float, n_sample: int = 16,
+                         t_sample: float = 50.0):
+    """The oracle on the host cores for the FPU GALI_4 workload: n_sample of the
+    bench's orbits per chain length, adaptive DOP 8(5) at the bench's tolerance
+    from t = 0 to t_sample (repeated while the chain length's share of budget_s
+    lasts); the rate is that of the bench's mix (orbit-steps of every chain
+    length in the proportion the GPU run took them)."""
+    import oracle as O
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+
+    parts, rates = [], {}
+    for N in Ns:
+        Q, P = normal_mode_draws(2000 + N, N, n_orbits)
+        ics = O.fput_mode_ics(O.fput(N), Q[:, :n_sample], P[:, :n_sample], np.full(n_sample, 0.1 * N))
+        prm = O.params(0.05, 10**9, n_dev=4, sample_every=100, integrator=O.DOP853)
+        t0 = time.perf_counter()
+        done = 0
+        while True:
+            e = O.Ensemble(O.fput(N), prm, ics, seed=7)
+            e.integrate_adaptive(prm, t_sample, tol, tol)
+            e.indicators()
+            done += int(e.n_exec.sum())
+            if time.perf_counter() - t0 >= budget_s / len(Ns):
+                break
+        el = time.perf_counter() - t0
+        rates[N] = done / el
+        parts.append(f"N={N}: {done} orbit-steps of {n_sample} orbits to t={t_sample:g} in {el:.1f} s")
+    return rates, {"cores": O.max_threads(), "kind": "oracle", "sample": "; ".join(parts)}
+
+
+def run_fput_gali(args):
+    """The FPU timing experiment of Sec. Examples: for every chain length N, 1e3
+    random normal-mode orbits (energy density 0.1) with k = 4 deviation vectors
+    integrated by adaptive DOP 8(5) (atol = rtol = --gali-tol) from t = 0 to
+    tau = --gali-tau, then GALI_2..4.  One bench step is the whole experiment
+    (set-up, integration and indicators for every N); per-N times by CUDA events."""
+    import torch
+
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+
+    cuda_build.build()
+    chs.load()
+    Ns = [int(v) for v in args.fput_n.split(",")]
+    n, k, tau, tol = args.gali_orbits, 4, args.gali_tau, args.gali_tol
+    runs = []
+    for N in Ns:
+        S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
+        Q, P = normal_mode_draws(2000 + N, N, n)
+        ics = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+        chs.chs_fput_mode_ics(S.h, n, torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(),
+                              torch.full((n,), 0.1 * N, dtype=torch.float64, device="cuda"), ics)
+        ens = chs.DeviceEnsemble.empty(n, 2 * N, k)
+        t = torch.empty(n, dtype=torch.float64, device="cuda")
+        h = torch.empty(n, dtype=torch.float64, device="cuda")
+        nr = torch.zeros(n, dtype=torch.int64, device="cuda")
+        gali = torch.empty((k - 1, n), dtype=torch.float64, device="cuda")
+        runs.append((N, S, ics, ens, t, h, nr, gali))
+    kw = dict(n_dev=k, ld_p=0.0, sample_every=100, integrator=chs.DOP853, seed=7)
+    ad = chs.Adaptive(tau, tol, tol, 0.0)
+    stream = torch.cuda.current_stream()
+
+    def one(N, S, ics, ens, t, h, nr, gali):
+        abi = ens.abi(with_ld=False)
+        chs.chs_ensemble_init(S.h, chs.params(0.05, 1, **kw), abi, ics)
+        t.zero_()
+        h.fill_(0.05)
+        nr.zero_()
+        chs.chs_integrate_adaptive(S.h, chs.params(0.05, 10**9, **kw), ad, abi, t, h, None, None, nr)
+        chs.chs_indicators(S.h, chs.params(0.05, 0, **kw), abi, 0, 0, None, gali, None, None)
+
+    for _ in range(args.warmup):
+        for r in runs:
+            one(*r)
+    torch.cuda.synchronize()
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in runs] for _ in range(args.steps)]
+    clocks = ClockSampler(None)
+    clocks.start()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        for j, r in enumerate(runs):
+            evs[i][j][0].record(stream)
+            one(*r)
+            evs[i][j][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    per_n, steps_by_n = {}, {}
+    total_steps = 0
+    for j, (N, S, ics, ens, t, h, nr, gali) in enumerate(runs):
+        ms = float(np.mean([evs[i][j][0].elapsed_time(evs[i][j][1]) for i in range(args.steps)]))
+        acc = int(ens.n_exec.sum())
+        rej = int(nr.sum())
+        st = ens.status.cpu().numpy()
+        g4 = gali[k - 2].cpu().numpy()
+        steps_by_n[N] = acc
+        total_steps += acc
+        tf = (acc * fput_ens_flops_per_step(N, k) + rej * 252 * N) / (ms / 1e3) / 1e12
+        per_n[str(N)] = {"s_per_run": ms / 1e3, "us_per_orbit": 1e3 * ms / n,
+                         "accepted_steps_per_orbit": acc / n, "rejected_per_orbit": rej / n,
+                         "orbit_steps_per_s": acc / (ms / 1e3), "fp64_tflops": tf,
+                         "frac_of_fp64_peak": tf / fp64_peak_tflops(clk["sm_mhz"] or 2070.0),
+                         "max_dH": float(ens.dh_max.max().item()),
+                         "status_ok": int((st == 0).sum()),
+                         "gali4_median": float(np.median(g4[st == 0])) if (st == 0).any() else None}
+    value = total_steps * args.steps / (total_ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fpu_gali4_adaptive_dop853", "N": Ns, "orbits_per_N": n,
+                       "k": k, "tau": tau, "atol": tol, "rtol": tol, "energy_density": 0.1,
+                       "bench_step": "init + adaptive integration to tau + GALI_2..4, every N"},
+            "clocks": clk, "per_N": per_n}
+    if not args.no_cpu_baseline:
+        rates, meta = cpu_fput_gali_sample(Ns, n, tol, args.cpu_budget)
+        # the GPU run's mix of orbit-steps over the chain lengths
+        inv = sum(steps_by_n[N] / total_steps / rates[N] for N in Ns)
+        line["cpu_baseline"] = {"value": 1.0 / inv, "unit": UNIT, **meta}
+    print(json.dumps(line))
+    return 0
+
+
 def classify_result(n_side: int, final_steps: int, confidence=None) -> dict:
     """Time to classify a Henon-Heiles section grid (E = 1/8, final t = steps * 0.01)
     by the plain form (FP64 vectors, every orbit to the end) and by the fast form
@@ -861,7 +994,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--workload", choices=["grid", "fput", "classify", "quartic", "integrators",
-                                           "saturation"], default="grid")
+                                           "saturation", "fput_gali"], default="grid")
     ap.add_argument("--quartic-orbits", type=int, default=4_194_304)
     ap.add_argument("--persistent", action="store_true",
                     help="quartic workload: one persistent work-queue launch per bench step")
@@ -875,6 +1008,9 @@ def main():
     ap.add_argument("--fput-orbits", type=int, default=4096)
     ap.add_argument("--qr-every", default="10", help="QR interval of the FPUT run, or 'auto' (autotuner)")
     ap.add_argument("--fput-batch", action="store_true", help="all chain lengths in one CUDA graph")
+    ap.add_argument("--gali-orbits", type=int, default=1000, help="fput_gali: orbits per chain length")
+    ap.add_argument("--gali-tau", type=float, default=1000.0, help="fput_gali: integration time")
+    ap.add_argument("--gali-tol", type=float, default=1e-8, help="fput_gali: atol = rtol")
     args = ap.parse_args()
     if args.workload == "fput":
         return run_fput(args)
@@ -886,6 +1022,8 @@ def main():
         return run_saturation(args)
     if args.workload == "quartic":
         return run_quartic(args)
+    if args.workload == "fput_gali":
+        return run_fput_gali(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

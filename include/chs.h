@@ -195,9 +195,12 @@ chs_status chs_shell_ics(chs_system s, int64_t n, const double* dirs, const doub
  * vec_precision) or,
  * when w_in is NULL, seeded on the device: component c of vector j of orbit o
  * is the m-th SplitMix64 output (m = (o*k + j)*d + c + 1) of the stream seeded
- * with p->seed, mapped to [-1, 1) by its top 53 bits.  Vectors are normalised
- * when p->renorm is set.  In FP32 mode the normalised vectors are factorised
- * in FP64 into the frame Q and triangle R described at chs_ensemble. */
+ * with p->seed, mapped to [-1, 1) by its top 53 bits, and normalised.  Every
+ * vector is normalised (once more, for seeded ones) when p->renorm is set.  In
+ * FP32 mode the normalised vectors are factorised in FP64 into the frame Q and
+ * triangle R described at chs_ensemble.
+ * FPUT chains (Eq. ham_FPU, N in {4, 8, 16, 32, 64}) take FP64 vectors
+ * (k <= 6) and no LD (ld_p = 0); other N return CHS_E_UNSUPPORTED. */
 chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemble* e,
                              const double* ics, const int32_t* ic_status, const void* w_in,
                              void* stream);
@@ -222,7 +225,9 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
  * ENERGY_DRIFT; with early_exit, SALI < sali_threshold -> frozen EARLY_CHAOTIC.
  * An orbit with t_end stops after t_end[o] total steps.  Splitting a run into
  * calls with consecutive step0 gives bit-identical results.  Supported: HENON_HEILES, HARMONIC, INVERTED
- * (k <= 4) and QUARTIC3 (k <= 6). */
+ * (k <= 4), QUARTIC3 (k <= 6) and FPUT (N in {4, 8, 16, 32, 64}, k <= 6, FP64
+ * vectors, no LD; the vectors advance through the same Runge-Kutta stages as
+ * the chain, with the tridiagonal Hessian of Eq. ham_eqs_FPU). */
 chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ensemble* e,
                                void* stream);
 
@@ -259,7 +264,8 @@ typedef struct {
  * stages are computed only for accepted trials).  p->dt, p->step0 and e->t_end
  * are not used (t_end must be NULL).  Forward in time only (t_final > t).
  * Supported: HENON_HEILES, HARMONIC,
- * INVERTED (k <= 4), QUARTIC3 (k <= 6); FP64 vectors. */
+ * INVERTED (k <= 4), QUARTIC3 (k <= 6), FPUT (N in {4, 8, 16, 32, 64},
+ * k <= 6, no LD); FP64 vectors. */
 chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_adaptive* a,
                                   const chs_ensemble* e, double* t, double* h, double* err_last,
                                   double* err_max, int64_t* n_rejected, void* stream);
@@ -272,7 +278,8 @@ chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_a
  * lane idle until the queue runs dry, in one launch.  `work` is caller-owned
  * device scratch of at least 8 bytes, 8-byte aligned (the queue counter; reset
  * by the call).  Calls that share a work buffer and overlap on the GPU race.
- * Supported: as chs_integrate_batch, both vector precisions and integrators. */
+ * Supported: the systems of chs_integrate_batch except FPUT, both vector
+ * precisions and integrators. */
 chs_status chs_integrate_persistent(chs_system s, const chs_params* p, const chs_ensemble* e,
                                     void* work, size_t work_bytes, void* stream);
 
@@ -288,7 +295,8 @@ size_t chs_compact_work_size(int64_t n_orbits);
  * the handle and reused while the ensemble pointers, sizes and parameters are
  * unchanged.  `work` is caller-owned device scratch of at least
  * chs_compact_work_size(n) bytes, 256-byte aligned; its contents are
- * overwritten.  Calls that share a work buffer and overlap on the GPU race. */
+ * overwritten.  Calls that share a work buffer and overlap on the GPU race.
+ * Supported: the systems of chs_integrate_batch except FPUT. */
 chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_ensemble* e,
                                    int32_t chunk_steps, void* work, size_t work_bytes,
                                    void* stream);
@@ -327,7 +335,8 @@ chs_status chs_integrate_compacted_static(chs_system s, const chs_params* p, con
  *                       indicators and neighbouring trajectories):
  *                         D_L = 1/4 sum_dir |LD(+) - LD(-)| / LD,
  *                         S_L = 1/2 sum_dir |2 - (LD(+) + LD(-)) / LD|;
- *                       NaN on the border and next to any non-OK cell.
+ *                       NaN on the border and next to any non-OK cell
+ *                       (Henon-Heiles grids; FPUT returns CHS_E_UNSUPPORTED).
  * Any output may be NULL.  FORBIDDEN orbits get NaN indicators. */
 chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble* e,
                           int32_t grid_ny, int32_t grid_npy, double* sali_out,

@@ -73,6 +73,21 @@ int max_dev(const chs::SysPar& sp)
     return sp.n_dof == 2 ? 4 : 6;
 }
 
+// Ensembles (init, fixed and adaptive integration, indicators) run for the
+// one-orbit-per-thread systems and for FPUT chains of N in {4, 8, 16, 32, 64}
+// with FP64 vectors and no LD.  Call after check_params.
+chs_status check_ens_model(const chs::SysPar& sp, const chs_params* p)
+{
+    if (chs::small_model(sp.model)) return ok();
+    if (sp.model != CHS_FPUT) return fail(CHS_E_UNSUPPORTED, "ensembles are not implemented for model %d", sp.model);
+    if (!chs::fput_ens_supported(sp.n_dof))
+        return fail(CHS_E_UNSUPPORTED, "FPUT ensembles support N in {4, 8, 16, 32, 64}");
+    if (p->vec_precision != CHS_VEC_FP64 && p->n_dev > 0)
+        return fail(CHS_E_UNSUPPORTED, "FPUT ensembles carry FP64 deviation vectors");
+    if (p->ld_p != 0.0) return fail(CHS_E_UNSUPPORTED, "FPUT ensembles do not accumulate the LD: ld_p must be 0");
+    return ok();
+}
+
 chs_status check_params(const chs_params* p, const chs::SysPar& sp)
 {
     if (!p) return fail(CHS_E_INVALID, "params is NULL");
@@ -289,12 +304,15 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
 {
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
-    if (!chs::small_model(s->sp.model))
-        return fail(CHS_E_UNSUPPORTED, "ensembles are implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ens_model(s->sp, p)) != CHS_OK) return r;
     if ((r = check_ensemble(e, p)) != CHS_OK) return r;
     if (e->n_orbits == 0) return ok();
     if (!ics) return fail(CHS_E_INVALID, "ics is NULL");
+    if (s->sp.model == CHS_FPUT)
+        return cuda_status(chs::launch_fput_ens_init(s->sp, p->n_dev, p->renorm, p->seed, ics, ic_status, w_in,
+                                                     ens_ptrs(e), as_stream(stream)),
+                           "FPUT ensemble init launch");
     return cuda_status(chs::launch_init(s->sp, p->n_dev, p->vec_precision, p->renorm, p->seed, ics,
                                         ic_status, w_in, ens_ptrs(e), as_stream(stream)),
                        "ensemble init launch");
@@ -304,11 +322,14 @@ chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ense
 {
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
-    if (!chs::small_model(s->sp.model))
-        return fail(CHS_E_UNSUPPORTED, "integration is implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ens_model(s->sp, p)) != CHS_OK) return r;
     if ((r = check_ensemble(e, p)) != CHS_OK) return r;
     if (e->n_orbits == 0 || p->n_steps == 0) return ok();
+    if (s->sp.model == CHS_FPUT)
+        return cuda_status(chs::launch_fput_ens(s->sp, p->integrator, p->n_dev, step_args(p), ens_ptrs(e),
+                                                as_stream(stream)),
+                           "FPUT ensemble integrate launch");
     return cuda_status(launch_selected(s->sp, p, step_args(p), ens_ptrs(e), nullptr, as_stream(stream)),
                        "integrate launch");
 }
@@ -319,9 +340,8 @@ chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_a
 {
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
-    if (!chs::small_model(s->sp.model))
-        return fail(CHS_E_UNSUPPORTED, "integration is implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ens_model(s->sp, p)) != CHS_OK) return r;
     if ((r = check_ensemble(e, p)) != CHS_OK) return r;
     if (p->integrator != CHS_DOP853) return fail(CHS_E_INVALID, "adaptive runs need integrator = CHS_DOP853");
     if (!a) return fail(CHS_E_INVALID, "adaptive controls are NULL");
@@ -334,6 +354,10 @@ chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_a
     if (e->n_orbits == 0 || p->n_steps == 0) return ok();
     const chs::AdaptArgs ad{a->t_final, a->rtol, a->atol, a->h_max};
     const chs::AdaptPtrs ap{t, h, err_last, err_max, n_rejected};
+    if (s->sp.model == CHS_FPUT)
+        return cuda_status(chs::launch_fput_ens_adapt(s->sp, p->n_dev, step_args(p), ad, ens_ptrs(e), ap,
+                                                      as_stream(stream)),
+                           "adaptive FPUT ensemble launch");
     return cuda_status(chs::launch_integrate_adaptive(s->sp, p->n_dev, p->ld_p > 0.0, step_args(p), ad,
                                                       ens_ptrs(e), ap, as_stream(stream)),
                        "adaptive integrate launch");
@@ -345,7 +369,7 @@ chs_status chs_integrate_persistent(chs_system s, const chs_params* p, const chs
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if (!chs::small_model(s->sp.model))
-        return fail(CHS_E_UNSUPPORTED, "integration is implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
+        return fail(CHS_E_UNSUPPORTED, "persistent runs are implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
     if ((r = check_ensemble(e, p)) != CHS_OK) return r;
     if (!work || ((uintptr_t)work & 7u)) return fail(CHS_E_INVALID, "work must be an 8-byte aligned device buffer");
@@ -371,7 +395,7 @@ chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if (!chs::small_model(s->sp.model))
-        return fail(CHS_E_UNSUPPORTED, "integration is implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
+        return fail(CHS_E_UNSUPPORTED, "compacted runs are implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
     if ((r = check_ensemble(e, p)) != CHS_OK) return r;
     if (chunk_steps < 1) return fail(CHS_E_INVALID, "chunk_steps must be >= 1");
@@ -445,10 +469,11 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
 {
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
-    if (!chs::small_model(s->sp.model))
-        return fail(CHS_E_UNSUPPORTED, "indicators are implemented for HENON_HEILES, HARMONIC, INVERTED, QUARTIC3");
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
+    if ((r = check_ens_model(s->sp, p)) != CHS_OK) return r;
     if ((r = check_ensemble(e, p)) != CHS_OK) return r;
+    if (s->sp.model == CHS_FPUT && ld_ind_out)
+        return fail(CHS_E_UNSUPPORTED, "LD indicators are for the Henon-Heiles section grid");
     if ((sali_out || label_out) && p->n_dev < 2) return fail(CHS_E_INVALID, "SALI and labels need n_dev >= 2");
     if (gali_out && p->n_dev < 2) return fail(CHS_E_INVALID, "GALI needs n_dev >= 2");
     if (ld_ind_out) {
@@ -459,6 +484,12 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
     if (e->n_orbits == 0) return ok();
     cudaStream_t st = as_stream(stream);
     const chs::EnsPtrs ep = ens_ptrs(e);
+    if (s->sp.model == CHS_FPUT) {
+        if (!sali_out && !gali_out && !label_out) return ok();
+        return cuda_status(chs::launch_fput_ens_indicators(s->sp, p->n_dev, p->sali_threshold, ep, sali_out,
+                                                           gali_out, label_out, st),
+                           "FPUT indicator launch");
+    }
     if (sali_out || gali_out || label_out) {
         r = cuda_status(chs::launch_indicators(s->sp, p->n_dev, p->vec_precision, p->sali_threshold, ep,
                                                sali_out, gali_out, label_out, st),

@@ -119,9 +119,19 @@ cudaError_t launch_mlp_backward(const void* P, const float* X, const void* act, 
 cudaError_t launch_mlp_adam(float* W, float* m, float* v, const float* g, float lr, float b1, float b2,
                             float eps, int step, void* Wb, cudaStream_t st);
 
+// FPUT ensembles with k <= 6 FP64 deviation vectors (k_fput_ens.cu).
+cudaError_t launch_fput_ens_init(const SysPar& sp, int k, int renorm, uint64_t seed, const double* ics,
+                                 const int32_t* ic_status, const void* w_in, const EnsPtrs& e,
+                                 cudaStream_t st);
+cudaError_t launch_fput_ens(const SysPar& sp, int integrator, int k, const StepArgs& a, const EnsPtrs& e,
+                            cudaStream_t st);
+cudaError_t launch_fput_ens_indicators(const SysPar& sp, int k, double thr, const EnsPtrs& e, double* sali,
+                                       double* gali, int8_t* label, cudaStream_t st);
+
 // Which systems each kernel family supports.
 bool small_model(int model);
 bool fput_lyap_supported(int n_dof);
+bool fput_ens_supported(int n_dof);
 
 // Appends orbit o to ol.next when keep is set, one atomic per converged group of
 // lanes.

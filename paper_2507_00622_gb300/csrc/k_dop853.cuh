@@ -53,4 +53,9 @@ cudaError_t launch_lyap_small_adapt(const SysPar& sp, const StepArgs& a, const A
                                     const double* ics, const int32_t* ic_status, double* lambda,
                                     int32_t* status, int64_t* n_acc, int64_t* n_rej, cudaStream_t st);
 
+// Adaptive DOP 8(5) on FPUT ensembles (k_fput_ens_adapt.cu; the
+// chs_integrate_adaptive contract without LD).
+cudaError_t launch_fput_ens_adapt(const SysPar& sp, int k, const StepArgs& a, const AdaptArgs& ad,
+                                  const EnsPtrs& e, const AdaptPtrs& ap, cudaStream_t st);
+
 }  // namespace chs

@@ -7,17 +7,9 @@
 // none (its propagator is a degree-12 polynomial in the stage Jacobians), and
 // running the 2N deviation vectors through the twelve stages side by side
 // would need 11 stage copies of the 2N x 2N matrix W (1.4 MB per orbit at
-// N = 64).  So a step runs in two phases:
-//
-//   phase 1  the orbit: thread l of the orbit's 2N threads owns component l and
-//            its stage derivatives (in registers); the stage states pass
-//            through a double-buffered shared array (one barrier per stage),
-//            and each stage leaves its N + 1 bond stiffnesses V''(D_b) behind;
-//   phase 2  the columns of W, one at a time per warp segment: L = min(N, 32)
-//            lanes split the column's N (q, p) row pairs, keep the column's
-//            stage derivatives in registers and exchange the tridiagonal
-//            neighbours q_{i-1}, q_{i+1} by warp shuffles.  No barrier, no
-//            stage storage in memory.
+// N = 64).  So a step runs in the two phases of fput_stages.cuh: the orbit
+// through its stages (one thread per component), then the columns of W one at
+// a time per warp segment, with their stage derivatives in registers.
 //
 // W lives in shared memory column-major with a padded column stride 2N + 1, so
 // that both a warp reading down a column and the QR's thread-per-column sweeps
@@ -28,7 +20,7 @@
 // of a trial is a sum over the orbit's 2N components, formed by every thread of
 // the orbit from a shared array in the same order; the columns of W advance
 // only for accepted trials.  A block loops until all of its orbits are done.
-#include "dop853.cuh"
+#include "fput_stages.cuh"
 
 namespace chs {
 namespace {
@@ -38,16 +30,12 @@ struct FputDpCfg {
     static constexpr int D = 2 * N;
     static constexpr int G = D >= 128 ? 1 : 128 / D;  // orbits per block
     static constexpr int THREADS = G * D;             // 128
-    static constexpr int L = N < 32 ? N : 32;          // lanes per column
-    static constexpr int R = N / L;                    // row pairs per lane
-    static constexpr int CPW = 32 / L;                 // columns per warp at a time
     static constexpr int WS = D + 1;                   // padded column stride
     // doubles per orbit: W, two stage-state buffers, 12 stage stiffness rows,
     // two error-sum rows, control words
     static constexpr int PER = D * WS + 2 * D + 12 * (N + 1) + 2 * D + 4;
     static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
     static_assert(THREADS == 128, "one 128-thread block per orbit group");
-    static_assert((G * D) % (4 * CPW) == 0, "every warp takes the same number of columns");
 };
 
 // Offsets inside an orbit's shared slab.
@@ -60,167 +48,6 @@ struct FputDpSlab {
     static constexpr int ER = CS + 12 * (N + 1);    // [2][D] error sums
     static constexpr int CTL = ER + 2 * Cfg::D;     // [0] red, [1] any, [2] step of phase 2, [3] advance
 };
-
-struct FputDpCoef {
-    double k, a2, b3;  // V''(r) = k + 2 alpha r + 3 beta r^2
-    double alpha, beta;
-};
-
-__device__ __forceinline__ double fdv(const FputDpCoef& fc, double r)
-{
-    return r * fma(r, fma(fc.beta, r, fc.alpha), fc.k);  // V'(r)
-}
-
-__device__ __forceinline__ double fd2v(const FputDpCoef& fc, double r)
-{
-    return fma(r, fma(fc.b3, r, fc.a2), fc.k);  // V''(r)
-}
-
-// Phase 1 for component l of one orbit (every thread of the block calls it;
-// it has one barrier per stage).  Returns x_l + h sum_s b_s F_s; with ERR the
-// error sums err5 = sum_s e5_s F_s and err3 = sum_s (b_s - b3_s) F_s.
-template <int N, bool ERR>
-__device__ __forceinline__ double orbit_stages(const double xi, const double h, const int l,
-                                               double* slab, const FputDpCoef& fc, double& e5,
-                                               double& e3)
-{
-    using Sl = FputDpSlab<N>;
-    constexpr int D = 2 * N;
-    double* xb = slab + Sl::XB;
-    double* cs = slab + Sl::CS;
-    double F[12] = {};
-    double acc = 0.0, a5 = 0.0, a3 = 0.0;
-    dp::static_for<0, 12>([&](auto sc) {
-        constexpr int s = decltype(sc)::value;
-        double sum = 0.0;
-        dp::static_for<0, s>([&](auto jc) {
-            constexpr int j = decltype(jc)::value;
-            constexpr double c = dp::kA[s][j];
-            if constexpr (c != 0.0) sum = fma(c, F[j], sum);
-        });
-        double* xs = xb + (s & 1) * D;
-        xs[l] = (s == 0) ? xi : fma(h, sum, xi);
-        __syncthreads();
-        double f;
-        if (l < N) {
-            f = xs[N + l];
-        } else {
-            const int i = l - N;
-            const double qm = i > 0 ? xs[i - 1] : 0.0;
-            const double q0 = xs[i];
-            const double qp = i < N - 1 ? xs[i + 1] : 0.0;
-            f = fdv(fc, qp - q0) - fdv(fc, q0 - qm);
-        }
-        if (l <= N) {
-            const double qa = l < N ? xs[l] : 0.0;
-            const double qb = l > 0 ? xs[l - 1] : 0.0;
-            cs[s * (N + 1) + l] = fd2v(fc, qa - qb);
-        }
-        F[s] = f;
-        constexpr double cb = dp::kB[s], c5 = dp::kE5[s], c3 = dp::kB[s] - dp::kB3[s];
-        if constexpr (s == 0) {
-            acc = cb * f;
-            if constexpr (ERR) {
-                a5 = c5 * f;
-                a3 = c3 * f;
-            }
-        } else {
-            if constexpr (cb != 0.0) acc = fma(cb, f, acc);
-            if constexpr (ERR && c5 != 0.0) a5 = fma(c5, f, a5);
-            if constexpr (ERR && c3 != 0.0) a3 = fma(c3, f, a3);
-        }
-    });
-    if constexpr (ERR) {
-        e5 = a5;
-        e3 = a3;
-    }
-    return fma(h, acc, xi);
-}
-
-// Phase 2: every column of every orbit g of the block with step(g) > 0 advances
-// through the twelve stages of w' = J_s w with that step.
-template <int N, class StepOf>
-__device__ __forceinline__ void columns(double* smem, StepOf step_of)
-{
-    using Cfg = FputDpCfg<N>;
-    using Sl = FputDpSlab<N>;
-    constexpr int D = Cfg::D, G = Cfg::G, PER = Cfg::PER, L = Cfg::L, R = Cfg::R, CPW = Cfg::CPW,
-                  WS = Cfg::WS;
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int seg = lane / L, r0 = lane % L;
-    for (int task = warp * CPW + seg; task < G * D; task += 4 * CPW) {
-        const int og = task / D, col = task % D;
-        double* slab = smem + og * PER;
-        const double h = step_of(og, slab);
-        // the whole warp takes part in the shuffles; columns of orbits that do
-        // not advance compute with h = 0 and are not written back
-        double* Wc = slab + col * WS;
-        const double* c_s = slab + Sl::CS;
-        double q[R], p[R];
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            q[k] = Wc[r0 + k * L];
-            p[k] = Wc[N + r0 + k * L];
-        }
-        double Mq[12][R], Mp[12][R], aq[R], ap[R];
-        dp::static_for<0, 12>([&](auto sc) {
-            constexpr int s = decltype(sc)::value;
-            double wq[R], wp[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                double sq = 0.0, sp_ = 0.0;
-                dp::static_for<0, s>([&](auto jc) {
-                    constexpr int j = decltype(jc)::value;
-                    constexpr double c = dp::kA[s][j];
-                    if constexpr (c != 0.0) {
-                        sq = fma(c, Mq[j][k], sq);
-                        sp_ = fma(c, Mp[j][k], sp_);
-                    }
-                });
-                wq[k] = (s == 0) ? q[k] : fma(h, sq, q[k]);
-                wp[k] = (s == 0) ? p[k] : fma(h, sp_, p[k]);
-            }
-            // neighbours of row r = r0 + k L in the column (walls: 0)
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                double left = __shfl_up_sync(0xffffffffu, wq[k], 1, L);
-                double right = __shfl_down_sync(0xffffffffu, wq[k], 1, L);
-                if constexpr (R > 1) {
-                    // row blocks wrap from lane L-1 of block k-1 / lane 0 of block k+1
-                    const double prev_last = __shfl_sync(0xffffffffu, wq[k > 0 ? k - 1 : 0], L - 1, L);
-                    const double next_first = __shfl_sync(0xffffffffu, wq[k < R - 1 ? k + 1 : 0], 0, L);
-                    if (r0 == 0) left = k > 0 ? prev_last : 0.0;
-                    if (r0 == L - 1) right = k < R - 1 ? next_first : 0.0;
-                } else {
-                    if (r0 == 0) left = 0.0;
-                    if (r0 == L - 1) right = 0.0;
-                }
-                const int r = r0 + k * L;
-                const double cl = c_s[s * (N + 1) + r], cr = c_s[s * (N + 1) + r + 1];
-                Mq[s][k] = wp[k];
-                Mp[s][k] = fma(cr, right - wq[k], -cl * (wq[k] - left));
-            }
-            constexpr double cb = dp::kB[s];
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                if constexpr (s == 0) {
-                    aq[k] = cb * Mq[0][k];
-                    ap[k] = cb * Mp[0][k];
-                } else if constexpr (cb != 0.0) {
-                    aq[k] = fma(cb, Mq[s][k], aq[k]);
-                    ap[k] = fma(cb, Mp[s][k], ap[k]);
-                }
-            }
-        });
-        if (h > 0.0 || h < 0.0) {
-#pragma unroll
-            for (int k = 0; k < R; ++k) {
-                Wc[r0 + k * L] = fma(h, aq[k], q[k]);
-                Wc[N + r0 + k * L] = fma(h, ap[k], p[k]);
-            }
-        }
-    }
-}
 
 // Modified Gram-Schmidt of the orbit's W (thread l owns column l), when `mine`
 // is set for the orbit; every thread takes part in the barriers.  S += ln R_ll.
@@ -282,7 +109,7 @@ k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double*
     double* slab = smem + g * PER;
     double* red = slab + Sl::CTL;
 
-    const FputDpCoef fc = {sp.kk, 2.0 * sp.alpha, 3.0 * sp.beta, sp.alpha, sp.beta};
+    const fs::Coef fc = fs::coef_of(sp);
     int32_t st = valid ? (ic_status ? ic_status[o] : CHS_ORBIT_OK) : CHS_ORBIT_FORBIDDEN;
     double xi = valid ? ics[(int64_t)l * n + o] : 0.0;
 
@@ -309,9 +136,9 @@ k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double*
     int64_t until = a.sample_every > 0 ? a.sample_every : -1;
     for (int64_t step = 1; step <= a.n_steps; ++step) {
         double e5, e3;
-        xi = orbit_stages<N, false>(xi, h, l, slab, fc, e5, e3);
+        xi = fs::orbit_stages<N, fs::TabDop853, false>(xi, h, l, slab + Sl::XB, slab + Sl::CS, fc, e5, e3);
         __syncthreads();  // every stage stiffness is written
-        columns<N>(smem, [&](int, const double*) { return h; });
+        fs::columns<N, fs::TabDop853, G, PER, WS, Sl::CS>(smem, D, [&](int, const double*) { return h; });
         __syncthreads();  // W complete; stage stiffnesses free
         if (--until_qr == 0 || step == a.n_steps) {
             until_qr = a.qr_every;
@@ -349,7 +176,7 @@ k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const i
     double* ctl = slab + Sl::CTL;
     double* er = slab + Sl::ER;
 
-    const FputDpCoef fc = {sp.kk, 2.0 * sp.alpha, 3.0 * sp.beta, sp.alpha, sp.beta};
+    const fs::Coef fc = fs::coef_of(sp);
     int32_t st = valid ? (ic_status ? ic_status[o] : CHS_ORBIT_OK) : CHS_ORBIT_FORBIDDEN;
     double xi = valid ? ics[(int64_t)l * n + o] : 0.0;
     // a non-finite initial state is never accepted: it ends as STEP_FAIL
@@ -394,7 +221,7 @@ k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const i
         if (!__syncthreads_or(active)) break;
 
         double e5 = 0.0, e3 = 0.0;
-        const double xn = orbit_stages<N, true>(xi, hh, l, slab, fc, e5, e3);
+        const double xn = fs::orbit_stages<N, fs::TabDop853, true>(xi, hh, l, slab + Sl::XB, slab + Sl::CS, fc, e5, e3);
         // error norm over the orbit's components, summed in index order by
         // every thread of the orbit
         const double sc = ad.atol + ad.rtol * fmax(fabs(xi), fabs(xn));
@@ -412,7 +239,7 @@ k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const i
         if (l == 0) ctl[2] = accept ? hh : 0.0;
         __syncthreads();  // stage stiffnesses and phase-2 steps are in place
 
-        columns<N>(smem, [&](int, const double* sl) { return sl[Sl::CTL + 2]; });
+        fs::columns<N, fs::TabDop853, G, PER, WS, Sl::CS>(smem, D, [&](int, const double* sl) { return sl[Sl::CTL + 2]; });
         if (active) {
             const double r8 = (err > 0.0) ? 1.0 / sqrt(sqrt(sqrt(err))) : 0.0;
             if (accept) {

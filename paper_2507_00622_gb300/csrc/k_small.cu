@@ -64,9 +64,10 @@ k_init(const SysPar sp, const int renorm, const uint64_t seed, const double* __r
                 v[c] = __dsub_rn(__dmul_rn(2.0, __dmul_rn((double)(z >> 11), 0x1.0p-53)), 1.0);
             }
         }
-        if (renorm) {
-            // sum of squares in index order, no contraction: the same rounding as a
-            // plain sequential loop
+        // seeded vectors are normalised, and every vector once more with renorm;
+        // sums of squares in index order, no contraction: the same rounding as a
+        // plain sequential loop
+        for (int pass = w_in ? 1 : 0; pass < 1 + renorm; ++pass) {
             double acc = 0.0;
 #pragma unroll
             for (int c = 0; c < D; ++c) acc = __dadd_rn(acc, __dmul_rn(v[c], v[c]));

@@ -53,12 +53,18 @@ def test_section_grid_bit_exact(E, ny, npy):
 
 
 def test_seeded_vectors_bit_exact():
+    """Seeded vectors are the normalised SplitMix64 draws (the oracle's
+    seed_vectors, bit for bit, without renorm) and are normalised once more
+    with renorm, as the oracle's ensemble set-up does."""
     g = _grid(1 / 6, 19, 23)
     ics, st = O.grid_ics(*g)
     for k in (2, 4):
-        out = gpu_run(HH, 2, ics, st, dt=0.01, n_steps=0, k=k, seed=12345)
         ref = O.seed_vectors(12345, ics.shape[1], k, 4)
+        out = gpu_run(HH, 2, ics, st, dt=0.01, n_steps=0, k=k, seed=12345, renorm=False)
         np.testing.assert_array_equal(out["w"].view(np.int64), ref.view(np.int64))
+        out = gpu_run(HH, 2, ics, st, dt=0.01, n_steps=0, k=k, seed=12345)
+        e = O.Ensemble(O.henon_heiles(), O.params(0.01, 1, n_dev=k), ics, st, seed=12345)
+        np.testing.assert_array_equal(out["w"].view(np.int64), e.w.view(np.int64))
 
 
 def test_fput_mode_ics_match_oracle():
