@@ -4,8 +4,10 @@
 //
 // An ensemble orbit carries its state x (2N components, one per thread of the
 // orbit's 2N threads) and k <= 6 deviation vectors (columns in shared memory,
-// advanced by the phase 2 of fput_stages.cuh).  A block of 128 threads holds
-// G = 128 / 2N orbits (one orbit per block at N = 64).
+// advanced by the phase 2 of fput_stages.cuh).  A block holds one warp's worth
+// of orbits, G = 32 / 2N, for N <= 16, and one orbit (2N threads) above: small
+// blocks spread an ensemble of a thousand orbits over every SM, and the FP64
+// pipe needs only a few warps per SM.
 #pragma once
 
 #include "fput_stages.cuh"
@@ -16,8 +18,8 @@ namespace fe {
 template <int N, class Tab>
 struct Cfg {
     static constexpr int D = 2 * N;
-    static constexpr int G = D >= 128 ? 1 : 128 / D;  // orbits per block
-    static constexpr int THREADS = 128;
+    static constexpr int G = D >= 32 ? 1 : 32 / D;  // orbits per block
+    static constexpr int THREADS = G * D;             // 32, 64 or 128
     static constexpr int WS = D;                       // column stride
     // slab of one orbit: kMaxDev columns, two stage-state buffers, the stage
     // stiffnesses, error-sum partials, warp partials of orbit sums, control
@@ -27,8 +29,7 @@ struct Cfg {
     static constexpr int RED = CS + Tab::S * (N + 1);  // [4] warp partials
     static constexpr int CTL = RED + 4;                // [0] step of phase 2
     static constexpr int PER = CTL + 4;
-    static_assert(G * D == THREADS, "one 128-thread block per orbit group");
-    static_assert(D <= 128, "N <= 64");
+    static_assert(THREADS % 32 == 0 && THREADS <= 128, "whole warps, N <= 64");
 };
 
 // Sum over the orbit's D threads, the same value (bit for bit) in each of

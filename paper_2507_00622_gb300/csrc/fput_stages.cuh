@@ -134,22 +134,29 @@ struct ColShape {
 // Phase 2: the kc columns of every orbit of the block (G orbits, each orbit's
 // slab at smem + g * PER, column c at + c * WS, stiffnesses at + CS) advance
 // through the stages of w' = J_s w with step step_of(g, slab); a step of 0
-// leaves the columns untouched.  With renorm set every updated column is
-// scaled to unit length.  Every lane of every warp must call this, and G must
-// be a multiple of ColShape<N>::CPW so that the segments of a warp take the
-// same number of columns (the shuffles run on full warps).
-template <int N, class Tab, int G, int PER, int WS, int CS, class StepOf>
+// leaves the columns untouched, and with SKIP a warp whose segments all have
+// step 0 skips the work (callers whose steps are never 0 leave SKIP off: the
+// vote changes the register allocation of the stage loop).  With renorm set
+// every updated column is scaled to unit length.  Every lane of every warp must call this: the segments of a warp
+// loop together (a segment past the last column computes on column 0 of orbit
+// 0 with step 0), so the shuffles always run on full warps.
+template <int N, class Tab, int G, int PER, int WS, int CS, bool SKIP, class StepOf>
 __device__ __forceinline__ void columns(double* smem, const int kc, StepOf step_of, const int renorm = 0)
 {
     constexpr int L = ColShape<N>::L, R = ColShape<N>::R, CPW = ColShape<N>::CPW;
-    static_assert(G % CPW == 0, "the segments of a warp take the same number of columns");
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int nwarps = blockDim.x / 32;
     const int seg = lane / L, r0 = lane % L;
-    for (int task = warp * CPW + seg; task < G * kc; task += nwarps * CPW) {
-        const int og = task / kc, col = task % kc;
+    const int total = G * kc;
+    for (int base = warp * CPW; base < total; base += nwarps * CPW) {
+        const int task = base + seg;
+        const bool real = task < total;
+        const int og = real ? task / kc : 0, col = real ? task % kc : 0;
         double* slab = smem + og * PER;
-        const double h = step_of(og, slab);
+        const double h = real ? step_of(og, slab) : 0.0;
+        if constexpr (SKIP) {
+            if (!__any_sync(0xffffffffu, h != 0.0)) continue;
+        }
         double* Wc = slab + col * WS;
         const double* c_s = slab + CS;
         double q[R], p[R];

@@ -28,14 +28,14 @@ namespace {
 template <int N>
 struct FputDpCfg {
     static constexpr int D = 2 * N;
-    static constexpr int G = D >= 128 ? 1 : 128 / D;  // orbits per block
-    static constexpr int THREADS = G * D;             // 128
+    static constexpr int G = D >= 32 ? 1 : 32 / D;  // orbits per block: one warp for N <= 16
+    static constexpr int THREADS = G * D;             // 32, 64 or 128
     static constexpr int WS = D + 1;                   // padded column stride
     // doubles per orbit: W, two stage-state buffers, 12 stage stiffness rows,
     // two error-sum rows, control words
     static constexpr int PER = D * WS + 2 * D + 12 * (N + 1) + 2 * D + 4;
     static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
-    static_assert(THREADS == 128, "one 128-thread block per orbit group");
+    static_assert(THREADS % 32 == 0 && THREADS <= 128, "whole warps, N <= 64");
 };
 
 // Offsets inside an orbit's shared slab.
@@ -138,7 +138,7 @@ k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double*
         double e5, e3;
         xi = fs::orbit_stages<N, fs::TabDop853, false>(xi, h, l, slab + Sl::XB, slab + Sl::CS, fc, e5, e3);
         __syncthreads();  // every stage stiffness is written
-        fs::columns<N, fs::TabDop853, G, PER, WS, Sl::CS>(smem, D, [&](int, const double*) { return h; });
+        fs::columns<N, fs::TabDop853, G, PER, WS, Sl::CS, false>(smem, D, [&](int, const double*) { return h; });
         __syncthreads();  // W complete; stage stiffnesses free
         if (--until_qr == 0 || step == a.n_steps) {
             until_qr = a.qr_every;
@@ -239,7 +239,7 @@ k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const i
         if (l == 0) ctl[2] = accept ? hh : 0.0;
         __syncthreads();  // stage stiffnesses and phase-2 steps are in place
 
-        fs::columns<N, fs::TabDop853, G, PER, WS, Sl::CS>(smem, D, [&](int, const double* sl) { return sl[Sl::CTL + 2]; });
+        fs::columns<N, fs::TabDop853, G, PER, WS, Sl::CS, true>(smem, D, [&](int, const double* sl) { return sl[Sl::CTL + 2]; });
         if (active) {
             const double r8 = (err > 0.0) ? 1.0 / sqrt(sqrt(sqrt(err))) : 0.0;
             if (accept) {

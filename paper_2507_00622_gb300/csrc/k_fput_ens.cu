@@ -132,7 +132,7 @@ k_fput_ens(const StepArgs a, const SysPar sp, const int K, const EnsPtrs e)
         const double xn = fs::orbit_stages<N, Tab, false>(xi, ho, l, slab + C::XB, slab + C::CS, fc, e5, e3);
         if (l == 0) slab[C::CTL] = ho;
         __syncthreads();  // stage stiffnesses and phase-2 steps in place
-        fs::columns<N, Tab, G, PER, WS, C::CS>(smem, K, [](int, const double* sl) { return sl[C::CTL]; },
+        fs::columns<N, Tab, G, PER, WS, C::CS, true>(smem, K, [](int, const double* sl) { return sl[C::CTL]; },
                                                a.renorm);
         __syncthreads();  // columns complete; stage buffers free
         const bool stepped = active;

@@ -84,7 +84,7 @@ k_fput_ens_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const in
         const bool accept = active && err < 1.0;
         if (l == 0) slab[C::CTL] = accept ? hh : 0.0;
         __syncthreads();  // stage stiffnesses and phase-2 steps in place
-        fs::columns<N, Tab, G, PER, WS, C::CS>(smem, K, [](int, const double* sl) { return sl[C::CTL]; },
+        fs::columns<N, Tab, G, PER, WS, C::CS, true>(smem, K, [](int, const double* sl) { return sl[C::CTL]; },
                                                a.renorm);
         __syncthreads();  // columns complete; stage buffers free
         if (active) {
