@@ -335,8 +335,15 @@ def run_gpu(args):
     dop = args.integrator == "dop853"
     if dop and vec_fp32:
         raise SystemExit("DOP853 runs with FP64 deviation vectors only")
+    block = 0
+    if not dop and args.block == "auto":
+        from paper_2507_00622_gb300 import autotune
+        block = autotune.tune_block_integrate(k=K_DEV, ld=True, vec_fp32=vec_fp32)["block_threads"]
+    elif not dop:
+        block = int(args.block)
     kw = dict(n_dev=K_DEV, ld_p=0.5, escape_r2=4.0, sample_every=100, seed=1 + rank,
-              vec_precision=vp, sali_threshold=1e-8, integrator=chs.DOP853 if dop else chs.RK4)
+              vec_precision=vp, sali_threshold=1e-8, integrator=chs.DOP853 if dop else chs.RK4,
+              block_threads=block)
     ens = chs.DeviceEnsemble.empty(n, 4, K_DEV, vec_fp32, device=dev)
     abi = ens.abi()
     chs.chs_ensemble_init(S.h, chs.params(DT, 1, **kw), abi, ics, ic_st)
@@ -446,6 +453,7 @@ def run_gpu(args):
                        "grid_per_gpu": [ny, npy], "n_orbits_per_gpu": ny * npy, "dt": DT,
                        "integrator": "DOP853 (fixed step)" if dop else "RK4",
                        "steps_per_bench_step": args.chunk,
+                       "block_threads": None if dop else (block or 128),
                        "t_window": [t_window0, t_window1], "t_end_of_full_run": 1e4,
                        "deviation_vectors": f"{K_DEV} x {'fp32' if vec_fp32 else 'fp64'}",
                        "l2": "inputs larger than L2: ensemble state %.0f MB per GPU" %
@@ -453,7 +461,7 @@ def run_gpu(args):
                        "parallelism": f"orbit-range shards x{world}, no data-path collective"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": None if dop else recorded_traffic(ny, vec_fp32),
+                         "traffic": None if dop or block not in (0, 128) else recorded_traffic(ny, vec_fp32),
                          "kernel": "k_integrate_dp<HenonHeiles,4,LD>" if dop else
                                    "k_integrate<HenonHeiles,4,LD>",
                          "flops_per_orbit_step": {"fp64": f64, "fp32": f32},
@@ -537,8 +545,17 @@ def run_fput(args):
         else:
             qr[N] = int(args.qr_every)
     dop = args.integrator == "dop853"
+    blk = {}
+    for N in Ns:
+        if dop:
+            blk[N] = 0  # the DOP853 kernel keeps its own block shape
+        elif args.block == "auto":
+            from paper_2507_00622_gb300 import autotune
+            blk[N] = autotune.tune_fput_block(N, qr_every=qr[N])["block_threads"]
+        else:
+            blk[N] = int(args.block)
     prms = {N: chs.params(0.05, args.chunk, qr_every=qr[N], sample_every=100,
-                          integrator=chs.DOP853 if dop else chs.RK4) for N in Ns}
+                          integrator=chs.DOP853 if dop else chs.RK4, block_threads=blk[N]) for N in Ns}
     flops = fput_dp_flops_per_orbit_step if dop else fput_flops_per_orbit_step
     stream = torch.cuda.current_stream()
 
@@ -575,7 +592,8 @@ def run_fput(args):
         os_ = n * args.chunk / (ms / 1e3)
         tf = flops(N, qr[N]) * os_ / 1e12
         per_n[str(N)] = {"orbit_steps_per_s": os_, "kernel_ms": ms, "fp64_tflops": tf,
-                         "frac_of_fp64_peak": tf / fp64_peak_tflops(2070.0), "qr_every": qr[N]}
+                         "frac_of_fp64_peak": tf / fp64_peak_tflops(2070.0), "qr_every": qr[N],
+                         "block_threads": blk[N] or None}
     value = len(runs) * n * args.chunk * args.steps / (total_ms / 1e3)
     print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup,
@@ -1008,6 +1026,9 @@ def main():
     ap.add_argument("--fput-orbits", type=int, default=4096)
     ap.add_argument("--qr-every", default="10", help="QR interval of the FPUT run, or 'auto' (autotuner)")
     ap.add_argument("--fput-batch", action="store_true", help="all chain lengths in one CUDA graph")
+    ap.add_argument("--block", default="0", choices=["0", "32", "64", "128", "auto"],
+                    help="threads per block of the RK4 kernels (grid: integrate kernel; fput: "
+                         "Lyapunov kernel); 0 = library default, auto = autotuner")
     ap.add_argument("--gali-orbits", type=int, default=1000, help="fput_gali: orbits per chain length")
     ap.add_argument("--gali-tau", type=float, default=1000.0, help="fput_gali: integration time")
     ap.add_argument("--gali-tol", type=float, default=1e-8, help="fput_gali: atol = rtol")

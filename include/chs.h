@@ -112,7 +112,9 @@ typedef struct {
     double sali_threshold;   /* label: chaotic when SALI < sali_threshold */
     uint64_t seed;           /* SplitMix64 seed for device-seeded deviation vectors */
     int32_t integrator;      /* CHS_RK4 or CHS_DOP853 */
-    int32_t reserved;        /* ignored */
+    int32_t block_threads;   /* threads per block where a kernel offers the choice: 0 (the
+                                library's default), 32, 64 or 128; results never depend on
+                                it (see chs_integrate_batch, chs_lyapunov_spectrum) */
 } chs_params;
 
 /* Resumable ensemble state: caller-owned device arrays over n_orbits orbits.
@@ -224,7 +226,9 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
  * NONFINITE; dh_max <- max(dh_max, |H - h0|); |H - h0| > dh_limit -> frozen
  * ENERGY_DRIFT; with early_exit, SALI < sali_threshold -> frozen EARLY_CHAOTIC.
  * An orbit with t_end stops after t_end[o] total steps.  Splitting a run into
- * calls with consecutive step0 gives bit-identical results.  Supported: HENON_HEILES, HARMONIC, INVERTED
+ * calls with consecutive step0 gives bit-identical results.  p->block_threads sets the
+ * block size of the RK4 one-orbit-per-thread kernels (both vector precisions;
+ * default 128); the DOP853 and FPUT kernels keep their own.  Supported: HENON_HEILES, HARMONIC, INVERTED
  * (k <= 4), QUARTIC3 (k <= 6) and FPUT (N in {4, 8, 16, 32, 64}, k <= 6, FP64
  * vectors, no LD; the vectors advance through the same Runge-Kutta stages as
  * the chain, with the tridiagonal Hessian of Eq. ham_eqs_FPU). */
@@ -354,7 +358,10 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
  * ic_status may be NULL.  Supported: FPUT with N in {4, 8, 16, 32, 64} (the
  * vectors live in shared memory; RK4 propagates them by its exact one-step
  * propagator, DOP853 column by column with the stages in registers), and
- * HENON_HEILES, HARMONIC, INVERTED.  FP64 throughout. */
+ * HENON_HEILES, HARMONIC, INVERTED.  FP64 throughout.  For FPUT under RK4,
+ * p->block_threads (0, or 32, 64, 128 and at least 2N) sets the block size
+ * (block_threads / 2N orbits per block; default: the smallest allowed); the
+ * results do not depend on it. */
 chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n,
                                  const double* ics, const int32_t* ic_status,
                                  double* lambda_out, int32_t* status_out, void* stream);

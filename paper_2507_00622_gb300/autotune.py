@@ -13,6 +13,13 @@ Tuned parameters:
 - chunk_steps of compacted runs (chs_integrate_compacted): the fastest candidate
   on a sample grid; short chunks drop finished orbits sooner, long chunks launch
   less often.
+- block_threads (threads per block) of the one-orbit-per-thread RK4 integrate
+  kernels and of the RK4 FPUT Lyapunov kernel (orbits per block = threads / 2N):
+  the fastest of 32, 64 and 128 on a sample.  Results do not depend on the block
+  size, so no accuracy guard is needed.  Orbits per thread stay at one: a thread
+  holds its orbit's whole joint state in registers (168 for Henon-Heiles with
+  four vectors and the LD), and the kernels are bound by the FP64 pipe, which a
+  second interleaved orbit per thread could not feed any faster.
 """
 from __future__ import annotations
 
@@ -127,5 +134,85 @@ def tune_compact_chunk(E: float = 0.125, side: int = 256, steps: int = 100_000, 
     choice = min(candidates, key=lambda c: times[c])
     out = {"chunk_steps": int(choice), "seconds": {str(c): times[c] for c in candidates},
            "side": side, "steps": steps}
+    _store(key, out)
+    return out
+
+
+def _best_time(fn, reps: int = 2) -> float:
+    best = None
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    return best
+
+
+def tune_block_integrate(k: int = 4, ld: bool = True, vec_fp32: bool = False, side: int = 512,
+                         steps: int = 200, candidates=(32, 64, 128), refresh: bool = False) -> dict:
+    """Pick block_threads of chs_integrate_batch on a Henon-Heiles grid at E = 1/6
+    (k vectors, LD p = 1/2 when `ld`)."""
+    key = (f"block_integrate|{_gpu()}|k={k}|ld={int(ld)}|fp32={int(vec_fp32)}|side={side}"
+           f"|cand={','.join(map(str, candidates))}")
+    if not refresh:
+        hit = _load().get(key)
+        if hit:
+            return hit
+    E = 1.0 / 6.0
+    S = chs.System(chs.HENON_HEILES, 2)
+    y0, y1, p0, p1 = hh_section_box(E)
+    n = side * side
+    ics = torch.empty((4, n), dtype=torch.float64, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    chs.chs_section_grid_ics(S.h, E, y0, y1, side, p0, p1, side, ics, st)
+    vp = chs.VEC_FP32 if vec_fp32 else chs.VEC_FP64
+    kw = dict(n_dev=k, ld_p=0.5 if ld else 0.0, escape_r2=4.0, vec_precision=vp)
+    ens = chs.DeviceEnsemble.empty(n, 4, k, vec_fp32=vec_fp32)
+    abi = ens.abi(with_ld=ld)
+    chs.chs_ensemble_init(S.h, chs.params(0.01, 1, **kw), abi, ics, st)
+    times = {}
+    step = 0
+    for b in candidates:
+        def run():
+            nonlocal step
+            chs.chs_integrate_batch(S.h, chs.params(0.01, steps, step0=step, block_threads=b, **kw), abi)
+            step += steps
+        run()  # warm-up
+        times[b] = _best_time(run)
+    choice = min(candidates, key=lambda b: times[b])
+    out = {"block_threads": int(choice), "seconds": {str(b): times[b] for b in candidates},
+           "side": side, "steps": steps}
+    _store(key, out)
+    return out
+
+
+def tune_fput_block(N: int, qr_every: int = 10, n_orbits: int = 4096, steps: int = 200,
+                    refresh: bool = False) -> dict:
+    """Pick block_threads of the RK4 FPUT Lyapunov kernel for chains of N sites
+    (every multiple of 2N among 32, 64, 128)."""
+    cands = [b for b in (32, 64, 128) if b >= 2 * N]
+    key = f"block_fput|{_gpu()}|N={N}|qr={qr_every}|n={n_orbits}|cand={','.join(map(str, cands))}"
+    if not refresh:
+        hit = _load().get(key)
+        if hit:
+            return hit
+    S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
+    Q, P = normal_mode_draws(4343 + N, N, n_orbits)
+    ics = torch.empty((2 * N, n_orbits), dtype=torch.float64, device="cuda")
+    chs.chs_fput_mode_ics(S.h, n_orbits, torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(),
+                          torch.full((n_orbits,), 0.1 * N, dtype=torch.float64, device="cuda"), ics)
+    lam = torch.empty((2 * N, n_orbits), dtype=torch.float64, device="cuda")
+    st = torch.empty(n_orbits, dtype=torch.int32, device="cuda")
+    times = {}
+    for b in cands:
+        prm = chs.params(0.05, steps, qr_every=qr_every, sample_every=100, block_threads=b)
+        run = lambda: chs.chs_lyapunov_spectrum(S.h, prm, n_orbits, ics, None, lam, st)  # noqa: E731
+        run()  # warm-up
+        times[b] = _best_time(run)
+    choice = min(cands, key=lambda b: times[b])
+    out = {"block_threads": int(choice), "seconds": {str(b): times[b] for b in cands},
+           "n_orbits": n_orbits, "steps": steps}
     _store(key, out)
     return out

@@ -112,6 +112,8 @@ chs_status check_params(const chs_params* p, const chs::SysPar& sp)
         return fail(CHS_E_INVALID, "integrator must be CHS_RK4 or CHS_DOP853");
     if (p->integrator == CHS_DOP853 && p->vec_precision == CHS_VEC_FP32 && p->n_dev > 0)
         return fail(CHS_E_UNSUPPORTED, "DOP853 runs with FP64 deviation vectors only");
+    if (p->block_threads != 0 && p->block_threads != 32 && p->block_threads != 64 && p->block_threads != 128)
+        return fail(CHS_E_INVALID, "block_threads must be 0, 32, 64 or 128");
     return ok();
 }
 
@@ -143,6 +145,7 @@ chs::StepArgs step_args(const chs_params* p)
     a.dh_limit = p->dh_limit;
     a.early_exit = p->early_exit;
     a.sali_threshold = p->sali_threshold;
+    a.block = p->block_threads;
     return a;
 }
 
@@ -597,6 +600,10 @@ static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const
     if (p->vec_precision != CHS_VEC_FP64) return fail(CHS_E_UNSUPPORTED, "the Lyapunov path is FP64 only");
     if (p->integrator != CHS_RK4 && p->integrator != CHS_DOP853)
         return fail(CHS_E_INVALID, "integrator must be CHS_RK4 or CHS_DOP853");
+    if (p->block_threads != 0 && p->block_threads != 32 && p->block_threads != 64 && p->block_threads != 128)
+        return fail(CHS_E_INVALID, "block_threads must be 0, 32, 64 or 128");
+    if (s->sp.model == CHS_FPUT && p->block_threads != 0 && p->block_threads < 2 * s->sp.n_dof)
+        return fail(CHS_E_INVALID, "FPUT: block_threads must be 0 or at least 2N");
     if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
     if (n > ((int64_t)1 << 31)) return fail(CHS_E_SIZE, "n exceeds 2^31");
     if (n > 0 && (!ics || !lambda_out || !status_out)) return fail(CHS_E_INVALID, "pointers must be non-NULL");

@@ -65,7 +65,19 @@ struct StepArgs {
     double dh_limit;       // 0: off
     int32_t early_exit;    // freeze as EARLY_CHAOTIC once SALI < sali_threshold
     double sali_threshold;
+    int32_t block;         // threads per block requested (0: the kernel's default)
 };
+
+// Threads per block of the one-orbit-per-thread RK4 kernels, and the slot of
+// that size in per-size launch caches.
+inline int small_threads(const StepArgs& a)
+{
+    return a.block > 0 ? a.block : kSmallBlock;
+}
+inline int block_slot(int threads)
+{
+    return threads <= 32 ? 0 : (threads <= 64 ? 1 : 2);
+}
 
 // Launchers (host side, one per kernel family).  Each returns the launch error.
 cudaError_t launch_grid_ics(double E, double y0, double y1, int ny, double py0, double py1, int npy,

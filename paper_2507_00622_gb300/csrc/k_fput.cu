@@ -1,7 +1,7 @@
 // k_fput.cu -- Lyapunov spectrum of the FPUT chain by periodic QR.
 //
-// One orbit per d = 2N threads (several orbits per 128-thread block for
-// N < 64).  Thread l owns state component l and column l of the d x d matrix
+// One orbit per d = 2N threads; a block of T = 32, 64 or 128 threads (at
+// least d) holds T / d orbits.  Thread l owns state component l and column l of the d x d matrix
 // W of deviation vectors, which lives in shared memory (128 KB at N = 64).
 //
 // Propagation of W uses the exact one-step propagator of classic RK4 applied
@@ -30,11 +30,12 @@
 
 namespace chs {
 
-template <int N>
+template <int N, int T>
 struct FputLyapCfg {
     static constexpr int D = 2 * N;
-    static constexpr int G = D >= 128 ? 1 : 128 / D;  // orbits per block
-    static constexpr int THREADS = G * D;
+    static constexpr int THREADS = T;
+    static constexpr int G = T / D;  // orbits per block
+    static_assert(T % D == 0 && T <= 128 && T % 32 == 0, "blocks of whole orbits and whole warps");
     // doubles per orbit: W, band rows, stage state, stage stiffnesses, 2 scratch
     static constexpr int PER = D * D + 18 * N + D + 4 * (N + 1) + 2;
     static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
@@ -154,13 +155,13 @@ __device__ __forceinline__ void apply_phi(double* W, const double* cf, const int
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(FputLyapCfg<N>::THREADS)
+template <int N, int T>
+__global__ void __launch_bounds__(T)
 k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __restrict__ ics,
             const int32_t* __restrict__ ic_status, double* __restrict__ lambda,
             int32_t* __restrict__ status_out)
 {
-    using Cfg = FputLyapCfg<N>;
+    using Cfg = FputLyapCfg<N, T>;
     constexpr int D = Cfg::D, G = Cfg::G, PER = Cfg::PER;
     extern __shared__ double smem[];
     const int g = threadIdx.x / D, l = threadIdx.x % D;
@@ -268,9 +269,9 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
         }
     }
     if (valid) {
-        const double T = (double)a.n_steps * a.dt;
+        const double t_total = (double)a.n_steps * a.dt;
         lambda[(int64_t)l * n + o] =
-            (st == CHS_ORBIT_OK) ? S / T : __longlong_as_double(0x7ff8000000000000LL);
+            (st == CHS_ORBIT_OK) ? S / t_total : __longlong_as_double(0x7ff8000000000000LL);
         if (l == 0) status_out[o] = st;
     }
 }
@@ -280,15 +281,28 @@ bool fput_lyap_supported(int n_dof)
     return n_dof == 4 || n_dof == 8 || n_dof == 16 || n_dof == 32 || n_dof == 64;
 }
 
+// Block sizes offered per chain length: every multiple of 2N among 32, 64, 128.
+template <int N, int T>
+static cudaError_t prepare_nt()
+{
+    if constexpr (T >= 2 * N) {
+        static bool done[kCacheDevices] = {};  // per device; set before any stream capture
+        const int dev = cache_device();
+        if (done[dev]) return cudaSuccess;
+        cudaError_t err = cudaFuncSetAttribute(k_fput_lyap<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)FputLyapCfg<N, T>::SMEM);
+        if (err == cudaSuccess) done[dev] = true;
+        return err;
+    }
+    return cudaSuccess;
+}
+
 template <int N>
 static cudaError_t prepare_n()
 {
-    static bool done[kCacheDevices] = {};  // per device; set before any stream capture
-    const int dev = cache_device();
-    if (done[dev]) return cudaSuccess;
-    cudaError_t err = cudaFuncSetAttribute(k_fput_lyap<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)FputLyapCfg<N>::SMEM);
-    if (err == cudaSuccess) done[dev] = true;
+    cudaError_t err = prepare_nt<N, 32>();
+    if (err == cudaSuccess) err = prepare_nt<N, 64>();
+    if (err == cudaSuccess) err = prepare_nt<N, 128>();
     return err;
 }
 
@@ -304,17 +318,34 @@ cudaError_t prepare_fput_lyap(int n_dof)
     return cudaErrorInvalidValue;
 }
 
+template <int N, int T>
+static cudaError_t fput_lyap_nt(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
+                                const int32_t* ic_status, double* lambda, int32_t* status, cudaStream_t st)
+{
+    if constexpr (T >= 2 * N) {
+        using Cfg = FputLyapCfg<N, T>;
+        cudaError_t err = prepare_nt<N, T>();
+        if (err != cudaSuccess) return err;
+        k_fput_lyap<N, T><<<blocks_for(n, Cfg::G), T, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status, lambda, status);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Default block: one warp of orbits for N <= 16, one orbit above (the smallest
+// block; many small blocks spread an ensemble over every SM).  The autotuner
+// (autotune.tune_fput_block) measures every size per N.
 template <int N>
 static cudaError_t fput_lyap_n(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
                                const int32_t* ic_status, double* lambda, int32_t* status,
                                cudaStream_t st)
 {
-    using Cfg = FputLyapCfg<N>;
-    cudaError_t err = prepare_n<N>();
-    if (err != cudaSuccess) return err;
-    k_fput_lyap<N><<<blocks_for(n, Cfg::G), Cfg::THREADS, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status,
-                                                                          lambda, status);
-    return cudaGetLastError();
+    switch (a.block > 0 ? a.block : (2 * N > 32 ? 2 * N : 32)) {
+    case 32: return fput_lyap_nt<N, 32>(sp, a, n, ics, ic_status, lambda, status, st);
+    case 64: return fput_lyap_nt<N, 64>(sp, a, n, ics, ic_status, lambda, status, st);
+    case 128: return fput_lyap_nt<N, 128>(sp, a, n, ics, ic_status, lambda, status, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fput_lyap(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,

@@ -444,16 +444,18 @@ template <class Sys, int K, bool LD>
 static void integ_one(const unsigned g, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
                       const OrbitList* ol, cudaStream_t st)
 {
+    const int tb = small_threads(a);
     if (ol && ol->queue) {
-        static unsigned pgs[kCacheDevices] = {};  // blocks of the persistent grid, per device
-        unsigned& pg = pgs[cache_device()];
-        if (!pg && persistent_blocks(k_integrate_f32<Sys, K, LD, kModeQueue>, kSmallBlock, 0, &pg) != cudaSuccess)
+        // blocks of the persistent grid, per device and block size
+        static unsigned pgs[kCacheDevices][3] = {};
+        unsigned& pg = pgs[cache_device()][block_slot(tb)];
+        if (!pg && persistent_blocks(k_integrate_f32<Sys, K, LD, kModeQueue>, tb, 0, &pg) != cudaSuccess)
             pg = 0;
-        k_integrate_f32<Sys, K, LD, kModeQueue><<<pg ? pg : g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+        k_integrate_f32<Sys, K, LD, kModeQueue><<<pg ? pg : g, tb, 0, st>>>(a, sp, e, *ol);
     } else if (ol) {
-        k_integrate_f32<Sys, K, LD, kModeList><<<g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+        k_integrate_f32<Sys, K, LD, kModeList><<<g, tb, 0, st>>>(a, sp, e, *ol);
     } else {
-        k_integrate_f32<Sys, K, LD, kModeAll><<<g, kSmallBlock, 0, st>>>(a, sp, e, OrbitList{});
+        k_integrate_f32<Sys, K, LD, kModeAll><<<g, tb, 0, st>>>(a, sp, e, OrbitList{});
     }
 }
 
@@ -461,7 +463,7 @@ template <class Sys, bool LD>
 static cudaError_t integ_sys(int k, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
                              const OrbitList* ol, cudaStream_t st)
 {
-    const unsigned g = blocks_for(e.n, kSmallBlock);
+    const unsigned g = blocks_for(e.n, small_threads(a));
     switch (k) {
     case 1: integ_one<Sys, 1, LD>(g, a, sp, e, ol, st); break;
     case 2: integ_one<Sys, 2, LD>(g, a, sp, e, ol, st); break;

@@ -620,16 +620,18 @@ template <class Sys, int K, bool LD>
 static void integ_one(const unsigned g, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
                       const OrbitList* ol, cudaStream_t st)
 {
+    const int tb = small_threads(a);
     if (ol && ol->queue) {
-        static unsigned pgs[kCacheDevices] = {};  // blocks of the persistent grid, per device
-        unsigned& pg = pgs[cache_device()];
-        if (!pg && persistent_blocks(k_integrate<Sys, K, LD, kModeQueue>, kSmallBlock, 0, &pg) != cudaSuccess)
+        // blocks of the persistent grid, per device and block size
+        static unsigned pgs[kCacheDevices][3] = {};
+        unsigned& pg = pgs[cache_device()][block_slot(tb)];
+        if (!pg && persistent_blocks(k_integrate<Sys, K, LD, kModeQueue>, tb, 0, &pg) != cudaSuccess)
             pg = 0;
-        k_integrate<Sys, K, LD, kModeQueue><<<pg ? pg : g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+        k_integrate<Sys, K, LD, kModeQueue><<<pg ? pg : g, tb, 0, st>>>(a, sp, e, *ol);
     } else if (ol) {
-        k_integrate<Sys, K, LD, kModeList><<<g, kSmallBlock, 0, st>>>(a, sp, e, *ol);
+        k_integrate<Sys, K, LD, kModeList><<<g, tb, 0, st>>>(a, sp, e, *ol);
     } else {
-        k_integrate<Sys, K, LD, kModeAll><<<g, kSmallBlock, 0, st>>>(a, sp, e, OrbitList{});
+        k_integrate<Sys, K, LD, kModeAll><<<g, tb, 0, st>>>(a, sp, e, OrbitList{});
     }
 }
 
@@ -637,7 +639,7 @@ template <class Sys, bool LD>
 static cudaError_t integ_k(int k, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
                            const OrbitList* ol, cudaStream_t st)
 {
-    const unsigned g = blocks_for(e.n, kSmallBlock);
+    const unsigned g = blocks_for(e.n, small_threads(a));
     switch (k) {
     case 0: integ_one<Sys, 0, LD>(g, a, sp, e, ol, st); break;
     case 1: integ_one<Sys, 1, LD>(g, a, sp, e, ol, st); break;

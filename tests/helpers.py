@@ -58,7 +58,8 @@ def oracle_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm
 def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=True,
             sample_every=100, escape_r2=0.0, dh_limit=0.0, seed=1, w_in=None,
             sali_threshold=1e-8, chunks=None, grid=None, vec_fp32=False, sys_params=(),
-            early_exit=False, t_end=None, compact_chunk=None, integrator=0, persistent=False):
+            early_exit=False, t_end=None, compact_chunk=None, integrator=0, persistent=False,
+            block_threads=0):
     import torch
 
     from paper_2507_00622_gb300 import chs
@@ -69,7 +70,7 @@ def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=Tr
     vp = chs.VEC_FP32 if vec_fp32 else chs.VEC_FP64
     kw = dict(n_dev=k, ld_p=ld_p, renorm=renorm, sample_every=sample_every, escape_r2=escape_r2,
               dh_limit=dh_limit, sali_threshold=sali_threshold, seed=seed, vec_precision=vp,
-              early_exit=early_exit, integrator=integrator)
+              early_exit=early_exit, integrator=integrator, block_threads=block_threads)
     ics_t = torch.from_numpy(np.ascontiguousarray(ics)).cuda()
     st_t = None if ic_status is None else torch.from_numpy(
         np.ascontiguousarray(ic_status, dtype=np.int32)).cuda()
