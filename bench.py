@@ -949,8 +949,10 @@ def run_saturation(args):
     """GPU saturation curve of the paper's Henon-Heiles experiment (Sec. Examples:
     time per initial condition against the number of initial conditions, SALI
     with 2 deviation vectors): section grids at E = 1/8 of 2^10 ... 2^20 cells,
-    --chunk steps of the chosen integrator (h = 0.01; DOP853 at the same step)
-    plus SALI, timed with CUDA events; one JSON line with the curve."""
+    --chunk steps of the chosen integrator (h = 0.01; DOP853 at the same step),
+    or with --sat-tol > 0 adaptive DOP 8(5) at atol = rtol = --sat-tol over the
+    same time span (--chunk x 0.01), plus SALI, timed with CUDA events; one JSON
+    line with the curve."""
     import torch
 
     from paper_2507_00622_gb300 import build as cuda_build
@@ -963,8 +965,11 @@ def run_saturation(args):
     E = 1.0 / 8.0
     y0, y1, p0, p1 = hh_section_box(E)
     S = chs.System(chs.HENON_HEILES, 2)
-    integ = chs.DOP853 if args.integrator == "dop853" else chs.RK4
-    kw = dict(n_dev=2, ld_p=0.5, escape_r2=4.0, sample_every=100, integrator=integ)
+    adaptive = args.sat_tol > 0.0
+    integ = chs.DOP853 if (args.integrator == "dop853" or adaptive) else chs.RK4
+    # health checks (and so max |H - H0|) every 100 fixed steps, every 10 accepted adaptive ones
+    kw = dict(n_dev=2, ld_p=0.5, escape_r2=4.0, sample_every=10 if adaptive else 100, integrator=integ)
+    t_span = args.chunk * 0.01
     stream = torch.cuda.current_stream()
     curve = []
     for e in range(10, 21, 2):
@@ -976,12 +981,21 @@ def run_saturation(args):
         ens = chs.DeviceEnsemble.empty(n, 4, 2)
         abi = ens.abi()
         sali = torch.empty(n, dtype=torch.float64, device="cuda")
+        tt = torch.zeros(n, dtype=torch.float64, device="cuda")
+        hh = torch.zeros(n, dtype=torch.float64, device="cuda")
         times = []
         for rep in range(1 + max(1, args.steps)):
             chs.chs_ensemble_init(S.h, chs.params(0.01, 1, **kw), abi, ics, st)
+            tt.zero_()
+            hh.fill_(0.01)
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            chs.chs_integrate_batch(S.h, chs.params(0.01, args.chunk, **kw), abi, stream)
+            if adaptive:
+                chs.chs_integrate_adaptive(S.h, chs.params(0.01, 10**9, **kw),
+                                           chs.Adaptive(t_span, args.sat_tol, args.sat_tol, 0.0), abi, tt, hh,
+                                           stream=stream)
+            else:
+                chs.chs_integrate_batch(S.h, chs.params(0.01, args.chunk, **kw), abi, stream)
             chs.chs_indicators(S.h, chs.params(0.01, 0, **kw), abi, sali=sali, stream=stream)
             ev1.record(stream)
             torch.cuda.synchronize()
@@ -989,10 +1003,15 @@ def run_saturation(args):
                 times.append(ev0.elapsed_time(ev1))
         ms = float(np.median(times))
         valid = int((st == 0).sum())
+        steps_done = int(ens.n_exec.sum())
         curve.append({"n_ics": n, "valid": valid, "ms": ms, "us_per_ic": 1e3 * ms / valid,
-                      "orbit_steps_per_s": valid * args.chunk / (ms / 1e3)})
+                      "orbit_steps_per_s": steps_done / (ms / 1e3),
+                      "steps_per_ic": steps_done / valid, "max_dH": float(ens.dh_max[st == 0].max())})
     print(json.dumps({"workload": "henon_heiles_E1/8_saturation_sali_k2_ld",
-                      "integrator": args.integrator, "steps": args.chunk, "dt": 0.01, "curve": curve}))
+                      "integrator": ("DOP 8(5) adaptive, atol = rtol = %g" % args.sat_tol) if adaptive
+                                    else args.integrator,
+                      "t_span": t_span, "steps": None if adaptive else args.chunk, "dt": 0.01,
+                      "curve": curve}))
     return 0
 
 
@@ -1029,6 +1048,8 @@ def main():
     ap.add_argument("--block", default="0", choices=["0", "32", "64", "128", "auto"],
                     help="threads per block of the RK4 kernels (grid: integrate kernel; fput: "
                          "Lyapunov kernel); 0 = library default, auto = autotuner")
+    ap.add_argument("--sat-tol", type=float, default=0.0,
+                    help="saturation: adaptive DOP 8(5) at this atol = rtol (0: fixed steps)")
     ap.add_argument("--gali-orbits", type=int, default=1000, help="fput_gali: orbits per chain length")
     ap.add_argument("--gali-tau", type=float, default=1000.0, help="fput_gali: integration time")
     ap.add_argument("--gali-tol", type=float, default=1e-8, help="fput_gali: atol = rtol")
