@@ -26,6 +26,10 @@ struct AdaptPtrs {
 cudaError_t launch_integrate_dp(const SysPar& sp, int k, bool ld, const StepArgs& a,
                                 const EnsPtrs& e, const OrbitList* ol, cudaStream_t st);
 
+// The quartic oscillator's part of launch_integrate_dp (k_dop853_q3.cu).
+cudaError_t launch_integrate_dp_q3(int k, bool ld, const StepArgs& a, const SysPar& sp, const EnsPtrs& e,
+                                   const OrbitList* ol, cudaStream_t st);
+
 // Adaptive DOP 8(5) (the chs_integrate_adaptive contract).
 cudaError_t launch_integrate_adaptive(const SysPar& sp, int k, bool ld, const StepArgs& a,
                                       const AdaptArgs& ad, const EnsPtrs& e, const AdaptPtrs& ap,

@@ -8,6 +8,8 @@
 // FP64 pipe (GB300: 2 DFMA/clk/SM), not by HBM.
 #include <math.h>
 
+#include <type_traits>
+
 #include "rk4_common.cuh"
 
 namespace chs {
@@ -205,10 +207,20 @@ __device__ __forceinline__ void rk4_step_phi(double* x, double (*w)[2 * Sys::N],
                                              const double h, const int ld_sqrt, const double ld_p,
                                              const SysPar& sp)
 {
-    double H[4][Sys::NH];
-    rk4_state_capture<Sys, LD>(x, L, h, ld_sqrt, ld_p, sp, H);
     PhiBlocks<Sys::N, double> P;
-    phi_build<Sys::N, Sys::NH, double>(H, h, P);
+    if constexpr (std::is_same<Sys, SysHenonHeiles>::value) {
+        // the propagator from the stage positions (phi_build_hh)
+        double q[4][2];
+        rk4_stages<Sys, LD, false>(x, L, h, ld_sqrt, ld_p, sp, [&](int s, const double* xs, const double*) {
+            q[s][0] = xs[0];
+            q[s][1] = xs[1];
+        });
+        phi_build_hh(q, h, P);
+    } else {
+        double H[4][Sys::NH];
+        rk4_state_capture<Sys, LD>(x, L, h, ld_sqrt, ld_p, sp, H);
+        phi_build<Sys::N, Sys::NH, double>(H, h, P);
+    }
 #pragma unroll
     for (int j = 0; j < K; ++j) phi_apply<Sys::N, double>(P, w[j]);
 }

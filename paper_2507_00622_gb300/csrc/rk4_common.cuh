@@ -187,6 +187,52 @@ __device__ __forceinline__ void phi_build(const T (*Hs)[NH], const double h, Phi
     }
 }
 
+// Henon-Heiles: Hess V = I + 2 M(q) with M(q) = [[q2, q1], [q1, -q2]] (from
+// Eq. ham_eqs_HH), M linear in q, and M(a) M(b) = [[p, r], [-r, p]] with
+// p = a1 b1 + a2 b2, r = a2 b1 - a1 b2.  The blocks of Phi from the four stage
+// positions q_s, with c1 = h/6, c2 = h^2/6, c3 = h^3/12, c4 = h^4/24:
+//   A = (1 - 3 c2 + c4) I + 2 M(c4 (q1 + q3) - c2 (q1 + q2 + q3)) + 4 c4 M(q3) M(q1)
+//   B = (h - 2 c3) I - 2 c3 M(q2 + q3)
+//   C = (2 c3 - 6 c1) I + 2 M(c3 (q1 + q2 + q3 + q4) - c1 (q1 + 2 q2 + 2 q3 + q4))
+//       + 4 c3 (M(q3) M(q1) + M(q4) M(q2))
+//   D = (1 - 3 c2 + c4) I + 2 M(c4 (q2 + q4) - c2 (q2 + q3 + q4)) + 4 c4 M(q4) M(q2)
+// (the general blocks above with H_s = I + 2 M(q_s)); no Hessian is formed.
+__device__ __forceinline__ void phi_build_hh(const double (*q)[2], const double h, PhiBlocks<2, double>& P)
+{
+    const double c1 = h / 6.0, c2 = h * h / 6.0, c3 = h * h * h / 12.0, c4 = h * h * h * h / 24.0;
+    const double aAD = 1.0 - 3.0 * c2 + c4, aB = h - 2.0 * c3, aC = 2.0 * c3 - 6.0 * c1;
+    double mA[2], mB[2], mC[2], mD[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double s13 = q[0][i] + q[2][i], s24 = q[1][i] + q[3][i], s23 = q[1][i] + q[2][i];
+        const double s123 = s13 + q[1][i], s234 = s24 + q[2][i], sall = s13 + s24;
+        mA[i] = fma(2.0 * c4, s13, -2.0 * c2 * s123);
+        mB[i] = -2.0 * c3 * s23;
+        mC[i] = fma(2.0 * c3, sall, -2.0 * c1 * (sall + s23));
+        mD[i] = fma(2.0 * c4, s24, -2.0 * c2 * s234);
+    }
+    const double p31 = fma(q[2][0], q[0][0], q[2][1] * q[0][1]), r31 = fma(q[2][1], q[0][0], -q[2][0] * q[0][1]);
+    const double p42 = fma(q[3][0], q[1][0], q[3][1] * q[1][1]), r42 = fma(q[3][1], q[1][0], -q[3][0] * q[1][1]);
+    const double k4 = 4.0 * c4, k3 = 4.0 * c3;
+    P.A[0][0] = fma(k4, p31, aAD + mA[1]);
+    P.A[1][1] = fma(k4, p31, aAD - mA[1]);
+    P.A[0][1] = fma(k4, r31, mA[0]);
+    P.A[1][0] = fma(-k4, r31, mA[0]);
+    P.B[0][0] = aB + mB[1];
+    P.B[1][1] = aB - mB[1];
+    P.B[0][1] = mB[0];
+    P.B[1][0] = mB[0];
+    const double pc = p31 + p42, rc = r31 + r42;
+    P.C[0][0] = fma(k3, pc, aC + mC[1]);
+    P.C[1][1] = fma(k3, pc, aC - mC[1]);
+    P.C[0][1] = fma(k3, rc, mC[0]);
+    P.C[1][0] = fma(-k3, rc, mC[0]);
+    P.D[0][0] = fma(k4, p42, aAD + mD[1]);
+    P.D[1][1] = fma(k4, p42, aAD - mD[1]);
+    P.D[0][1] = fma(k4, r42, mD[0]);
+    P.D[1][0] = fma(-k4, r42, mD[0]);
+}
+
 // w <- Phi w for one vector w = (u, v).
 template <int N, typename T>
 __device__ __forceinline__ void phi_apply(const PhiBlocks<N, T>& P, T* w)
