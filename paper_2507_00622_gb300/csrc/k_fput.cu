@@ -23,7 +23,13 @@
 // QR: modified Gram-Schmidt in the "dot products first" order: for column j
 // every column l >= j forms r_l = w_j . w_l (r_j = |w_j|^2), then each l > j
 // subtracts (r_l / r_j) w_j; the columns are scaled to unit length at the end
-// and S_j += ln |w_j| (so R_jj > 0).
+// and S_j += ln |w_j| (so R_jj > 0).  Thread l works column l, except at
+// d = 128, where the orbit's Q = 4 warps split the rows instead: warp w takes
+// rows 32w..32w+31 of the columns lane + 32m (m < Q), and the Q partial dot
+// products of a column are summed in a fixed order from shared memory.  Every
+// warp then works while any column is left (with columns per thread, the warp
+// holding the last columns would do all d iterations alone while the others
+// wait at the barriers).
 #include <math.h>
 
 #include "chs_internal.cuh"
@@ -36,8 +42,14 @@ struct FputLyapCfg {
     static constexpr int THREADS = T;
     static constexpr int G = T / D;  // orbits per block
     static_assert(T % D == 0 && T <= 128 && T % 32 == 0, "blocks of whole orbits and whole warps");
-    // doubles per orbit: W, band rows, stage state, stage stiffnesses, 2 scratch
-    static constexpr int PER = D * D + 18 * N + D + 4 * (N + 1) + 2;
+    // row blocks of the split QR: the orbit's 4 warps at N = 64, where shared
+    // memory holds one orbit per SM and the QR's critical path is the kernel's
+    // (measured: 1213 -> 1012 ms per 200 steps at QR every 10).  At N = 32 six
+    // orbits share an SM and hide the imbalance; the split measured 4 % slower.
+    static constexpr int Q = D >= 128 ? D / 32 : 1;
+    // doubles per orbit: W, band rows, stage state, stage stiffnesses, 2 scratch,
+    // the QR's double-buffered partial dot products [2][Q][D] and exponent sums [D]
+    static constexpr int PER = D * D + 18 * N + D + 4 * (N + 1) + 2 + (Q > 1 ? 2 * Q * D + D : 0);
     static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
 };
 
@@ -155,6 +167,63 @@ __device__ __forceinline__ void apply_phi(double* W, const double* cf, const int
     }
 }
 
+// The split modified Gram-Schmidt for d = 128 (see the file comment): t is
+// the thread's index in its orbit, P the [2][Q][d] partial sums, Sv[c] the
+// exponent sum of column c.  Every thread of the block calls it.
+template <int N>
+__device__ __forceinline__ void qr_split(double* W, double* P, double* Sv, const int t)
+{
+    constexpr int D = 2 * N, Q = D / 32;
+    const int w = t / 32, lane = t % 32;
+    const int r0 = 32 * w;
+    double inv[Q];
+#pragma unroll
+    for (int m = 0; m < Q; ++m) inv[m] = 1.0;
+    for (int j = 0; j < D; ++j) {
+        __syncwarp();  // rows of column j in this warp's block are final
+        double* Pb = P + (j & 1) * Q * D;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const int c = lane + 32 * m;
+            if (c >= j) {
+                double a0 = 0.0, a1 = 0.0;
+#pragma unroll 4
+                for (int i = 0; i < 32; i += 2) {
+                    a0 = fma(W[(r0 + i) * D + j], W[(r0 + i) * D + c], a0);
+                    a1 = fma(W[(r0 + i + 1) * D + j], W[(r0 + i + 1) * D + c], a1);
+                }
+                Pb[w * D + c] = a0 + a1;
+            }
+        }
+        __syncthreads();
+        double nj = Pb[j];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) nj += Pb[q * D + j];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const int c = lane + 32 * m;
+            if (c > j) {
+                double r = Pb[c];
+#pragma unroll
+                for (int q = 1; q < Q; ++q) r += Pb[q * D + c];
+                const double cfac = -r / nj;
+#pragma unroll 4
+                for (int i = 0; i < 32; ++i) W[(r0 + i) * D + c] = fma(cfac, W[(r0 + i) * D + j], W[(r0 + i) * D + c]);
+            } else if (c == j) {
+                inv[m] = rsqrt(nj);
+                if (w == 0) Sv[j] += 0.5 * log(nj);
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+        const int c = lane + 32 * m;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) W[(r0 + i) * D + c] *= inv[m];
+    }
+}
+
 template <int N, int T>
 __global__ void __launch_bounds__(T)
 k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __restrict__ ics,
@@ -172,6 +241,8 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
     double* xs = cf + 18 * N;
     double* cs = xs + D;
     double* red = cs + 4 * (N + 1);
+    double* qp = red + 2;            // split QR: partial sums [2][Q][D] (d = 128)
+    double* Sv = qp + 2 * Cfg::Q * D;  // split QR: exponent sums [D]
 
     const FputCoef fc = {sp.kk, 2.0 * sp.alpha, 3.0 * sp.beta, sp.alpha, sp.beta};
     int32_t st = valid ? (ic_status ? ic_status[o] : CHS_ORBIT_OK) : CHS_ORBIT_FORBIDDEN;
@@ -194,6 +265,7 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
     for (int i = 0; i < D; ++i) W[i * D + l] = (i == l) ? 1.0 : 0.0;
     xs[l] = xi;
     double S = 0.0;
+    if constexpr (Cfg::Q > 1) Sv[l] = 0.0;
     __syncthreads();
 
     const double h = a.dt;
@@ -233,35 +305,40 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
         if (--until_qr == 0 || s == a.n_steps) {
             until_qr = a.qr_every;
             __syncthreads();
-            double inv = 1.0;
-            for (int j = 0; j < D; ++j) {
-                double r = 0.0;
-                if (l >= j) {
-                    double r0 = 0.0, r1 = 0.0;
+            if constexpr (Cfg::Q > 1) {
+                qr_split<N>(W, qp, Sv, l);
+            } else {
+                double inv = 1.0;
+                for (int j = 0; j < D; ++j) {
+                    double r = 0.0;
+                    if (l >= j) {
+                        double r0 = 0.0, r1 = 0.0;
 #pragma unroll 4
-                    for (int i = 0; i < D; i += 2) {
-                        r0 = fma(W[i * D + j], W[i * D + l], r0);
-                        r1 = fma(W[(i + 1) * D + j], W[(i + 1) * D + l], r1);
+                        for (int i = 0; i < D; i += 2) {
+                            r0 = fma(W[i * D + j], W[i * D + l], r0);
+                            r1 = fma(W[(i + 1) * D + j], W[(i + 1) * D + l], r1);
+                        }
+                        r = r0 + r1;
                     }
-                    r = r0 + r1;
-                }
-                if (l == j) red[0] = r;
-                __syncthreads();
-                const double nj = red[0];
-                if (l > j) {
-                    const double cfac = -r / nj;
+                    if (l == j) red[0] = r;
+                    __syncthreads();
+                    const double nj = red[0];
+                    if (l > j) {
+                        const double cfac = -r / nj;
 #pragma unroll 4
-                    for (int i = 0; i < D; ++i) W[i * D + l] = fma(cfac, W[i * D + j], W[i * D + l]);
-                } else if (l == j) {
-                    S += 0.5 * log(nj);
-                    inv = rsqrt(nj);
+                        for (int i = 0; i < D; ++i) W[i * D + l] = fma(cfac, W[i * D + j], W[i * D + l]);
+                    } else if (l == j) {
+                        S += 0.5 * log(nj);
+                        inv = rsqrt(nj);
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
+#pragma unroll 4
+                for (int i = 0; i < D; ++i) W[i * D + l] *= inv;
             }
-#pragma unroll 4
-            for (int i = 0; i < D; ++i) W[i * D + l] *= inv;
         }
         __syncthreads();
+        if constexpr (Cfg::Q > 1) S = Sv[l];
         if (--until == 0) {
             until = a.sample_every;
             if (orbit_any(!(isfinite(xi) && isfinite(S))) && st == CHS_ORBIT_OK)
