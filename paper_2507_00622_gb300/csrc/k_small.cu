@@ -200,8 +200,9 @@ __device__ __forceinline__ void rk4_step_direct(double* x, VT (*w)[2 * Sys::N], 
 
 // The same RK4 step with the vectors advanced by the exact one-step propagator
 // Phi of RK4 on the variational equations (rk4_common.cuh); identical to the
-// direct form in exact arithmetic and cheaper for k >= 3 vectors (Phi is built
-// once per step and applied to each vector).
+// direct form in exact arithmetic and cheaper for k >= 3 vectors, and for
+// k = 2 with Henon-Heiles (Phi is built once per step and applied to each
+// vector).
 template <class Sys, int K, bool LD>
 __device__ __forceinline__ void rk4_step_phi(double* x, double (*w)[2 * Sys::N], double& L,
                                              const double h, const int ld_sqrt, const double ld_p,
@@ -230,7 +231,10 @@ __device__ __forceinline__ void rk4_step(double* x, double (*w)[2 * Sys::N], dou
                                          const double h, const int ld_sqrt, const double ld_p,
                                          const SysPar& sp)
 {
-    if constexpr (K >= 3)
+    // Henon-Heiles builds Phi from the stage positions (phi_build_hh), cheap
+    // enough to pay off from two vectors on
+    constexpr bool phi = K >= 3 || (K == 2 && std::is_same<Sys, SysHenonHeiles>::value);
+    if constexpr (phi)
         rk4_step_phi<Sys, K, LD>(x, w, L, h, ld_sqrt, ld_p, sp);
     else
         rk4_step_direct<Sys, K, LD, double>(x, w, L, h, ld_sqrt, ld_p, sp);
