@@ -27,7 +27,7 @@ struct Cfg {
     static constexpr int XB = kMaxDev * WS;            // [2][D]
     static constexpr int CS = XB + 2 * D;              // [S][N + 1]
     static constexpr int RED = CS + Tab::S * (N + 1);  // [4] warp partials
-    static constexpr int CTL = RED + 4;                // [0] step of phase 2
+    static constexpr int CTL = RED + 4;                // [0] step of phase 2, [1] error, [2] err^(-1/8)
     static constexpr int PER = CTL + 4;
     static_assert(THREADS % 32 == 0 && THREADS <= 128, "whole warps, N <= 64");
 };

@@ -79,17 +79,23 @@ k_fput_ens_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const in
         const double q5 = e5 / sc, q3 = e3 / sc;
         const double E5 = fe::orbit_sum<D>(q5 * q5, red, l);
         const double E3 = fe::orbit_sum<D>(q3 * q3, red, l);
-        const double err =
-            (E5 == 0.0 && E3 == 0.0) ? 0.0 : fabs(hh) * E5 / sqrt((double)D * (E5 + 0.01 * E3));
+        // the orbit's first thread forms the error and err^(-1/8) (three square
+        // roots and a division) for all of its threads, which read them back
+        // after the barrier: the other warps of a long chain skip that work
+        if (l == 0) {
+            const double err =
+                (E5 == 0.0 && E3 == 0.0) ? 0.0 : fabs(hh) * E5 / sqrt((double)D * (E5 + 0.01 * E3));
+            slab[C::CTL] = (active && err < 1.0) ? hh : 0.0;
+            slab[C::CTL + 1] = err;
+            slab[C::CTL + 2] = (active && err > 0.0) ? 1.0 / sqrt(sqrt(sqrt(err))) : 0.0;
+        }
+        __syncthreads();  // stage stiffnesses, phase-2 steps and the error in place
+        const double err = slab[C::CTL + 1], r8 = slab[C::CTL + 2];
         const bool accept = active && err < 1.0;
-        if (l == 0) slab[C::CTL] = accept ? hh : 0.0;
-        __syncthreads();  // stage stiffnesses and phase-2 steps in place
         fs::columns<N, Tab, G, PER, WS, C::CS, true>(smem, K, [](int, const double* sl) { return sl[C::CTL]; },
                                                a.renorm);
         __syncthreads();  // columns complete; stage buffers free
         if (active) {
-            // err^(-1/8) as three square roots and a division
-            const double r8 = (err > 0.0) ? 1.0 / sqrt(sqrt(sqrt(err))) : 0.0;
             if (accept) {
                 double fac = (err == 0.0) ? 10.0 : fmin(10.0, 0.9 * r8);
                 if (rejected) fac = fmin(fac, 1.0);
