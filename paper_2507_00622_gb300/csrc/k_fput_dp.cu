@@ -17,10 +17,11 @@
 // kernel ("dot products first"); S_j += ln R_jj, lambda_j = S_j / T.
 //
 // Adaptive runs give every orbit its own time and step size.  The error norm
-// of a trial is a sum over the orbit's 2N components, formed by every thread of
-// the orbit from a shared array in the same order; the columns of W advance
-// only for accepted trials.  A block loops until all of its orbits are done.
-#include "fput_stages.cuh"
+// of a trial is a sum over the orbit's 2N components (an xor butterfly, the
+// same in every thread), from which the orbit's first thread forms the error
+// and the step factor for all of its threads; the columns of W advance only
+// for accepted trials.  A block loops until all of its orbits are done.
+#include "fput_ens.cuh"
 
 namespace chs {
 namespace {
@@ -33,7 +34,7 @@ struct FputDpCfg {
     static constexpr int WS = D + 1;                   // padded column stride
     // doubles per orbit: W, two stage-state buffers, 12 stage stiffness rows,
     // two error-sum rows, control words
-    static constexpr int PER = D * WS + 2 * D + 12 * (N + 1) + 2 * D + 4;
+    static constexpr int PER = D * WS + 2 * D + 12 * (N + 1) + 2 * D + 6;
     static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
     static_assert(THREADS % 32 == 0 && THREADS <= 128, "whole warps, N <= 64");
 };
@@ -46,7 +47,8 @@ struct FputDpSlab {
     static constexpr int XB = Cfg::D * Cfg::WS;     // [2][D]
     static constexpr int CS = XB + 2 * Cfg::D;      // [12][N + 1]
     static constexpr int ER = CS + 12 * (N + 1);    // [2][D] error sums
-    static constexpr int CTL = ER + 2 * Cfg::D;     // [0] red, [1] any, [2] step of phase 2, [3] advance
+    static constexpr int CTL = ER + 2 * Cfg::D;     // [0] red, [1] any, [2] step of phase 2, [3] advance,
+                                                    // [4] error, [5] err^(-1/8)
 };
 
 // Modified Gram-Schmidt of the orbit's W (thread l owns column l), when `mine`
@@ -226,22 +228,22 @@ k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const i
         // every thread of the orbit
         const double sc = ad.atol + ad.rtol * fmax(fabs(xi), fabs(xn));
         const double q5 = e5 / sc, q3 = e3 / sc;
-        er[l] = q5 * q5;
-        er[D + l] = q3 * q3;
-        __syncthreads();
-        double E5 = 0.0, E3 = 0.0;
-        for (int i = 0; i < D; ++i) {
-            E5 += er[i];
-            E3 += er[D + i];
+        const double E5 = fe::orbit_sum<D>(q5 * q5, er, l);
+        const double E3 = fe::orbit_sum<D>(q3 * q3, er, l);
+        if (l == 0) {
+            const double err =
+                (E5 == 0.0 && E3 == 0.0) ? 0.0 : fabs(hh) * E5 / sqrt((double)D * (E5 + 0.01 * E3));
+            ctl[2] = (active && err < 1.0) ? hh : 0.0;
+            ctl[4] = err;
+            // err^(-1/8) as three square roots and a division
+            ctl[5] = (active && err > 0.0) ? 1.0 / sqrt(sqrt(sqrt(err))) : 0.0;
         }
-        const double err = (E5 == 0.0 && E3 == 0.0) ? 0.0 : fabs(hh) * E5 / sqrt((double)D * (E5 + 0.01 * E3));
+        __syncthreads();  // stage stiffnesses, phase-2 steps and the error are in place
+        const double err = ctl[4], r8 = ctl[5];
         const bool accept = active && err < 1.0;
-        if (l == 0) ctl[2] = accept ? hh : 0.0;
-        __syncthreads();  // stage stiffnesses and phase-2 steps are in place
 
         fs::columns<N, fs::TabDop853, G, PER, WS, Sl::CS, true>(smem, D, [&](int, const double* sl) { return sl[Sl::CTL + 2]; });
         if (active) {
-            const double r8 = (err > 0.0) ? 1.0 / sqrt(sqrt(sqrt(err))) : 0.0;
             if (accept) {
                 double fac = (err == 0.0) ? 10.0 : fmin(10.0, 0.9 * r8);
                 if (rejected) fac = fmin(fac, 1.0);
