@@ -34,7 +34,7 @@ struct FputDpCfg {
     static constexpr int WS = D + 1;                   // padded column stride
     // doubles per orbit: W, two stage-state buffers, 12 stage stiffness rows,
     // two error-sum rows, control words
-    static constexpr int PER = D * WS + 2 * D + 12 * (N + 1) + 2 * D + 6;
+    static constexpr int PER = D * WS + 2 * D + 12 * (N + 1) + 2 * D + 6 + (D == 128 ? 8 * D : 0);
     static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
     static_assert(THREADS % 32 == 0 && THREADS <= 128, "whole warps, N <= 64");
 };
@@ -49,16 +49,92 @@ struct FputDpSlab {
     static constexpr int ER = CS + 12 * (N + 1);    // [2][D] error sums
     static constexpr int CTL = ER + 2 * Cfg::D;     // [0] red, [1] any, [2] step of phase 2, [3] advance,
                                                     // [4] error, [5] err^(-1/8)
+    static constexpr int QP = CTL + 6;              // N = 64: the split QR's partial sums [2][4][D]
+    static_assert(QP + (Cfg::D == 128 ? 8 * Cfg::D : 0) == Cfg::PER, "slab layout");
 };
+
+// N = 64 (one orbit per block and per SM): the same Gram-Schmidt with the rows
+// split across the orbit's four warps (warp w takes rows 32w..32w+31 of the
+// columns lane + 32m), the four partial dot products of a column summed in a
+// fixed order from double-buffered shared memory; otherwise the warp holding
+// the last columns would work all 128 iterations alone.  Thread l still adds
+// ln R_ll to its S.
+template <int N>
+__device__ __forceinline__ void qr_step_split(double* slab, const int l, double& S)
+{
+    using Cfg = FputDpCfg<N>;
+    using Sl = FputDpSlab<N>;
+    constexpr int D = Cfg::D, WS = Cfg::WS, Q = D / 32;
+    static_assert(Cfg::G == 1, "one orbit per block");
+    double* W = slab + Sl::W;
+    double* P = slab + Sl::QP;
+    const int w = l / 32, lane = l % 32, r0 = 32 * w;
+    double inv[Q];
+#pragma unroll
+    for (int m = 0; m < Q; ++m) inv[m] = 1.0;
+    for (int j = 0; j < D; ++j) {
+        __syncwarp();  // rows of column j in this warp's block are final
+        double* Pb = P + (j & 1) * Q * D;
+        const double* wj = W + j * WS + r0;
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const int c = lane + 32 * m;
+            if (c >= j) {
+                const double* wc = W + c * WS + r0;
+                double a0 = 0.0, a1 = 0.0;
+#pragma unroll 4
+                for (int i = 0; i < 32; i += 2) {
+                    a0 = fma(wj[i], wc[i], a0);
+                    a1 = fma(wj[i + 1], wc[i + 1], a1);
+                }
+                Pb[w * D + c] = a0 + a1;
+            }
+        }
+        __syncthreads();
+        double nj = Pb[j];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) nj += Pb[q * D + j];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+            const int c = lane + 32 * m;
+            if (c > j) {
+                double r = Pb[c];
+#pragma unroll
+                for (int q = 1; q < Q; ++q) r += Pb[q * D + c];
+                const double cfac = -r / nj;
+                double* wc = W + c * WS + r0;
+#pragma unroll 4
+                for (int i = 0; i < 32; ++i) wc[i] = fma(cfac, wj[i], wc[i]);
+            } else if (c == j) {
+                inv[m] = rsqrt(nj);
+            }
+        }
+        if (l == j) S += 0.5 * log(nj);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+        double* wc = W + (lane + 32 * m) * WS + r0;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) wc[i] *= inv[m];
+    }
+    __syncthreads();
+}
 
 // Modified Gram-Schmidt of the orbit's W (thread l owns column l), when `mine`
 // is set for the orbit; every thread takes part in the barriers.  S += ln R_ll.
+// At N = 64 (one orbit per block, so `mine` is set whenever this runs) the
+// rows are split across the warps instead (qr_step_split).
 template <int N>
 __device__ __forceinline__ void qr_step(double* slab, const int l, const bool mine, double& S)
 {
     using Cfg = FputDpCfg<N>;
     using Sl = FputDpSlab<N>;
     constexpr int D = Cfg::D, WS = Cfg::WS;
+    if constexpr (D == 128) {
+        qr_step_split<N>(slab, l, S);
+        return;
+    }
     double* W = slab + Sl::W;
     double* red = slab + Sl::CTL;
     double* wl = W + l * WS;
