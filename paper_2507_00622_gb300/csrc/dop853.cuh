@@ -102,20 +102,62 @@ template <int J>
 constexpr bool kReadLater = read_later(J);
 static_assert(!read_later(11), "the last stage is never read by another stage");
 
+// The last stage that reads stage j's derivative (-1: none).
+constexpr int last_reader(int j)
+{
+    int r = -1;
+    for (int s = j + 1; s < 12; ++s)
+        if (kA[s][j] != 0.0) r = s;
+    return r;
+}
+
+// Slab row of stage s's derivative: the lowest row whose occupant no stage
+// after s reads (a stage reads all of its inputs before it writes its own
+// derivative, so a row read last by stage s itself can take it); -1 for a
+// stage that no later stage reads.  Stages 2 and 3 of the pair are read only
+// up to stages 3 and 5, so 11 derivatives fit in 9 rows.
+constexpr int k_row(int s)
+{
+    int occ[12] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    for (int t = 0; t <= s; ++t) {
+        if (!read_later(t)) {
+            if (t == s) return -1;
+            continue;
+        }
+        int row = 0;
+        while (occ[row] >= 0 && last_reader(occ[row]) > t) ++row;
+        occ[row] = t;
+        if (t == s) return row;
+    }
+    return -1;
+}
+constexpr int k_rows()
+{
+    int n = 0;
+    for (int s = 0; s < 12; ++s)
+        if (k_row(s) + 1 > n) n = k_row(s) + 1;
+    return n;
+}
+template <int S>
+constexpr int kRow = k_row(S);
+static_assert(k_rows() == 9, "the DOP853 pair's derivatives fit in 9 rows");
+
 // A thread's column of the block's shared array: H[s][t] (stage Hessians,
-// packed upper triangle, 12 stages) then K[s][i] (stage derivatives of the 11
-// stages a later stage reads), entry e at base[e * kBlock].  Accesses are
-// volatile so that stage values are re-read from shared memory instead of
-// being kept in registers.
+// packed upper triangle, 12 stages) then the stage derivatives a later stage
+// reads, in the k_rows() rows given by k_row, entry e at base[e * kBlock].
+// Accesses are volatile so that stage values are re-read from shared memory
+// instead of being kept in registers.
 template <class Sys>
 struct Slab {
     static constexpr int D = 2 * Sys::N, NH = Sys::NH;
-    static constexpr int kDoubles = 12 * NH + 11 * D;
+    static constexpr int kDoubles = 12 * NH + k_rows() * D;
     volatile double* base;
     __device__ __forceinline__ volatile double& H(int s, int t) const { return base[(s * NH + t) * kBlock]; }
-    __device__ __forceinline__ volatile double& K(int s, int i) const
+    template <int S>
+    __device__ __forceinline__ volatile double& K(int i) const
     {
-        return base[(12 * NH + s * D + i) * kBlock];
+        static_assert(kRow<S> >= 0, "a stage derivative that no later stage reads is not stored");
+        return base[(12 * NH + kRow<S> * D + i) * kBlock];
     }
 };
 
@@ -140,7 +182,7 @@ __device__ __forceinline__ double stage_sum(const Slab<Sys>& sl, const int i)
     static_for<0, S>([&](auto jc) {
         constexpr int j = decltype(jc)::value;
         constexpr double c = kA[S][j];
-        if constexpr (c != 0.0) acc = fma(c, sl.K(j, i), acc);
+        if constexpr (c != 0.0) acc = fma(c, sl.template K<j>(i), acc);
     });
     return acc;
 }
@@ -168,7 +210,7 @@ __device__ __forceinline__ void orbit_step(const Slab<Sys>& sl, const double* x,
         for (int t = 0; t < NH; ++t) sl.H(s, t) = H[t];
         if constexpr (kReadLater<s>) {
 #pragma unroll
-            for (int i = 0; i < D; ++i) sl.K(s, i) = f[i];
+            for (int i = 0; i < D; ++i) sl.template K<s>(i) = f[i];
         }
         constexpr double cb = kB[s], c5 = kE5[s], c3 = kB[s] - kB3[s];
 #pragma unroll
@@ -228,7 +270,7 @@ __device__ __forceinline__ void vector_step(const Slab<Sys>& sl, double* w, cons
         }
         if constexpr (kReadLater<s>) {
 #pragma unroll
-            for (int i = 0; i < D; ++i) sl.K(s, i) = m[i];
+            for (int i = 0; i < D; ++i) sl.template K<s>(i) = m[i];
         }
         constexpr double cb = kB[s];
 #pragma unroll
