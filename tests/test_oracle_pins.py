@@ -459,6 +459,42 @@ def test_lyapunov_harmonic_chain_limit():
     assert abs(lam[:, 0].sum()) < 1e-6
 
 
+def test_fput_linear_chain_ensemble_follows_matrix_exponential():
+    """alpha = beta = 0: the chain is linear, x' = A x with A = [[0, I], [-K, 0]]
+    and K the fixed-end Laplacian (Eq. ham_eqs_FPU at k = 1), and the deviation
+    vectors obey the same equation.  After time t the ensemble's state is
+    expm(A t) x0 and each renormalised vector the unit vector along
+    expm(A t) w0, up to RK4's O(h^4) error; GALI_2 and SALI follow from those
+    unit vectors.  An independent check (scipy's expm) of the FPUT ensemble
+    path: Hessian, stage loop, renormalisation and indicators together."""
+    from scipy.linalg import expm
+    N, k, n, h, steps = 6, 3, 5, 0.005, 2000
+    F = O.fput(N, beta=0.0)
+    K = 2.0 * np.eye(N) - np.eye(N, k=1) - np.eye(N, k=-1)
+    A = np.block([[np.zeros((N, N)), np.eye(N)], [-K, np.zeros((N, N))]])
+    Q, P = normal_mode_draws(17, N, n)
+    ics = O.fput_mode_ics(F, Q, P, np.full(n, 0.3))
+    e = O.Ensemble(F, O.params(h, 1, n_dev=k), ics, seed=21)
+    w0 = e.w.copy()
+    e.integrate(O.params(h, steps, n_dev=k))
+    Phi = expm(A * h * steps)
+    d = 2 * N
+    np.testing.assert_allclose(e.x, Phi @ ics, atol=1e-9)
+    U = np.empty((k, d, n))
+    for j in range(k):
+        v = Phi @ w0[j * d:(j + 1) * d]
+        U[j] = v / np.linalg.norm(v, axis=0)
+        np.testing.assert_allclose(e.w[j * d:(j + 1) * d], U[j], atol=1e-9)
+    sali, gali, _ = e.indicators()
+    for o in range(n):
+        for m in range(2, k + 1):  # GALI_m from the first m unit vectors
+            sv = np.linalg.svd(U[:m, :, o].T, compute_uv=False)
+            np.testing.assert_allclose(gali[m - 2, o], np.prod(sv), rtol=1e-7)
+        a, b = U[0, :, o], U[1, :, o]
+        np.testing.assert_allclose(sali[o], min(np.linalg.norm(a + b), np.linalg.norm(a - b)),
+                                   rtol=1e-7)
+
+
 # --------------------------------------------------------------------------
 # Lagrangian descriptors
 # --------------------------------------------------------------------------
