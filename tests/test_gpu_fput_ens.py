@@ -256,3 +256,35 @@ def test_fput_ensemble_argument_checks():
     assert e.value.code == chs.CHS_E_UNSUPPORTED
     S.close()
     S5.close()
+
+
+@pytest.mark.parametrize("integ", [RK4, DP])
+def test_fput_ensemble_linear_chain_matches_matrix_exponential(integ):
+    """alpha = beta = 0: state and renormalised vectors equal expm(A t) applied to
+    the start (A = [[0, I], [-K, 0]], K the fixed-end Laplacian), up to the
+    integrator's error; SALI and GALI_2..4 equal those of the exact unit vectors."""
+    from scipy.linalg import expm
+    N, n, k, h, steps = 16, 7, 4, 0.005, 2000
+    K = 2.0 * np.eye(N) - np.eye(N, k=1) - np.eye(N, k=-1)
+    A = np.block([[np.zeros((N, N)), np.eye(N)], [-K, np.zeros((N, N))]])
+    Q, P = normal_mode_draws(23, N, n)
+    ics = O.fput_mode_ics(O.fput(N, beta=0.0), Q, P, np.full(n, 0.2 * N))
+    w0 = np.random.default_rng(24).standard_normal((k * 2 * N, n))
+    g = gpu_run(FPUT, N, ics, None, dt=h, n_steps=steps, k=k, ld_p=0.0, sys_params=(1.0, 0.0, 0.0),
+                integrator=integ, w_in=w0)
+    Phi = expm(A * h * steps)
+    d = 2 * N
+    np.testing.assert_allclose(g["x"], Phi @ ics, atol=1e-8)
+    U = []
+    for j in range(k):
+        v = Phi @ w0[j * d:(j + 1) * d]
+        U.append(v / np.linalg.norm(v, axis=0))
+        np.testing.assert_allclose(g["w"][j * d:(j + 1) * d], U[j], atol=1e-8)
+    U = np.stack(U)
+    for o in range(n):
+        for m in range(2, k + 1):
+            sv = np.linalg.svd(U[:m, :, o].T, compute_uv=False)
+            np.testing.assert_allclose(g["gali"][m - 2, o], np.prod(sv), rtol=1e-6)
+        a, b = U[0, :, o], U[1, :, o]
+        np.testing.assert_allclose(g["sali"][o], min(np.linalg.norm(a + b), np.linalg.norm(a - b)),
+                                   rtol=1e-6)
