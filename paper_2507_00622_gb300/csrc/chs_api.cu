@@ -439,7 +439,7 @@ chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_
             a.step0 = p->step0 + c * chunk_steps;
             a.n_steps = std::min<int64_t>(chunk_steps, p->n_steps - c * chunk_steps);
             le = cudaMemsetAsync(cb, 0, sizeof(int32_t), cs);
-            const chs::OrbitList ol{la, ca, lb, cb};
+            const chs::OrbitList ol{la, ca, lb, cb, nullptr};
             if (le == cudaSuccess) le = launch_selected(s->sp, p, a, ep, &ol, cs);
             std::swap(la, lb);
             std::swap(ca, cb);

@@ -98,7 +98,7 @@ extern "C" chs_status chs_integrate_compacted_static(chs_system s, const chs_par
         a.step0 = p->step0 + c * chunk_steps;
         a.n_steps = (p->n_steps - c * chunk_steps < chunk_steps) ? p->n_steps - c * chunk_steps : chunk_steps;
         ce = cudaMemsetAsync(cb, 0, sizeof(int32_t), st);
-        const chs::OrbitList ol{la, ca, lb, cb};
+        const chs::OrbitList ol{la, ca, lb, cb, nullptr};
         if (ce == cudaSuccess)
             ce = chs::api_launch_integrate(sp, p, a, ep, &ol, st);
         int32_t* t = la;
