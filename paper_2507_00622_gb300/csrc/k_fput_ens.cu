@@ -13,19 +13,10 @@
 // steps of size 0 (its state is not written) until every orbit of the block is
 // done.
 #include "fput_ens.cuh"
+#include "seed.cuh"
 
 namespace chs {
 namespace {
-
-// SplitMix64 finaliser applied to the state seed + m * 0x9e3779b97f4a7c15,
-// i.e. the m-th output of the stream seeded with `seed`.
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t m)
-{
-    uint64_t z = seed + m * 0x9e3779b97f4a7c15ULL;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
-    return z ^ (z >> 31);
-}
 
 // Set-up, one thread per orbit: x <- ics, H0, status, counters; vector j is
 // w_in's (normalised with renorm) or seeded: component c is the m-th output of
@@ -73,9 +64,7 @@ k_fput_ens_init(const SysPar sp, const int K, const int renorm, const uint64_t s
             if (w_in) {
                 v = w_in[((int64_t)j * D + c) * n + o];
             } else {
-                const uint64_t m = ((uint64_t)o * K + j) * D + c + 1;
-                const uint64_t z = splitmix64_at(seed, m);
-                v = __dsub_rn(__dmul_rn(2.0, __dmul_rn((double)(z >> 11), 0x1.0p-53)), 1.0);
+                v = seed_uniform(seed, ((uint64_t)o * K + j) * D + c + 1);
             }
             wj[c * n] = v;
             acc = __dadd_rn(acc, __dmul_rn(v, v));

@@ -26,18 +26,11 @@
 #include <math.h>
 
 #include "rk4_common.cuh"
+#include "seed.cuh"
 
 namespace chs {
 
 __host__ __device__ constexpr int tri(int i, int j) { return j * (j + 1) / 2 + i; }
-
-__device__ __forceinline__ uint64_t splitmix64_at32(uint64_t seed, uint64_t m)
-{
-    uint64_t z = seed + m * 0x9e3779b97f4a7c15ULL;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
-    return z ^ (z >> 31);
-}
 
 template <class Sys, int K>
 __global__ void __launch_bounds__(kSmallBlock)
@@ -72,9 +65,7 @@ k_init_f32(const SysPar sp, const uint64_t seed, const double* __restrict__ ics,
             if (w_in) {
                 V[j][c] = (double)w_in[(j * D + c) * n + o];
             } else {
-                const uint64_t m = ((uint64_t)o * K + j) * D + c + 1;
-                const uint64_t z = splitmix64_at32(seed, m);
-                V[j][c] = __dsub_rn(__dmul_rn(2.0, __dmul_rn((double)(z >> 11), 0x1.0p-53)), 1.0);
+                V[j][c] = seed_uniform(seed, ((uint64_t)o * K + j) * D + c + 1);
             }
         }
         double acc = 0.0;

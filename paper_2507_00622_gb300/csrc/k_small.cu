@@ -11,22 +11,13 @@
 #include <type_traits>
 
 #include "rk4_common.cuh"
+#include "seed.cuh"
 
 namespace chs {
 
 // --------------------------------------------------------------------------
 // Ensemble set-up
 // --------------------------------------------------------------------------
-
-// SplitMix64 finaliser applied to the state seed + m * 0x9e3779b97f4a7c15,
-// i.e. the m-th output of the stream seeded with `seed`.
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t m)
-{
-    uint64_t z = seed + m * 0x9e3779b97f4a7c15ULL;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
-    return z ^ (z >> 31);
-}
 
 template <class Sys, int K, typename VT>
 __global__ void __launch_bounds__(kSmallBlock)
@@ -61,9 +52,7 @@ k_init(const SysPar sp, const int renorm, const uint64_t seed, const double* __r
             if (w_in) {
                 v[c] = (double)w_in[(j * D + c) * n + o];
             } else {
-                const uint64_t m = ((uint64_t)o * K + j) * D + c + 1;
-                const uint64_t z = splitmix64_at(seed, m);
-                v[c] = __dsub_rn(__dmul_rn(2.0, __dmul_rn((double)(z >> 11), 0x1.0p-53)), 1.0);
+                v[c] = seed_uniform(seed, ((uint64_t)o * K + j) * D + c + 1);
             }
         }
         // seeded vectors are normalised, and every vector once more with renorm;
