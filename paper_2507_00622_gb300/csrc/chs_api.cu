@@ -196,7 +196,7 @@ SysPar api_syspar(chs_system s) { return s->sp; }
 
 extern "C" {
 
-const char* chs_version(void) { return "chs 0.2.0 (sm_103a)"; }
+const char* chs_version(void) { return "chs 0.3.0 (sm_103a)"; }
 
 const char* chs_last_error(void) { return g_err.c_str(); }
 
