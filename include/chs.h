@@ -149,13 +149,16 @@ typedef struct {
 
 typedef struct chs_system_s* chs_system;
 
-/* Creates a system handle on the current CUDA device.  `params` (host) holds
- * n_params model constants: FPUT {k, alpha, beta}; QUARTIC3 {eps}; none for
- * the others.  CHS_E_INVALID for an unknown model or a bad n_dof. */
+/* Creates a system handle on the current CUDA device for one of the
+ * Hamiltonians of Sec. Examples (Eq. Ham_HH; Eq. ham_FPU with fixed ends) or
+ * the quartic and test oscillators.  `params` (host) holds n_params model
+ * constants: FPUT {k, alpha, beta}; QUARTIC3 {eps}; none for the others.
+ * CHS_E_INVALID for an unknown model or a bad n_dof. */
 chs_status chs_create_system(chs_system* out, chs_model model, int32_t n_dof,
                              const double* params, int32_t n_params);
 
-/* Destroys a handle created by chs_create_system (NULL is accepted). */
+/* Destroys a handle created by chs_create_system (NULL is accepted); frees
+ * the handle's cached graph and private stream.  No paper counterpart. */
 chs_status chs_destroy_system(chs_system s);
 
 /* Phase-space dimension d = 2N of the system, or -1 for a NULL handle. */
@@ -183,7 +186,8 @@ chs_status chs_fput_mode_ics(chs_system s, int64_t n, const double* Qm, const do
                              const double* E, double* ics_out, void* stream);
 
 /* Quartic-3 initial conditions on energy shells (a0 for the coupled quartic
- * oscillator): the direction u = dir / |dir| of each 6-component draw is scaled
+ * oscillator, a test system outside the paper; the same radial scaling as
+ * the FPU normal modes of Sec. Examples): the direction u = dir / |dir| of each 6-component draw is scaled
  * by s > 0 so that H(s u) = E_o; with H2 = |u|^2/2 and H4 = eps (u1^2 u2^2 +
  * u2^2 u3^2 + u1^2 u3^2), s^2 = 2E / (H2 + sqrt(H2^2 + 4 H4 E)).
  * dirs [6][n], E [n], ics_out [6][n].  CHS_E_UNSUPPORTED for other models. */
@@ -274,8 +278,8 @@ chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_a
                                   const chs_ensemble* e, double* t, double* h, double* err_last,
                                   double* err_max, int64_t* n_rejected, void* stream);
 
-/* The same integration as chs_integrate_batch (identical results, bit for bit),
- * run by a persistent grid (every SM filled to the kernel's occupancy) whose
+/* The same integration as chs_integrate_batch (the fixed-step solvers of Sec.
+ * Functionalities; identical results, bit for bit), run by a persistent grid (every SM filled to the kernel's occupancy) whose
  * threads take orbit indices from a work queue, one orbit after another: a
  * thread whose orbit stops early -- its t_end, early exit, escape or any other
  * freeze -- takes the next orbit at once, so orbits of uneven length leave no
@@ -287,11 +291,13 @@ chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_a
 chs_status chs_integrate_persistent(chs_system s, const chs_params* p, const chs_ensemble* e,
                                     void* work, size_t work_bytes, void* stream);
 
-/* Bytes of device scratch that chs_integrate_compacted needs for n orbits. */
+/* Bytes of device scratch that chs_integrate_compacted needs for n orbits
+ * (two orbit lists and their counters).  No paper counterpart. */
 size_t chs_compact_work_size(int64_t n_orbits);
 
-/* The same integration as chs_integrate_batch (p->n_steps steps from step
- * p->step0, identical results bit for bit), run in chunks of chunk_steps steps
+/* The same integration as chs_integrate_batch (the fixed-step solvers of Sec.
+ * Functionalities; p->n_steps steps from step p->step0, identical results bit
+ * for bit), run in chunks of chunk_steps steps
  * over a list of the orbits still running: after every chunk the orbits that
  * froze (early exit, escape, ...) or reached their t_end are dropped from the
  * list, so later chunks launch only over live orbits.  The chunk sequence is
@@ -305,7 +311,8 @@ chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_
                                    int32_t chunk_steps, void* work, size_t work_bytes,
                                    void* stream);
 
-/* The run of chs_integrate_compacted (same results), for callers that cannot
+/* The run of chs_integrate_compacted (same results; the fixed-step solvers of
+ * Sec. Functionalities), for callers that cannot
  * provide a scratch buffer: callers whose device memory belongs to another
  * allocator (a framework's caching allocator, a fixed arena sized at start-up)
  * that does not hand out extra buffers, or whose rules forbid device
@@ -386,7 +393,9 @@ chs_status chs_lyapunov_adaptive(chs_system s, const chs_params* p, const chs_ad
 
 /* ------------------------------------------------------------------------
  * Early-stop surrogate (a learned classifier of the final label; the method's
- * indicators stay the judge).  A 12 -> 128 -> 128 -> 128 -> 2 ReLU perceptron
+ * indicators stay the judge).  Not in the paper: it learns the labels the
+ * indicators of Sec. Functionalities (SALI, LD) give, from their early values,
+ * and every entry point of this block serves it.  A 12 -> 128 -> 128 -> 128 -> 2 ReLU perceptron
  * with BF16 weights and activations and FP32 accumulation.  Features of an
  * orbit at the decision time t, from S <= 10 SALI samples taken at
  * t_i = (i + 1) t / S and the LD M_p(t):
@@ -448,7 +457,8 @@ typedef struct {
     int32_t* status_out;
 } chs_lyap_job;
 
-/* Runs several Lyapunov jobs -- typically FPUT chains of different N, each a
+/* Runs several Lyapunov jobs (Sec. Functionalities, Lyapunov item; the FPU
+ * example of Sec. Examples) -- typically FPUT chains of different N, each a
  * differently shaped kernel -- as one CUDA graph whose branches run
  * concurrently, so that blocks of different chain lengths share the SMs (an
  * N = 64 block holds 143 KB of shared memory and leaves room for smaller
@@ -456,10 +466,11 @@ typedef struct {
  * jobs must be on the current device; at most 16 jobs. */
 chs_status chs_lyapunov_batch(const chs_lyap_job* jobs, int32_t n_jobs, void* stream);
 
-/* Message for the last non-OK status returned on this thread ("" if none). */
+/* Message for the last non-OK status returned on this thread ("" if none).
+ * Diagnostics; no paper counterpart. */
 const char* chs_last_error(void);
 
-/* Library version string. */
+/* Library version string.  Diagnostics; no paper counterpart. */
 const char* chs_version(void);
 
 #ifdef __cplusplus
