@@ -64,6 +64,18 @@
  *   o_seed_vectors                 deviation vectors uniform in [-1, 1) from
  *                                  the SplitMix64 generator (Steele, Lea and
  *                                  Flood, OOPSLA 2014), then normalised.
+ *   o_ensemble_init                the ensemble's start: state, H0 from the
+ *                                  Hamiltonians above, statuses, and the
+ *                                  deviation vectors (given or seeded).
+ *   o_lyapunov_adaptive            the Lyapunov spectrum under DOP 8(5) (the
+ *                                  adaptive solver with QR, Sec.
+ *                                  Functionalities).
+ *   o_dop853_tableau               the pair's coefficients (Hairer et al.,
+ *                                  Sec. II.10), for the order-condition pins.
+ *   o_shell_ics                    quartic-oscillator states scaled onto an
+ *                                  energy shell (a test system outside the
+ *                                  paper; the radial scaling of the FPU
+ *                                  normal-mode states).
  */
 #include <math.h>
 #include <stdint.h>
