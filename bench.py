@@ -102,7 +102,46 @@ def dp_flops_per_orbit_step(k: int, ld: bool) -> int:
 
 
 def fp64_peak_tflops(sm_mhz: float) -> float:
+    """The formula FP64 peak: 152 SMs x 2 DFMA lanes per clock x 2 flops."""
     return SM_COUNT * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+
+
+def probe_rate(kind: int, n_blocks: int, n_threads: int, n_iter: int, reps: int = 5) -> dict:
+    """Best-of-reps rate of one pipe probe (chs_peak_probe), timed with CUDA
+    events on the launching stream after one untimed launch: operations per
+    second (flops for the FMA and MMA probes, square roots for the sqrt probe)."""
+    import torch
+
+    from paper_2507_00622_gb300 import chs
+
+    sink = torch.empty(n_blocks * n_threads, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    chs.chs_peak_probe(kind, n_blocks, n_threads, n_iter, sink, stream)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        chs.chs_peak_probe(kind, n_blocks, n_threads, n_iter, sink, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    ops = chs.chs_probe_ops_per_thread(kind, n_iter) * n_blocks * n_threads
+    return {"ops_per_s": ops / (best / 1e3), "ms": best, "blocks": n_blocks, "threads": n_threads,
+            "n_iter": n_iter}
+
+
+def measured_fp64_peak(sm_count: int) -> dict:
+    """The FP64 FMA peak measured by the DFMA probe (8 independent chains per
+    thread, 32 warps per SM), with the SM clock sampled while it ran."""
+    from paper_2507_00622_gb300 import chs
+
+    clocks = ClockSampler(None)
+    clocks.start()
+    r = probe_rate(chs.PROBE_DFMA, sm_count * 4, 256, 1 << 17)
+    clk = clocks.stop()
+    return {"tflops": r["ops_per_s"] / 1e12, "sm_mhz": clk["sm_mhz"], "ms": r["ms"],
+            "probe": f"DFMA, {sm_count * 4} x 256 threads x 8 chains x {r['n_iter']} iterations, best of 5"}
 
 
 def shard_rows(ny: int, rank: int, world: int) -> tuple[int, int, int, int]:
@@ -274,6 +313,50 @@ def cpu_quartic_sample(chunk: int, budget_s: float, n_sample: int = 16384):
                       f"({done} orbit-steps in {el:.1f} s)"}
 
 
+def run_peaks(args):
+    """Pipe peaks on this GPU (chs_peak_probe, CUDA events, best of 5): FP64 FMA,
+    FP32 FMA, FP64 sqrt and FP64 mma.sync m8n8k4 at 32 warps per SM; the FP64 FMA
+    rate against warps per SM (one warp per block, 8 independent chains per
+    thread); and the dependent FP64 FMA latency (one chain, one warp per SM)."""
+    import torch
+
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+
+    cuda_build.build()
+    chs.load()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    clocks = ClockSampler(None)
+    clocks.start()
+    time.sleep(0.3)
+    full = {"dfma": probe_rate(chs.PROBE_DFMA, sms * 4, 256, 1 << 17),
+            "ffma": probe_rate(chs.PROBE_FFMA, sms * 4, 256, 1 << 21),
+            "dsqrt": probe_rate(chs.PROBE_DSQRT, sms * 4, 256, 1 << 12),
+            "dmma": probe_rate(chs.PROBE_DMMA, sms * 4, 256, 1 << 14)}
+    sweep = []
+    for w in (1, 2, 3, 4, 6, 8, 12, 16, 32):
+        r = probe_rate(chs.PROBE_DFMA, sms * w, 32, max(4096, (1 << 20) // w))
+        sweep.append({"warps_per_sm": w, "tflops": r["ops_per_s"] / 1e12, "ms": r["ms"]})
+    dep = probe_rate(chs.PROBE_DFMA_DEP, sms, 32, 1 << 18)
+    dep4 = probe_rate(chs.PROBE_DFMA_DEP, sms * 4, 32, 1 << 18)
+    clk = clocks.stop()
+    mhz = clk["sm_mhz"] or 2070.0
+    line = {"workload": "pipe_peaks", "sms": sms, "clocks": clk,
+            "fp64_fma_tflops": full["dfma"]["ops_per_s"] / 1e12,
+            "fp32_fma_tflops": full["ffma"]["ops_per_s"] / 1e12,
+            "fp64_sqrt_per_s": full["dsqrt"]["ops_per_s"],
+            "fp64_mma_m8n8k4_tflops": full["dmma"]["ops_per_s"] / 1e12,
+            "fp64_formula_tflops": fp64_peak_tflops(mhz),
+            "fp64_fma_lanes_per_sm_per_clock": full["dfma"]["ops_per_s"] / 2 / (sms * mhz * 1e6),
+            "fp64_vs_warps_per_sm": sweep,
+            "fp64_dependent_fma_cycles": {
+                "1_warp_per_sm": dep["ms"] * 1e-3 * mhz * 1e6 / dep["n_iter"],
+                "4_warps_per_sm": dep4["ms"] * 1e-3 * mhz * 1e6 / dep4["n_iter"]},
+            "probes": full}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -442,7 +525,11 @@ def run_gpu(args):
         per_launch_steps = (exec1 - exec0) / args.steps
         achieved = f64 * per_launch_steps / (kern_ms / 1e3) / 1e12
         peak_mhz = clk["sm_max_mhz"] or 2070.0
-        peak = fp64_peak_tflops(peak_mhz)
+        formula = fp64_peak_tflops(peak_mhz)
+        mp = measured_fp64_peak(torch.cuda.get_device_properties(local).multi_processor_count)
+        # the probe's rate at the clock the timed region ran at
+        scale = (clk["sm_mhz"] / mp["sm_mhz"]) if (clk["sm_mhz"] and mp["sm_mhz"]) else 1.0
+        peak = mp["tflops"] * scale
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -465,7 +552,16 @@ def run_gpu(args):
                          "kernel": "k_integrate_dp<HenonHeiles,4,LD>" if dop else
                                    "k_integrate<HenonHeiles,4,LD>",
                          "flops_per_orbit_step": {"fp64": f64, "fp32": f32},
-                         "peak_basis": f"152 SMs x 2 DFMA/clk x 2 flop x {peak_mhz:.0f} MHz",
+                         "flops_basis": "algorithmic count of the method as the oracle computes it "
+                                        "(direct stage-wise RK4 on orbit, vectors and LD; FMA = 2, "
+                                        "sqrt = 1); the RK4 kernel executes the vectors by the "
+                                        "equivalent one-step propagator and fewer FP64 instructions",
+                         "peak_basis": f"measured: FP64 FMA probe {mp['tflops']:.4f} TFLOP/s at "
+                                       f"{mp['sm_mhz']} MHz, scaled to the timed region's median "
+                                       f"{clk['sm_mhz']} MHz (x{scale:.4f}); {mp['probe']}",
+                         "peak_formula": formula,
+                         "peak_formula_basis": f"152 SMs x 2 DFMA/clk x 2 flop x {peak_mhz:.0f} MHz",
+                         "frac_of_formula": achieved / formula,
                          "kernel_ms_avg": kern_ms},
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"],
                        "reasons": clk["reasons"]},
@@ -583,6 +679,7 @@ def run_fput(args):
     t1.record(stream)
     torch.cuda.synchronize()
     total_ms = t0.elapsed_time(t1)
+    mp = measured_fp64_peak(torch.cuda.get_device_properties(0).multi_processor_count)
     per_n = {}
     for j, (N, *_rest) in enumerate(runs):
         if args.fput_batch:
@@ -592,7 +689,8 @@ def run_fput(args):
         os_ = n * args.chunk / (ms / 1e3)
         tf = flops(N, qr[N]) * os_ / 1e12
         per_n[str(N)] = {"orbit_steps_per_s": os_, "kernel_ms": ms, "fp64_tflops": tf,
-                         "frac_of_fp64_peak": tf / fp64_peak_tflops(2070.0), "qr_every": qr[N],
+                         "frac_of_fp64_peak": tf / mp["tflops"],
+                         "frac_of_fp64_formula": tf / fp64_peak_tflops(2070.0), "qr_every": qr[N],
                          "block_threads": blk[N] or None}
     value = len(runs) * n * args.chunk * args.steps / (total_ms / 1e3)
     print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
@@ -606,6 +704,8 @@ def run_fput(args):
                                  "launch": "one CUDA graph, concurrent branches" if args.fput_batch
                                            else "one launch per N"},
                       "per_N": per_n,
+                      "fp64_peak": {"measured_tflops": mp["tflops"], "sm_mhz": mp["sm_mhz"],
+                                    "probe": mp["probe"], "formula_tflops": fp64_peak_tflops(2070.0)},
                       **({} if args.no_cpu_baseline else
                          {"cpu_baseline": cpu_fput_sample(Ns, args.chunk, qr, args.cpu_budget,
                                                           args.integrator)})}))
@@ -1031,7 +1131,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--workload", choices=["grid", "fput", "classify", "quartic", "integrators",
-                                           "saturation", "fput_gali"], default="grid")
+                                           "saturation", "fput_gali", "peaks"], default="grid")
     ap.add_argument("--quartic-orbits", type=int, default=4_194_304)
     ap.add_argument("--persistent", action="store_true",
                     help="quartic workload: one persistent work-queue launch per bench step")
@@ -1066,6 +1166,8 @@ def main():
         return run_quartic(args)
     if args.workload == "fput_gali":
         return run_fput_gali(args)
+    if args.workload == "peaks":
+        return run_peaks(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

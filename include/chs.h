@@ -466,6 +466,32 @@ typedef struct {
  * jobs must be on the current device; at most 16 jobs. */
 chs_status chs_lyapunov_batch(const chs_lyap_job* jobs, int32_t n_jobs, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Throughput probes of the arithmetic pipes (a measurement aid for the
+ * roofline of the integrators, which are bound by the FP64 pipe, or by FP32 for
+ * the FP32 deviation-vector frame).  The paper has no counterpart.
+ * ------------------------------------------------------------------------ */
+typedef enum {
+    CHS_PROBE_DFMA = 1,     /* FP64 fma, 8 independent chains per thread */
+    CHS_PROBE_DFMA_DEP = 2, /* FP64 fma, one dependent chain per thread */
+    CHS_PROBE_FFMA = 3,     /* FP32 fma, 8 independent chains per thread */
+    CHS_PROBE_DSQRT = 4,    /* FP64 sqrt (with one fma), 8 chains per thread */
+    CHS_PROBE_DMMA = 5      /* FP64 mma.sync m8n8k4, 8 accumulators per warp */
+} chs_probe_kind;
+
+/* Launches one probe kernel of n_blocks x n_threads threads (n_threads a
+ * multiple of 32 in 32..1024, n_blocks in 1..65535), each running n_iter
+ * iterations (1..2^28) of its chains; sink [n_blocks * n_threads] (device,
+ * FP64, caller-owned) receives one value per thread.  Time it with events on
+ * `stream`; the work per thread is chs_probe_ops_per_thread(kind, n_iter).
+ * The run time grows with n_blocks * n_threads * n_iter: the caller bounds it. */
+chs_status chs_peak_probe(int32_t kind, int32_t n_blocks, int32_t n_threads, int64_t n_iter, double* sink,
+                          void* stream);
+
+/* Operations one thread of chs_peak_probe performs: flops (FMA = 2) for the
+ * FMA and MMA probes, square roots for CHS_PROBE_DSQRT; 0 for an unknown kind. */
+double chs_probe_ops_per_thread(int32_t kind, int64_t n_iter);
+
 /* Message for the last non-OK status returned on this thread ("" if none).
  * Diagnostics; no paper counterpart. */
 const char* chs_last_error(void);

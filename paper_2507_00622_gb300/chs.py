@@ -31,7 +31,8 @@ EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_sec
            "chs_indicators",
            "chs_lyapunov_spectrum", "chs_lyapunov_batch", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
            "chs_mlp_loss_grad", "chs_mlp_backward", "chs_mlp_adam", "chs_surrogate_decide",
-           "chs_last_error", "chs_version")
+           "chs_peak_probe", "chs_probe_ops_per_thread", "chs_last_error", "chs_version")
+PROBE_DFMA, PROBE_DFMA_DEP, PROBE_FFMA, PROBE_DSQRT, PROBE_DMMA = 1, 2, 3, 4, 5
 
 
 class ChsError(RuntimeError):
@@ -109,6 +110,8 @@ def load(path: str | None = None):
         "chs_mlp_backward": (C.c_int, [P, P, P, P, I64, P, P, P]),
         "chs_mlp_adam": (C.c_int, [P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, P, P]),
         "chs_surrogate_decide": (C.c_int, [P, P, I32, P, D, P, D, I64, P, P, P]),
+        "chs_peak_probe": (C.c_int, [I32, I32, I32, I64, P, P]),
+        "chs_probe_ops_per_thread": (D, [I32, I64]),
         "chs_last_error": (C.c_char_p, []),
         "chs_version": (C.c_char_p, []),
     }
@@ -281,6 +284,14 @@ def chs_surrogate_decide(params, series, n_samples, ld, t_decide, E, confidence,
                          stream=None):
     _check(load().chs_surrogate_decide(_ptr(params), _ptr(series), n_samples, _ptr(ld), t_decide, _ptr(E),
                                        confidence, n, _ptr(status), _ptr(prob), _stream(stream)))
+
+
+def chs_peak_probe(kind: int, n_blocks: int, n_threads: int, n_iter: int, sink, stream=None):
+    _check(load().chs_peak_probe(kind, n_blocks, n_threads, n_iter, _ptr(sink), _stream(stream)))
+
+
+def chs_probe_ops_per_thread(kind: int, n_iter: int) -> float:
+    return float(load().chs_probe_ops_per_thread(kind, n_iter))
 
 
 def chs_last_error() -> str:

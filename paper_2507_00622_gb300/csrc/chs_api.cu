@@ -653,6 +653,24 @@ chs_status chs_lyapunov_adaptive(chs_system s, const chs_params* p, const chs_ad
                        "adaptive Lyapunov launch");
 }
 
+chs_status chs_peak_probe(int32_t kind, int32_t n_blocks, int32_t n_threads, int64_t n_iter, double* sink,
+                          void* stream)
+{
+    if (kind < CHS_PROBE_DFMA || kind > CHS_PROBE_DMMA) return fail(CHS_E_INVALID, "unknown probe kind %d", kind);
+    if (n_blocks < 1 || n_blocks > 65535) return fail(CHS_E_INVALID, "n_blocks must be in 1..65535");
+    if (n_threads < 32 || n_threads > 1024 || n_threads % 32 != 0)
+        return fail(CHS_E_INVALID, "n_threads must be a multiple of 32 in 32..1024");
+    if (n_iter < 1 || n_iter > ((int64_t)1 << 28)) return fail(CHS_E_INVALID, "n_iter must be in 1..2^28");
+    if (!sink) return fail(CHS_E_INVALID, "sink is NULL");
+    return cuda_status(chs::launch_peak_probe(kind, n_blocks, n_threads, n_iter, sink, as_stream(stream)),
+                       "probe launch");
+}
+
+double chs_probe_ops_per_thread(int32_t kind, int64_t n_iter)
+{
+    return n_iter < 1 ? 0.0 : chs::probe_ops_per_thread(kind, n_iter);
+}
+
 size_t chs_mlp_param_count(void) { return chs::mlp_param_count(); }
 
 chs_status chs_mlp_features(const double* sali_series, int32_t n_samples, const double* ld,

@@ -114,6 +114,12 @@ cudaError_t launch_fput_lyap(const SysPar& sp, const StepArgs& a, int64_t n, con
                              const int32_t* ic_status, double* lambda, int32_t* status,
                              cudaStream_t st);
 cudaError_t prepare_fput_lyap(int n_dof);  // sets the shared-memory attribute once
+// Short chains (N = 4, 8): four lanes per orbit (k_fput_lanes.cu).
+bool fput_lyap_lanes_supported(int n_dof);
+cudaError_t launch_fput_lyap_lanes(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
+                                   const int32_t* ic_status, double* lambda, int32_t* status,
+                                   cudaStream_t st);
+cudaError_t prepare_fput_lyap_lanes(int n_dof);
 
 // Surrogate perceptron (k_mlp.cu).
 size_t mlp_param_count();
@@ -139,6 +145,11 @@ cudaError_t launch_fput_ens(const SysPar& sp, int integrator, int k, const StepA
                             cudaStream_t st);
 cudaError_t launch_fput_ens_indicators(const SysPar& sp, int k, double thr, const EnsPtrs& e, double* sali,
                                        double* gali, int8_t* label, cudaStream_t st);
+
+// Pipe throughput probes (k_peaks.cu).
+cudaError_t launch_peak_probe(int kind, int n_blocks, int n_threads, int64_t n_iter, double* sink,
+                              cudaStream_t st);
+double probe_ops_per_thread(int kind, int64_t n_iter);
 
 // Which systems each kernel family supports.
 bool small_model(int model);

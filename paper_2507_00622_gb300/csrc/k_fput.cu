@@ -385,6 +385,7 @@ static cudaError_t prepare_n()
 
 cudaError_t prepare_fput_lyap(int n_dof)
 {
+    if (fput_lyap_lanes_supported(n_dof)) return prepare_fput_lyap_lanes(n_dof);
     switch (n_dof) {
     case 4: return prepare_n<4>();
     case 8: return prepare_n<8>();
@@ -430,6 +431,7 @@ cudaError_t launch_fput_lyap(const SysPar& sp, const StepArgs& a, int64_t n, con
                              cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
+    if (fput_lyap_lanes_supported(sp.n_dof)) return launch_fput_lyap_lanes(sp, a, n, ics, ic_status, lambda, status, st);
     switch (sp.n_dof) {
     case 4: return fput_lyap_n<4>(sp, a, n, ics, ic_status, lambda, status, st);
     case 8: return fput_lyap_n<8>(sp, a, n, ics, ic_status, lambda, status, st);

@@ -90,3 +90,21 @@ def test_binding_refuses_host_tensors(lib):
     from paper_2507_00622_gb300 import chs
     with pytest.raises(ValueError):
         chs._ptr(torch.zeros(4))
+
+
+def test_peak_probe_validates_before_cuda(lib):
+    from paper_2507_00622_gb300 import chs
+    assert lib.chs_peak_probe(0, 1, 32, 10, None, None) == chs.CHS_E_INVALID
+    assert lib.chs_peak_probe(chs.PROBE_DFMA, 1, 33, 10, None, None) == chs.CHS_E_INVALID
+    assert lib.chs_peak_probe(chs.PROBE_DFMA, 0, 32, 10, None, None) == chs.CHS_E_INVALID
+    assert lib.chs_peak_probe(chs.PROBE_DFMA, 1, 32, 1 << 29, None, None) == chs.CHS_E_INVALID
+    assert lib.chs_peak_probe(chs.PROBE_DFMA, 1, 32, 10, None, None) == chs.CHS_E_INVALID
+    assert "sink" in chs.chs_last_error()
+    # work per thread: 8 chains of FMA (2 flops) per iteration, iterations in groups of 4
+    assert chs.chs_probe_ops_per_thread(chs.PROBE_DFMA, 1000) == 16000.0
+    assert chs.chs_probe_ops_per_thread(chs.PROBE_DFMA, 1001) == 16 * 1004.0
+    assert chs.chs_probe_ops_per_thread(chs.PROBE_DFMA_DEP, 1000) == 2000.0
+    assert chs.chs_probe_ops_per_thread(chs.PROBE_DSQRT, 1000) == 8000.0
+    # m8n8k4: 512 flops per MMA and warp, 8 MMAs per iteration, per lane
+    assert chs.chs_probe_ops_per_thread(chs.PROBE_DMMA, 1000) == 512 * 8 * 1000 / 32
+    assert chs.chs_probe_ops_per_thread(99, 1000) == 0.0

@@ -345,6 +345,40 @@ def test_fput_lyapunov_matches_oracle(N):
     assert np.abs(g.sum(axis=0) - r.sum(axis=0)).max() < 1e-9
 
 
+@pytest.mark.parametrize("N", [4, 8])
+def test_fput_alpha_beta_lyapunov_matches_oracle(N):
+    """The FPU chain with both nonlinearities (alpha = 0.25, beta = 1; Eq.
+    ham_FPU), QR every 7 steps, a last partial interval and a ragged block
+    (13 orbits): every exponent within 1e-8 of the oracle at t = 50."""
+    n = 13
+    Q, P = normal_mode_draws(300 + N, N, n)
+    ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))
+    prm = chs.params(0.05, 1003, qr_every=7, sample_every=50)
+    g, gs = _gpu_lyap(chs.FPUT, N, ics, prm, (1.0, 0.25, 1.0))
+    r, rs = O.lyapunov(O.fput(N, beta=1.0, alpha=0.25), O.params(0.05, 1003, qr_every=7, sample_every=50), ics)
+    np.testing.assert_array_equal(gs, rs)
+    assert np.abs(g - r).max() < 1e-8
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_fput_lyapunov_nonfinite_orbit(N):
+    """A NaN in one component of one orbit (a component of the third of the
+    orbit's lanes) makes that orbit NONFINITE with NaN exponents and leaves its
+    neighbours in the same warp untouched."""
+    n = 11
+    Q, P = normal_mode_draws(400 + N, N, n)
+    ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))
+    bad = ics.copy()
+    bad[N + N // 2, 5] = np.nan
+    prm = chs.params(0.05, 200, qr_every=10, sample_every=100)
+    g, gs = _gpu_lyap(chs.FPUT, N, bad, prm, (1.0, 0.0, 1.0))
+    r, rs = O.lyapunov(O.fput(N), O.params(0.05, 200, qr_every=10, sample_every=100), bad)
+    np.testing.assert_array_equal(gs, rs)
+    assert gs[5] == chs.ORBIT_NONFINITE and np.all(np.isnan(g[:, 5]))
+    keep = np.arange(n) != 5
+    assert np.abs(g[:, keep] - r[:, keep]).max() < 1e-8
+
+
 # --------------------------------------------------------------------------
 # full-size workload (1024 x 1024 grid at E = 1/6, k = 4), sampled
 # --------------------------------------------------------------------------
