@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libchs.so")
 CHS_OK, CHS_E_INVALID, CHS_E_UNSUPPORTED, CHS_E_CUDA, CHS_E_NOMEM, CHS_E_SIZE = range(6)
 HENON_HEILES, FPUT, QUARTIC3, HARMONIC, INVERTED = 1, 2, 3, 100, 101
 (ORBIT_OK, ORBIT_FORBIDDEN, ORBIT_ESCAPED, ORBIT_NONFINITE, ORBIT_ENERGY_DRIFT,
- ORBIT_EARLY_CHAOTIC, ORBIT_PREDICTED_REGULAR, ORBIT_STEP_FAIL) = range(8)
+ ORBIT_EARLY_CHAOTIC, ORBIT_PREDICTED_REGULAR, ORBIT_STEP_FAIL, ORBIT_STEP_BUDGET) = range(9)
 VEC_FP64, VEC_FP32 = 0, 1
 RK4, DOP853 = 0, 2
 
@@ -31,7 +31,8 @@ EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_sec
            "chs_indicators",
            "chs_lyapunov_spectrum", "chs_lyapunov_batch", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
            "chs_mlp_loss_grad", "chs_mlp_backward", "chs_mlp_adam", "chs_surrogate_decide",
-           "chs_peak_probe", "chs_probe_ops_per_thread", "chs_last_error", "chs_version")
+           "chs_peak_probe", "chs_probe_ops_per_thread", "chs_check_params", "chs_last_error",
+           "chs_version")
 PROBE_DFMA, PROBE_DFMA_DEP, PROBE_FFMA, PROBE_DSQRT, PROBE_DMMA = 1, 2, 3, 4, 5
 
 
@@ -47,7 +48,7 @@ class Params(C.Structure):
                 ("qr_every", C.c_int32), ("vec_precision", C.c_int32), ("early_exit", C.c_int32),
                 ("ld_p", C.c_double), ("escape_r2", C.c_double), ("dh_limit", C.c_double),
                 ("sali_threshold", C.c_double), ("seed", C.c_uint64), ("integrator", C.c_int32),
-                ("block_threads", C.c_int32)]
+                ("block_threads", C.c_int32), ("clock_budget", C.c_int64)]
 
 
 class Adaptive(C.Structure):
@@ -110,6 +111,7 @@ def load(path: str | None = None):
         "chs_mlp_backward": (C.c_int, [P, P, P, P, I64, P, P, P]),
         "chs_mlp_adam": (C.c_int, [P, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, I32, P, P]),
         "chs_surrogate_decide": (C.c_int, [P, P, I32, P, D, P, D, I64, P, P, P]),
+        "chs_check_params": (C.c_int, [C.POINTER(Params), C.c_int, I32]),
         "chs_peak_probe": (C.c_int, [I32, I32, I32, I64, P, P]),
         "chs_probe_ops_per_thread": (D, [I32, I64]),
         "chs_last_error": (C.c_char_p, []),
@@ -149,10 +151,10 @@ def params(dt: float, n_steps: int, *, step0: int = 0, n_dev: int = 0, renorm: b
            sample_every: int = 100, qr_every: int = 10, vec_precision: int = VEC_FP64,
            ld_p: float = 0.0, escape_r2: float = 0.0, dh_limit: float = 0.0,
            sali_threshold: float = 1e-8, seed: int = 1, early_exit: bool = False,
-           integrator: int = RK4, block_threads: int = 0) -> Params:
+           integrator: int = RK4, block_threads: int = 0, clock_budget: int = 0) -> Params:
     return Params(dt, n_steps, step0, n_dev, int(renorm), sample_every, qr_every, vec_precision,
                   int(early_exit), ld_p, escape_r2, dh_limit, sali_threshold, seed, integrator,
-                  block_threads)
+                  block_threads, clock_budget)
 
 
 # ----------------------------------------------------------------------------
@@ -286,6 +288,10 @@ def chs_surrogate_decide(params, series, n_samples, ld, t_decide, E, confidence,
                                        confidence, n, _ptr(status), _ptr(prob), _stream(stream)))
 
 
+def chs_check_params(prm: Params, model: int, n_dof: int):
+    _check(load().chs_check_params(C.byref(prm), model, n_dof))
+
+
 def chs_peak_probe(kind: int, n_blocks: int, n_threads: int, n_iter: int, sink, stream=None):
     _check(load().chs_peak_probe(kind, n_blocks, n_threads, n_iter, _ptr(sink), _stream(stream)))
 
@@ -331,20 +337,6 @@ def vector_rows(k: int, d: int, vec_fp32: bool) -> int:
     if k <= 0:
         return 1
     return k * d + (k * (k + 1) // 2 if vec_fp32 else 0)
-
-
-def frame_to_vectors(w, k: int, d: int):
-    """Unit vectors w_j / |w_j| = sum_i R_ij q_i from an FP32-mode vector buffer
-    (host-side inspection helper; works on numpy arrays [rows, n])."""
-    import numpy as np
-    w = np.asarray(w, dtype=np.float64)
-    n = w.shape[1]
-    Q = w[: k * d].reshape(k, d, n)
-    out = np.zeros((k, d, n))
-    for j in range(k):
-        for i in range(j + 1):
-            out[j] += w[k * d + j * (j + 1) // 2 + i] * Q[i]
-    return out.reshape(k * d, n)
 
 
 @dataclass

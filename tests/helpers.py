@@ -13,6 +13,20 @@ IND_TOL = 1e-8
 LABEL_AGREE = 0.995
 
 
+def frame_to_vectors(w, k: int, d: int) -> np.ndarray:
+    """Unit vectors w_j / |w_j| = sum_i R_ij q_i from an FP32-mode vector buffer
+    (rows: the k frame vectors q_i of length d, then the unit-column upper
+    triangle R by columns), as numpy [k*d, n]."""
+    w = np.asarray(w, dtype=np.float64)
+    n = w.shape[1]
+    Q = w[: k * d].reshape(k, d, n)
+    out = np.zeros((k, d, n))
+    for j in range(k):
+        for i in range(j + 1):
+            out[j] += w[k * d + j * (j + 1) // 2 + i] * Q[i]
+    return out.reshape(k * d, n)
+
+
 def state_rel_err(g: np.ndarray, r: np.ndarray) -> np.ndarray:
     """Per-orbit max |g - r| / max |r| over components ([c, o] arrays)."""
     scale = np.maximum(np.abs(r).max(axis=0), 1e-300)
@@ -59,7 +73,7 @@ def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=Tr
             sample_every=100, escape_r2=0.0, dh_limit=0.0, seed=1, w_in=None,
             sali_threshold=1e-8, chunks=None, grid=None, vec_fp32=False, sys_params=(),
             early_exit=False, t_end=None, compact_chunk=None, integrator=0, persistent=False,
-            block_threads=0):
+            block_threads=0, clock_budget=0):
     import torch
 
     from paper_2507_00622_gb300 import chs
@@ -70,7 +84,8 @@ def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=Tr
     vp = chs.VEC_FP32 if vec_fp32 else chs.VEC_FP64
     kw = dict(n_dev=k, ld_p=ld_p, renorm=renorm, sample_every=sample_every, escape_r2=escape_r2,
               dh_limit=dh_limit, sali_threshold=sali_threshold, seed=seed, vec_precision=vp,
-              early_exit=early_exit, integrator=integrator, block_threads=block_threads)
+              early_exit=early_exit, integrator=integrator, block_threads=block_threads,
+              clock_budget=clock_budget)
     ics_t = torch.from_numpy(np.ascontiguousarray(ics)).cuda()
     st_t = None if ic_status is None else torch.from_numpy(
         np.ascontiguousarray(ic_status, dtype=np.int32)).cuda()
@@ -108,7 +123,7 @@ def gpu_run(model, n_dof, ics, ic_status, *, dt, n_steps, k, ld_p=0.5, renorm=Tr
             out.update(dl=ldi[0].cpu().numpy(), sl=ldi[1].cpu().numpy())
     torch.cuda.synchronize()
     if vec_fp32 and k > 0:
-        w_out = chs.frame_to_vectors(ens.w.double().cpu().numpy(), k, S.d)
+        w_out = frame_to_vectors(ens.w.double().cpu().numpy(), k, S.d)
     else:
         w_out = ens.w[: k * S.d].double().cpu().numpy()
     out.update(x=ens.x.cpu().numpy(), w=w_out,

@@ -397,6 +397,12 @@ def test_full_size_grid_sampled_against_oracle():
     # vectors are taken from the GPU's seeding, which is bit-exact with the oracle's
     w_full = O.seed_vectors(2, ny * npy, 4, 4)
     r = oracle_run(HH, 2, ics[:, idx], st[idx], w_in=w_full[:, idx], **kw)
+    # the sampled cells integrated alone (their seeded vectors given) are bit for
+    # bit what they are inside the full-size launch: each thread integrates its
+    # own orbit, so sampled runs at longer horizons stand for the full grid
+    alone = gpu_run(HH, 2, ics[:, idx], st[idx], w_in=w_full[:, idx], **kw)
+    for key in ("x", "w", "ld", "dh_max", "n_exec", "status", "sali", "gali", "label"):
+        np.testing.assert_array_equal(alone[key], g[key][..., idx])
     np.testing.assert_array_equal(g["status"][idx], r["status"])
     ok = r["status"] == 0
     assert state_rel_err(g["x"][:, idx][:, ok], r["x"][:, ok]).max() < STATE_RTOL
@@ -554,6 +560,7 @@ def test_quartic_bench_size_sampled_against_oracle():
     abi = ens.abi(with_ld=False, t_end=te)
     prm = chs.params(0.01, 1000, n_dev=6, seed=3, vec_precision=chs.VEC_FP32, early_exit=True)
     chs.chs_ensemble_init(S.h, prm, abi, ics)
+    w0 = ens.w.clone()  # the set-up's FP32 frames, to restart the sample from
     work = chs.compact_work(n)
     chs.chs_integrate_compacted(S.h, prm, abi, 500, work)
     gali = torch.empty((5, n), dtype=torch.float64, device="cuda")
@@ -561,6 +568,19 @@ def test_quartic_bench_size_sampled_against_oracle():
     torch.cuda.synchronize()
     w_full = O.seed_vectors(3, n, 6, 6)
     r = oracle_run(chs.QUARTIC3, 3, ics_h, None, w_in=w_full[:, idx], t_end=t_end[idx], **kw)
+    # the sample integrated alone, from the FP32 frame the full-size set-up built
+    # for it, equals its part of the full-size compacted run bit for bit
+    alone = chs.DeviceEnsemble.empty(idx.size, 6, 6, vec_fp32=True)
+    it = torch.from_numpy(idx).cuda()
+    te_s = te[it].contiguous()
+    abi_s = alone.abi(with_ld=False, t_end=te_s)
+    chs.chs_ensemble_init(S.h, prm, abi_s, ics[:, it].contiguous())
+    alone.w.copy_(w0[:, it])
+    chs.chs_integrate_compacted(S.h, prm, abi_s, 500, chs.compact_work(idx.size))
+    torch.cuda.synchronize()
+    for name in ("x", "w", "dh_max", "n_exec", "status"):
+        np.testing.assert_array_equal(getattr(alone, name).cpu().numpy(),
+                                      getattr(ens, name)[..., it].cpu().numpy())
     np.testing.assert_array_equal(ens.n_exec.cpu().numpy()[idx], r["n_exec"])
     assert state_rel_err(ens.x.cpu().numpy()[:, idx], r["x"]).max() < STATE_RTOL
     g = gali.cpu().numpy()[:, idx]
