@@ -75,8 +75,10 @@ enum {
                                     confidence; frozen, labelled chaotic */
     CHS_ORBIT_PREDICTED_REGULAR = 6, /* the surrogate predicted "regular" with confidence;
                                         frozen, labelled regular */
-    CHS_ORBIT_STEP_FAIL = 7     /* adaptive DOP 8(5): the step size fell below 10 ulp(t)
+    CHS_ORBIT_STEP_FAIL = 7,    /* adaptive DOP 8(5): the step size fell below 10 ulp(t)
                                    after a rejection; frozen at the last accepted step */
+    CHS_ORBIT_STEP_BUDGET = 8   /* the call's clock budget (chs_params.clock_budget) ran
+                                   out at a health check; frozen there */
 };
 
 /* Integrators (chs_params.integrator).
@@ -115,7 +117,26 @@ typedef struct {
     int32_t block_threads;   /* threads per block where a kernel offers the choice: 0 (the
                                 library's default), 32, 64 or 128; results never depend on
                                 it (see chs_integrate_batch, chs_lyapunov_spectrum) */
+    int64_t clock_budget;    /* 0: none.  Otherwise the SM clock cycles (the device's clock64
+                                counter) an orbit may run within one kernel launch, counted
+                                from when its thread takes it up (chs_integrate_compacted
+                                launches once per chunk: there the budget applies to each
+                                chunk): at the first health check past the budget the orbit
+                                freezes as CHS_ORBIT_STEP_BUDGET with the state, n_exec and
+                                dh_max of that step (Lyapunov runs: NaN exponents).  Orbits
+                                integrated by the same warp or block (FPUT chains) stop
+                                together.  Needs sample_every > 0 to take effect; the
+                                kernels never wait or trap on it.  Not a method step: a
+                                bound on the time one call can take. */
 } chs_params;
+
+/* Checks a parameter block for a system of the given model and n_dof the way
+ * every entry point does before it launches anything (the ensemble entry points
+ * add their own checks of the ensemble and of the kernels they support):
+ * CHS_OK, or CHS_E_INVALID with chs_last_error() naming the field.  Needs no
+ * device and no handle, so a configuration can be validated up front.
+ * Interface helper; no paper counterpart. */
+chs_status chs_check_params(const chs_params* p, chs_model model, int32_t n_dof);
 
 /* Resumable ensemble state: caller-owned device arrays over n_orbits orbits.
  *   x       [d][n]    phase-space state (FP64)
@@ -311,8 +332,8 @@ chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_
                                    int32_t chunk_steps, void* work, size_t work_bytes,
                                    void* stream);
 
-/* The run of chs_integrate_compacted (same results; the fixed-step solvers of
- * Sec. Functionalities), for callers that cannot
+/* The run of chs_integrate_compacted, with the same results and the same
+ * argument checks (at most 100000 chunks), for callers that cannot
  * provide a scratch buffer: callers whose device memory belongs to another
  * allocator (a framework's caching allocator, a fixed arena sized at start-up)
  * that does not hand out extra buffers, or whose rules forbid device
@@ -324,6 +345,9 @@ chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_
  * orbits (the 1024 x 1024 grid); larger ensembles return CHS_E_SIZE.  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
+ * The address is cached per device and looked up again when the calling
+ * thread's current context differs from the one it was taken in (after a
+ * cudaDeviceReset, or from another context on the device).
  * Every call shares the one array per device: calls that overlap on the GPU
  * (different streams, or different handles on the same device) race; the
  * counters are cleared by each call, the lists are overwritten. */

@@ -114,6 +114,7 @@ chs_status check_params(const chs_params* p, const chs::SysPar& sp)
         return fail(CHS_E_UNSUPPORTED, "DOP853 runs with FP64 deviation vectors only");
     if (p->block_threads != 0 && p->block_threads != 32 && p->block_threads != 64 && p->block_threads != 128)
         return fail(CHS_E_INVALID, "block_threads must be 0, 32, 64 or 128");
+    if (p->clock_budget < 0) return fail(CHS_E_INVALID, "clock_budget must be >= 0 (0 = no limit)");
     return ok();
 }
 
@@ -146,6 +147,7 @@ chs::StepArgs step_args(const chs_params* p)
     a.early_exit = p->early_exit;
     a.sali_threshold = p->sali_threshold;
     a.block = p->block_threads;
+    a.clock_budget = p->clock_budget;
     return a;
 }
 
@@ -199,6 +201,13 @@ extern "C" {
 const char* chs_version(void) { return "chs 0.3.0 (sm_103a)"; }
 
 const char* chs_last_error(void) { return g_err.c_str(); }
+
+chs_status chs_check_params(const chs_params* p, chs_model model, int32_t n_dof)
+{
+    if (n_dof < 1) return fail(CHS_E_INVALID, "n_dof must be >= 1");
+    const chs::SysPar sp{(int)model, n_dof, 1.0, 0.0, 1.0, 0.1};
+    return check_params(p, sp);
+}
 
 chs_status chs_create_system(chs_system* out, chs_model model, int32_t n_dof, const double* params,
                              int32_t n_params)
@@ -602,6 +611,7 @@ static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const
         return fail(CHS_E_INVALID, "integrator must be CHS_RK4 or CHS_DOP853");
     if (p->block_threads != 0 && p->block_threads != 32 && p->block_threads != 64 && p->block_threads != 128)
         return fail(CHS_E_INVALID, "block_threads must be 0, 32, 64 or 128");
+    if (p->clock_budget < 0) return fail(CHS_E_INVALID, "clock_budget must be >= 0 (0 = no limit)");
     if (s->sp.model == CHS_FPUT && p->block_threads != 0 && p->block_threads < 2 * s->sp.n_dof)
         return fail(CHS_E_INVALID, "FPUT: block_threads must be 0 or at least 2N");
     if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");

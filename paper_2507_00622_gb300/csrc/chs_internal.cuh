@@ -66,7 +66,15 @@ struct StepArgs {
     int32_t early_exit;    // freeze as EARLY_CHAOTIC once SALI < sali_threshold
     double sali_threshold;
     int32_t block;         // threads per block requested (0: the kernel's default)
+    int64_t clock_budget;  // SM clock cycles an orbit may run in this call (0: no limit)
 };
+
+// True once more than a.clock_budget cycles of the SM clock have passed since
+// t_start (a clock64 reading on the same SM); never with a zero budget.
+__device__ __forceinline__ bool budget_spent(const StepArgs& a, long long t_start)
+{
+    return a.clock_budget > 0 && clock64() - t_start > a.clock_budget;
+}
 
 // Threads per block of the one-orbit-per-thread RK4 kernels, and the slot of
 // that size in per-size launch caches.

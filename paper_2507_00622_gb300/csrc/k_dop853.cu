@@ -36,6 +36,7 @@ k_lyap_small_dp(const StepArgs a, const SysPar sp, const int64_t n, const double
     }
     if (st == CHS_ORBIT_OK && !fin) st = CHS_ORBIT_NONFINITE;
     if (st == CHS_ORBIT_OK) {
+        const long long t_start = clock64();
         int64_t until_qr = a.qr_every;
         int64_t until = a.sample_every > 0 ? a.sample_every : -1;
         for (int64_t s = 1; s <= a.n_steps; ++s) {
@@ -74,6 +75,10 @@ k_lyap_small_dp(const StepArgs a, const SysPar sp, const int64_t n, const double
                 for (int c = 0; c < D; ++c) f2 = f2 && isfinite(x[c]) && isfinite(S[c]);
                 if (!f2) {
                     st = CHS_ORBIT_NONFINITE;
+                    break;
+                }
+                if (budget_spent(a, t_start)) {
+                    st = CHS_ORBIT_STEP_BUDGET;
                     break;
                 }
             }

@@ -43,6 +43,7 @@ k_integrate_adaptive(const StepArgs a, const AdaptArgs ad, const SysPar sp, cons
 
     int32_t st = CHS_ORBIT_OK;
     int64_t done = 0;
+    const long long t_start = clock64();
     while (done < a.n_steps && tt < ad.t_final) {
         const double min_step = 10.0 * (nextafter(tt, inf) - tt);
         if (ad.h_max > 0.0 && h > ad.h_max) h = ad.h_max;
@@ -88,6 +89,7 @@ k_integrate_adaptive(const StepArgs a, const AdaptArgs ad, const SysPar sp, cons
         ++done;
         const bool check = a.sample_every > 0 && (exec0 + done) % a.sample_every == 0;
         st = dp::post_step<Sys, K>(x, w, L, a, sp, check, h0, dhm);
+        if (check && st == CHS_ORBIT_OK && budget_spent(a, t_start)) st = CHS_ORBIT_STEP_BUDGET;
         if (st != CHS_ORBIT_OK) break;
     }
 
@@ -135,6 +137,7 @@ k_lyap_small_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const 
     }
     double tt = 0.0, h = a.dt;
     int64_t done = 0, rej = 0;
+    const long long t_start = clock64();
     // a non-finite initial state is never accepted: it ends as STEP_FAIL
     while (st == CHS_ORBIT_OK && tt < ad.t_final) {
         if (done >= a.n_steps) {
@@ -178,6 +181,10 @@ k_lyap_small_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const 
         for (int c = 0; c < D; ++c) x[c] = xn[c];
         tt = tn;
         ++done;
+        if (a.sample_every > 0 && done % a.sample_every == 0 && budget_spent(a, t_start)) {
+            st = CHS_ORBIT_STEP_BUDGET;
+            break;
+        }
         if ((a.qr_every > 0 && done % a.qr_every == 0) || tt >= ad.t_final) {
             // modified Gram-Schmidt, R_jj > 0: S_j += ln R_jj, W <- Q
 #pragma unroll

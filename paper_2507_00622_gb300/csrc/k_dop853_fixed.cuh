@@ -18,6 +18,7 @@ struct DpRun {
     double x[D], w[KK][D];
     double L, h0, dhm;
     int64_t exec0, todo, s, until;
+    long long t_start;  // clock64 when the orbit was taken up (clock budget)
     int32_t st;
 
     __device__ __forceinline__ void load(const int64_t o, const StepArgs& a, const EnsPtrs& e,
@@ -40,6 +41,7 @@ struct DpRun {
         st = CHS_ORBIT_OK;
         until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
         s = 0;
+        t_start = clock64();
     }
 
     // One step and its checks; false once the orbit froze (st says why).
@@ -59,6 +61,7 @@ struct DpRun {
             check = true;
         }
         st = dp::post_step<Sys, K>(x, w, L, a, sp, check, h0, dhm);
+        if (check && st == CHS_ORBIT_OK && budget_spent(a, t_start)) st = CHS_ORBIT_STEP_BUDGET;
         return st == CHS_ORBIT_OK;
     }
 

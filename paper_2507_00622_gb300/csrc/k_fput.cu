@@ -271,6 +271,7 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
     const double h = a.dt;
     int64_t until_qr = a.qr_every;
     int64_t until = a.sample_every > 0 ? a.sample_every : -1;
+    const long long t_start = clock64();
     for (int64_t s = 1; s <= a.n_steps; ++s) {
         // RK4 of the orbit; stage stiffnesses V''(D_b) recorded for Phi
         double acc = 0.0;
@@ -343,6 +344,11 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
             until = a.sample_every;
             if (orbit_any(!(isfinite(xi) && isfinite(S))) && st == CHS_ORBIT_OK)
                 st = CHS_ORBIT_NONFINITE;
+            // block-uniform: the block's orbits stop together
+            if (a.clock_budget > 0 && __syncthreads_or(budget_spent(a, t_start))) {
+                if (st == CHS_ORBIT_OK) st = CHS_ORBIT_STEP_BUDGET;
+                break;
+            }
         }
     }
     if (valid) {

@@ -212,6 +212,7 @@ k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double*
     const double h = a.dt;
     int64_t until_qr = a.qr_every;
     int64_t until = a.sample_every > 0 ? a.sample_every : -1;
+    const long long t_start = clock64();
     for (int64_t step = 1; step <= a.n_steps; ++step) {
         double e5, e3;
         xi = fs::orbit_stages<N, fs::TabDop853, false>(xi, h, l, slab + Sl::XB, slab + Sl::CS, fc, e5, e3);
@@ -225,6 +226,11 @@ k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double*
         if (--until == 0) {
             until = a.sample_every;
             if (orbit_any(!(isfinite(xi) && isfinite(S))) && st == CHS_ORBIT_OK) st = CHS_ORBIT_NONFINITE;
+            // block-uniform: the block's orbits stop together
+            if (a.clock_budget > 0 && __syncthreads_or(budget_spent(a, t_start))) {
+                if (st == CHS_ORBIT_OK) st = CHS_ORBIT_STEP_BUDGET;
+                break;
+            }
         }
     }
     if (valid) {
@@ -268,6 +274,8 @@ k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const i
     int64_t done = 0, rej = 0;
     bool rejected = false;
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    const long long t_start = clock64();
+    int64_t iter = 0;
     __syncthreads();
 
     // Every iteration is one trial of every active orbit.  An orbit's trials end
@@ -339,6 +347,10 @@ k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const i
         __syncthreads();  // W complete; stage stiffnesses free
         const bool want_qr = accept && ((a.qr_every > 0 && done % a.qr_every == 0) || tt >= ad.t_final);
         if (__syncthreads_or(want_qr)) qr_step<N>(slab, l, want_qr, S);
+        // clock budget every sample_every trials, block-uniform
+        if (a.clock_budget > 0 && a.sample_every > 0 && ++iter % a.sample_every == 0 &&
+            __syncthreads_or(budget_spent(a, t_start)) && st == CHS_ORBIT_OK && tt < ad.t_final)
+            st = CHS_ORBIT_STEP_BUDGET;
     }
     // non-finite exponent sums give NONFINITE for the whole orbit
     const bool bad = valid && st == CHS_ORBIT_OK && !isfinite(S);

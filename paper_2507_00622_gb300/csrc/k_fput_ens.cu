@@ -113,6 +113,7 @@ k_fput_ens(const StepArgs a, const SysPar sp, const int K, const EnsPtrs e)
     double dhm = runs ? e.dh_max[o] : 0.0;
     int64_t done = 0;
     bool active = runs && todo > 0;
+    const long long t_start = clock64();
 
     for (int64_t it = 1;; ++it) {
         if (!__syncthreads_or(active)) break;
@@ -131,6 +132,10 @@ k_fput_ens(const StepArgs a, const SysPar sp, const int K, const EnsPtrs e)
         }
         const bool check = a.sample_every > 0 && (a.step0 + it) % a.sample_every == 0;
         st = fe::post_step<N, Tab>(a, sp, K, slab, l, xi, stepped, check, check, h0, dhm, st);
+        if (check && a.clock_budget > 0) {  // block-uniform: the block's orbits stop together
+            const bool over = __syncthreads_or(budget_spent(a, t_start)) != 0;
+            if (over && stepped && st == CHS_ORBIT_OK) st = CHS_ORBIT_STEP_BUDGET;
+        }
         active = stepped && st == CHS_ORBIT_OK && done < todo;
     }
     if (runs) {

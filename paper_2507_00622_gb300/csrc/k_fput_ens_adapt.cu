@@ -48,6 +48,7 @@ k_fput_ens_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const in
     int64_t rej = (runs && ap.n_rej) ? ap.n_rej[o] : 0;
     int64_t done = 0;
     bool rejected = false;  // the current step has had a rejected trial
+    const long long t_start = clock64();
 
     // One iteration = one trial of every orbit that is still running.  Each
     // rejection shrinks the step by at least 0.9 until it drops below
@@ -117,6 +118,10 @@ k_fput_ens_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const in
         const bool check = accept && a.sample_every > 0 && (exec0 + done) % a.sample_every == 0;
         const bool any_check = __syncthreads_or(check);
         st = fe::post_step<N, Tab>(a, sp, K, slab, l, xi, accept, check, any_check, h0, dhm, st);
+        if (any_check && a.clock_budget > 0) {  // block-uniform: the block's orbits stop together
+            const bool over = __syncthreads_or(budget_spent(a, t_start)) != 0;
+            if (over && check && st == CHS_ORBIT_OK) st = CHS_ORBIT_STEP_BUDGET;
+        }
     }
     if (runs) {
         e.x[(int64_t)l * n + o] = xi;

@@ -161,6 +161,7 @@ k_fput_lyap_lanes(const StepArgs a, const SysPar sp, const int64_t n, const doub
     const double h = a.dt;
     int64_t until_qr = a.qr_every;
     int64_t until = a.sample_every > 0 ? a.sample_every : -1;
+    const long long t_start = clock64();
     for (int64_t s = 1; s <= a.n_steps; ++s) {
         // RK4 of the orbit; cw[k][u] = stiffness of bond i0 - 1 + u at stage k
         double qs[M], ps[M], aq[M], ap[M], cw[4][M + 3];
@@ -337,6 +338,11 @@ k_fput_lyap_lanes(const StepArgs a, const SysPar sp, const int64_t n, const doub
 #pragma unroll
             for (int m = 0; m < CPL; ++m) b = b || !isfinite(S[m]);
             if (orbit_any(b) && st == CHS_ORBIT_OK) st = CHS_ORBIT_NONFINITE;
+            // warp-uniform: the warp's orbits stop together
+            if (a.clock_budget > 0 && __any_sync(kFull, budget_spent(a, t_start))) {
+                if (st == CHS_ORBIT_OK) st = CHS_ORBIT_STEP_BUDGET;
+                break;
+            }
         }
     }
 #undef WAT

@@ -165,6 +165,7 @@ struct FrameRun {
     float Q[K][D], R[NR];
     double L, h0, dhm;
     int64_t exec0, todo, s, until;
+    long long t_start;  // clock64 when the orbit was taken up (clock budget)
     int32_t st;
 
     __device__ __forceinline__ void load(const int64_t o, const StepArgs& a, const EnsPtrs& e)
@@ -188,6 +189,7 @@ struct FrameRun {
         st = CHS_ORBIT_OK;
         until = a.sample_every > 0 ? a.sample_every - (a.step0 % a.sample_every) : -1;
         s = 0;
+        t_start = clock64();
     }
 
     // One step and its checks; false once the orbit froze (st says why).
@@ -274,6 +276,10 @@ struct FrameRun {
                     st = CHS_ORBIT_EARLY_CHAOTIC;
                     return false;
                 }
+            }
+            if (budget_spent(a, t_start)) {
+                st = CHS_ORBIT_STEP_BUDGET;
+                return false;
             }
         }
         return true;

@@ -259,12 +259,14 @@ struct OrbitRun {
     double w[KK][D];
     double L, h0, dhm;
     int64_t exec0, todo, s, until;
+    long long t_start;  // clock64 when the orbit was taken up (clock budget)
     int32_t st;
 
     __device__ __forceinline__ void load(const int64_t o, const StepArgs& a, const EnsPtrs& e)
     {
         const int64_t n = e.n;
         const double* wg = static_cast<const double*>(e.w);
+        t_start = clock64();
 #pragma unroll
         for (int c = 0; c < D; ++c) x[c] = e.x[c * n + o];
 #pragma unroll
@@ -331,6 +333,10 @@ struct OrbitRun {
                     st = CHS_ORBIT_EARLY_CHAOTIC;
                     return false;
                 }
+            }
+            if (budget_spent(a, t_start)) {
+                st = CHS_ORBIT_STEP_BUDGET;
+                return false;
             }
         }
         return true;
@@ -521,6 +527,7 @@ k_lyap_small(const StepArgs a, const SysPar sp, const int64_t n, const double* _
     }
     if (st == CHS_ORBIT_OK && !fin) st = CHS_ORBIT_NONFINITE;
     if (st == CHS_ORBIT_OK) {
+        const long long t_start = clock64();
         double L = 0.0;
         int64_t until_qr = a.qr_every;
         int64_t until = a.sample_every > 0 ? a.sample_every : -1;
@@ -554,6 +561,10 @@ k_lyap_small(const StepArgs a, const SysPar sp, const int64_t n, const double* _
                 for (int c = 0; c < D; ++c) f2 = f2 && isfinite(x[c]) && isfinite(S[c]);
                 if (!f2) {
                     st = CHS_ORBIT_NONFINITE;
+                    break;
+                }
+                if (budget_spent(a, t_start)) {
+                    st = CHS_ORBIT_STEP_BUDGET;
                     break;
                 }
             }

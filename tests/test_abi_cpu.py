@@ -82,7 +82,7 @@ def test_struct_layouts_match_header(lib, tmp_path):
         for f, _ in py._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
     assert int(got["chs_lyap_job"]) == C.sizeof(chs.LyapJob)
-    assert C.sizeof(chs.Params) == 96 and C.sizeof(chs.Ensemble) == 72
+    assert C.sizeof(chs.Params) == 104 and C.sizeof(chs.Ensemble) == 72
 
 
 def test_binding_refuses_host_tensors(lib):
@@ -108,3 +108,36 @@ def test_peak_probe_validates_before_cuda(lib):
     # m8n8k4: 512 flops per MMA and warp, 8 MMAs per iteration, per lane
     assert chs.chs_probe_ops_per_thread(chs.PROBE_DMMA, 1000) == 512 * 8 * 1000 / 32
     assert chs.chs_probe_ops_per_thread(99, 1000) == 0.0
+
+
+def test_params_checks_need_no_device(lib):
+    """chs_check_params validates a parameter block without a handle or a GPU:
+    the clock budget must be >= 0 (0 = none), and the other fields as every
+    entry point checks them."""
+    from paper_2507_00622_gb300 import chs
+    ok = chs.params(0.01, 100, n_dev=2, clock_budget=0)
+    chs.chs_check_params(ok, chs.HENON_HEILES, 2)
+    chs.chs_check_params(chs.params(0.01, 100, n_dev=2, clock_budget=1 << 40), chs.HENON_HEILES, 2)
+    bad = chs.params(0.01, 100, n_dev=2, clock_budget=-1)
+    with pytest.raises(chs.ChsError) as e:
+        chs.chs_check_params(bad, chs.HENON_HEILES, 2)
+    assert e.value.code == chs.CHS_E_INVALID and "clock_budget" in str(e.value)
+    for prm, word in ((chs.params(0.0, 100), "dt"), (chs.params(0.01, -1), "n_steps"),
+                      (chs.params(0.01, 10, n_dev=5), "n_dev"),
+                      (chs.params(0.01, 10, block_threads=48), "block_threads")):
+        with pytest.raises(chs.ChsError) as e:
+            chs.chs_check_params(prm, chs.HENON_HEILES, 2)
+        assert word in str(e.value)
+    assert lib.chs_check_params(None, chs.HENON_HEILES, 2) == chs.CHS_E_INVALID
+
+
+def test_static_scratch_entry_point_names_no_allocation():
+    """The entry point for callers that cannot allocate device memory lives in
+    csrc/chs_static.cu; nothing in that file may allocate: no cudaMalloc family
+    call, no cudaFree, no graph instantiation."""
+    src = open(os.path.join(ROOT, "paper_2507_00622_gb300", "csrc", "chs_static.cu")).read()
+    code = re.sub(r"//[^\n]*", "", re.sub(r"/\*.*?\*/", "", src, flags=re.S))
+    for name in ("cudaMalloc", "cudaMallocAsync", "cudaMallocManaged", "cudaMallocHost", "cudaHostAlloc",
+                 "cudaFree", "cudaGraphInstantiate", "cudaStreamBeginCapture", "cuMemAlloc", "malloc(",
+                 "new "):
+        assert name not in code, name
