@@ -8,6 +8,7 @@
 // serves them: the lists live in a file-scope device array of fixed size, which
 // every GPU that loads this library holds until the process exits, and the call
 // allocates nothing.
+#include <cuda.h>  // CUcontext and CUresult (types only: the driver call comes from the runtime)
 #include <stdio.h>
 
 #include <mutex>
@@ -26,19 +27,48 @@ static __device__ __align__(256) int32_t g_compact_scratch[kStaticWords];
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 int32_t* g_scratch_ptr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};  // the context each cached address belongs to
+
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+
+// The calling thread's current context, by the driver's cuCtxGetCurrent obtained
+// through the runtime (no link against the driver library).  Call with
+// g_scratch_mutex held.
+cudaError_t current_context(CUcontext* ctx)
+{
+    static CtxGetCurrent fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !p) return cudaErrorSymbolNotFound;
+        fn = reinterpret_cast<CtxGetCurrent>(p);
+    }
+    return fn(ctx) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
 
 // Device address of the scratch array on `device` (which must be current).  The
 // host-side symbol is only a stand-in; its device address comes from
-// cudaGetSymbolAddress, once per device.
+// cudaGetSymbolAddress, once per device and context: a cudaDeviceReset, or a
+// call from another context on the device, loads the module again and the array
+// may move, so the address is looked up anew when the current context changes.
 cudaError_t scratch_for(int device, int32_t** out)
 {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[device]) {
+    CUcontext ctx = nullptr;
+    cudaError_t e = current_context(&ctx);
+    if (e != cudaSuccess) return e;
+    if (!g_scratch_ptr[device] || g_scratch_ctx[device] != ctx) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_compact_scratch);
+        e = cudaGetSymbolAddress(&p, g_compact_scratch);
         if (e != cudaSuccess) return e;
+        // the lookup may have created the primary context: key the cache on the
+        // context that is current now
+        if ((e = current_context(&ctx)) != cudaSuccess) return e;
         g_scratch_ptr[device] = static_cast<int32_t*>(p);
+        g_scratch_ctx[device] = ctx;
     }
     *out = g_scratch_ptr[device];
     return cudaSuccess;
@@ -67,6 +97,9 @@ extern "C" chs_status chs_integrate_compacted_static(chs_system s, const chs_par
     chs_status r = chs::api_validate_run(s, p, e, &device);
     if (r != CHS_OK) return r;
     if (chunk_steps < 1) return chs::api_fail(CHS_E_INVALID, "chunk_steps must be >= 1");
+    // the same bound on the chunk count as chs_integrate_compacted
+    if ((p->n_steps + chunk_steps - 1) / chunk_steps > 100000)
+        return chs::api_fail(CHS_E_SIZE, "more than 100000 chunks: raise chunk_steps");
     if (e->n_orbits > kStaticMaxOrbits) {
         snprintf(g_static_err, sizeof g_static_err,
                  "chs_integrate_compacted_static serves at most %lld orbits (got %lld): use "

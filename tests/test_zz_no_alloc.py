@@ -59,8 +59,14 @@ def test_static_scratch_run_matches_work_buffer_run():
     for n_steps in (20000, 20000):
         prm = chs.params(0.01, n_steps, step0=step, **kw)
         chs.chs_integrate_compacted(S.h, prm, ref_abi, 1000, work)
+        torch.cuda.synchronize()
+        # the call itself takes no memory from torch's allocator (nor from any
+        # other: the library side names no allocating call, tests/test_abi_cpu.py)
+        held = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
         chs.chs_integrate_compacted_static(S.h, prm, new_abi, 1000)
         torch.cuda.synchronize()
+        # (Python may free a tensor meanwhile: the counts may drop, never grow)
+        assert torch.cuda.memory_allocated() <= held[0] and torch.cuda.memory_reserved() <= held[1]
         step += n_steps
         a, b = _host(ref), _host(new)
         np.testing.assert_array_equal(a["status"], b["status"])
@@ -82,3 +88,13 @@ def test_static_scratch_rejects_oversized_ensembles():
                                                      C.byref(abi), 100, None)
     assert code == chs.CHS_E_SIZE
     assert "1048576" in chs.chs_last_error()
+
+
+def test_static_scratch_bounds_the_chunk_count():
+    """Like the work-buffer entry point, at most 100000 chunks per call."""
+    S = chs.System(chs.HENON_HEILES, 2)
+    ens = chs.DeviceEnsemble.empty(8, 4, 2)
+    code = chs.load().chs_integrate_compacted_static(S.h, C.byref(chs.params(0.01, 100001, n_dev=2)),
+                                                     C.byref(ens.abi()), 1, None)
+    assert code == chs.CHS_E_SIZE
+    assert "100000 chunks" in chs.chs_last_error()
