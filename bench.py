@@ -8,8 +8,15 @@ GALI_2..4, LD indicators and labels.  One bench step advances the whole grid by
 timed steps cover a window of the t = 1e4 integration) and then evaluates every
 indicator on the new state: each step runs every stage of the hot path.
 
-Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
-bounded sample of the same workload instead.
+Prints one JSON line (rank 0).  Beside the headline, the line carries the other
+configurations, each with its roofline and CPU baseline (skip with --no-extra):
+the same grid with FP32 deviation vectors (`fp32_vectors`), the FPUT-beta
+Lyapunov spectra for N = 4 .. 64 at QR every 10 steps and at the tuned interval
+(`fput_lyapunov_qr10`, `fput_lyapunov_qr_tuned`), the coupled quartic
+oscillators (`quartic`), and the time to classify the 1024 x 1024 grid at
+E = 1/8 by the plain and the fast forms (`classify`; --classify-side 0 skips it).
+`--impl reference` times the CPU oracle on a bounded sample of the same workload
+instead.
 """
 from __future__ import annotations
 
@@ -41,7 +48,7 @@ FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA lanes per SM per clock (measured 1.20 TFLOP/s
 # and writes the ensemble state once whatever its step count), valid while the
 # kernel sources hash to the recorded value.
 TRAFFIC_SOURCES = ("k_small.cu", "rk4_common.cuh", "fastmath.cuh", "systems.cuh", "chs_internal.cuh")
-TRAFFIC_RECORD = {"sha256_16": "7fef31476e308a37", "bytes_per_launch": 147.059200e6 + 79.636992e6,
+TRAFFIC_RECORD = {"sha256_16": "c182f5c4a97e3bd0", "bytes_per_launch": 146491904.0 + 78790912.0,
                   "n_side": 1024}
 
 
@@ -142,6 +149,92 @@ def measured_fp64_peak(sm_count: int) -> dict:
     clk = clocks.stop()
     return {"tflops": r["ops_per_s"] / 1e12, "sm_mhz": clk["sm_mhz"], "ms": r["ms"],
             "probe": f"DFMA, {sm_count * 4} x 256 threads x 8 chains x {r['n_iter']} iterations, best of 5"}
+
+
+def measured_fp32_peak(sm_count: int) -> dict:
+    """The FP32 FMA peak measured by the FFMA probe (8 independent chains per
+    thread, 32 warps per SM), with the SM clock sampled while it ran."""
+    from paper_2507_00622_gb300 import chs
+
+    clocks = ClockSampler(None)
+    clocks.start()
+    r = probe_rate(chs.PROBE_FFMA, sm_count * 4, 256, 1 << 21)
+    clk = clocks.stop()
+    return {"tflops": r["ops_per_s"] / 1e12, "sm_mhz": clk["sm_mhz"],
+            "probe": f"FFMA, {sm_count * 4} x 256 threads x 8 chains x {r['n_iter']} iterations, best of 5"}
+
+
+def grid_fp32_result(steps: int, warmup: int, chunk: int, fp64_peak: dict, n_side: int = 1024) -> dict:
+    """The Henon-Heiles grid run with FP32 deviation vectors (the second run of
+    the E = 1/6 workload): the same grid, k = 4, LD, RK4 h = 0.01, `chunk` steps
+    per bench step plus the indicators; orbit-steps/s and the roofline fractions
+    of the integrate kernel on the FP64 pipe (orbit, energy, LD) and on the FP32
+    pipe (the vector frame) against the measured peaks."""
+    import torch
+
+    from paper_2507_00622_gb300 import chs
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    f32_peak = measured_fp32_peak(sms)
+    n = n_side * n_side
+    y0, y1, p0, p1 = grid_box(E_GRID)
+    S = chs.System(chs.HENON_HEILES, 2)
+    ics = torch.empty((4, n), dtype=torch.float64, device="cuda")
+    ic_st = torch.empty(n, dtype=torch.int32, device="cuda")
+    chs.chs_section_grid_ics(S.h, E_GRID, y0, y1, n_side, p0, p1, n_side, ics, ic_st)
+    kw = dict(n_dev=K_DEV, ld_p=0.5, escape_r2=4.0, sample_every=100, seed=1, vec_precision=chs.VEC_FP32)
+    ens = chs.DeviceEnsemble.empty(n, 4, K_DEV, True)
+    abi = ens.abi()
+    chs.chs_ensemble_init(S.h, chs.params(DT, 1, **kw), abi, ics, ic_st)
+    sali = torch.empty(n, dtype=torch.float64, device="cuda")
+    gali = torch.empty((K_DEV - 1, n), dtype=torch.float64, device="cuda")
+    label = torch.empty(n, dtype=torch.int8, device="cuda")
+    ldi = torch.empty((2, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    step = 0
+    kev = []
+
+    def one(timed):
+        nonlocal step
+        prm = chs.params(DT, chunk, step0=step, **kw)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(stream)
+        chs.chs_integrate_batch(S.h, prm, abi, stream)
+        ev[1].record(stream)
+        chs.chs_indicators(S.h, prm, abi, n_side, n_side, sali, gali, ldi, label, stream)
+        if timed:
+            kev.append(ev)
+        step += chunk
+
+    for _ in range(warmup):
+        one(False)
+    torch.cuda.synchronize()
+    e0 = int(ens.n_exec.sum())
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        one(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = t0.elapsed_time(t1)
+    kern_ms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+    done = int(ens.n_exec.sum()) - e0
+    f64, f32 = flops_per_orbit_step(K_DEV, True, True)
+    per_launch = done / steps
+    a64 = f64 * per_launch / (kern_ms / 1e3) / 1e12
+    a32 = f32 * per_launch / (kern_ms / 1e3) / 1e12
+    S.close()
+    return {"workload": f"henon_heiles_E1/6_grid{n_side}x{n_side}_k4_sali_gali2-4_ld_rk4_fp32vectors",
+            "value": done / (total_ms / 1e3), "unit": UNIT, "steps": steps, "warmup": warmup,
+            "steps_per_bench_step": chunk, "ms_per_step": total_ms / steps, "dtype": "f64 orbit + f32 frame",
+            "roofline": {"kernel": "k_integrate_f32<HenonHeiles,4,LD>", "kernel_ms_avg": kern_ms,
+                         "flops_per_orbit_step": {"fp64": f64, "fp32": f32},
+                         "fp64": {"achieved": a64, "peak": fp64_peak["tflops"], "frac": a64 / fp64_peak["tflops"],
+                                  "unit": "TFLOP/s"},
+                         "fp32": {"achieved": a32, "peak": f32_peak["tflops"], "frac": a32 / f32_peak["tflops"],
+                                  "unit": "TFLOP/s", "peak_basis": "measured: " + f32_peak["probe"]}},
+            "cpu_baseline_note": "the oracle integrates FP64 vectors only: the headline line's cpu_baseline "
+                                 "is this workload's CPU baseline too"}
 
 
 def shard_rows(ny: int, rank: int, world: int) -> tuple[int, int, int, int]:
@@ -354,6 +447,61 @@ def run_peaks(args):
                 "4_warps_per_sm": dep4["ms"] * 1e-3 * mhz * 1e6 / dep4["n_iter"]},
             "probes": full}
     print(json.dumps(line))
+    return 0
+
+
+def run_mlp(args):
+    """The surrogate's kernels on 1,048,576 orbits (the 1024 x 1024 grid): the
+    fused forward pass (chs_mlp_forward) and the decision (chs_surrogate_decide:
+    features, forward, status update), timed with CUDA events (best of 5 after a
+    warm-up), with their multiply-add rate against the measured FP32 FMA peak
+    (the perceptron runs on the FP32 pipe with BF16 operands)."""
+    import torch
+
+    from paper_2507_00622_gb300 import build as cuda_build
+    from paper_2507_00622_gb300 import chs
+    from paper_2507_00622_gb300 import surrogate as SG
+
+    cuda_build.build()
+    chs.load()
+    n = 1 << 20
+    rng = np.random.default_rng(11)
+    sur = SG.Surrogate.load()
+    X = torch.from_numpy(rng.standard_normal((12, n)).astype(np.float32)).cuda()
+    Y = torch.empty((2, n), dtype=torch.float32, device="cuda")
+    series = torch.from_numpy(10.0 ** rng.uniform(-12, 0, (10, n))).cuda()
+    ld = torch.from_numpy(rng.uniform(400.0, 700.0, n)).cuda()
+    E = torch.full((n,), 0.125, dtype=torch.float64, device="cuda")
+    status = torch.zeros(n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def best(fn):
+        fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            t.append(a.elapsed_time(b))
+        return min(t)
+
+    fwd_ms = best(lambda: chs.chs_mlp_forward(sur.params, X, n, Y))
+
+    def decide():
+        status.zero_()
+        chs.chs_surrogate_decide(sur.params, series, 10, ld, 500.0, E, 0.98, n, status)
+
+    dec_ms = best(decide)
+    macs = 12 * 128 + 128 * 128 + 128 * 128 + 128 * 2  # per orbit
+    f32 = measured_fp32_peak(torch.cuda.get_device_properties(0).multi_processor_count)
+    tf = 2.0 * macs * n / (fwd_ms / 1e3) / 1e12
+    print(json.dumps({"workload": "surrogate_mlp_12-128-128-128-2_bf16", "n_orbits": n,
+                      "forward_ms": fwd_ms, "decide_ms": dec_ms, "macs_per_orbit": macs,
+                      "forward_tflops": tf, "fp32_fma_peak_tflops": f32["tflops"],
+                      "frac_of_fp32_peak": tf / f32["tflops"]}))
     return 0
 
 
@@ -572,6 +720,19 @@ def run_gpu(args):
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_oracle_sample(args.chunk, args.cpu_budget,
                                                      integrator=args.integrator)
+        if world == 1 and not args.no_extra:
+            # the other configurations, each with its own roofline and CPU baseline
+            line["fp32_vectors"] = grid_fp32_result(3, 2, args.chunk, mp)
+            fa = argparse.Namespace(**vars(args))
+            fa.chunk, fa.steps, fa.warmup, fa.integrator, fa.block, fa.fput_batch = 200, 3, 2, "rk4", "0", False
+            fa.cpu_budget = min(args.cpu_budget, 6.0)
+            fa.qr_every = "10"
+            line["fput_lyapunov_qr10"] = fput_result(fa)
+            fa.qr_every = "auto"
+            line["fput_lyapunov_qr_tuned"] = fput_result(fa)
+            qa = argparse.Namespace(**vars(args))
+            qa.chunk, qa.steps, qa.warmup, qa.persistent = 1000, 3, 2, False
+            line["quartic"] = quartic_result(qa)
         if world == 1 and args.classify_side > 0:
             c = classify_result(args.classify_side, 1_000_000)
             line["classify"] = {
@@ -582,6 +743,7 @@ def run_gpu(args):
                 fs = c["fast_surrogate"]
                 line["classify"].update(surrogate_s=fs["seconds"], surrogate_speedup=fs["speedup"],
                                         surrogate_agreement=fs["agreement"],
+                                        surrogate_judge_sample=fs["judge_sample"],
                                         surrogate_judge_agreement=fs["judge_agreement"],
                                         surrogate_confidence=fs["confidence"])
         print(json.dumps(line))
@@ -613,14 +775,22 @@ def run_fput(args):
     """FPUT-beta Lyapunov spectra (k = 1, beta = 1, h = 0.05, QR every 10 steps):
     4096 normal-mode orbits at energy density 0.1 per chain length; one bench
     step integrates every chain length for --chunk steps."""
-    import torch
-
     from paper_2507_00622_gb300 import build as cuda_build
     from paper_2507_00622_gb300 import chs
-    from paper_2507_00622_gb300.inputs import normal_mode_draws
 
     cuda_build.build()
     chs.load()
+    print(json.dumps(fput_result(args)))
+    return 0
+
+
+def fput_result(args) -> dict:
+    """The FPUT Lyapunov line (see run_fput) as a dict."""
+    import torch
+
+    from paper_2507_00622_gb300 import chs
+    from paper_2507_00622_gb300.inputs import normal_mode_draws
+
     Ns = [int(v) for v in args.fput_n.split(",")]
     n = args.fput_orbits
     runs = []
@@ -693,23 +863,22 @@ def run_fput(args):
                          "frac_of_fp64_formula": tf / fp64_peak_tflops(2070.0), "qr_every": qr[N],
                          "block_threads": blk[N] or None}
     value = len(runs) * n * args.chunk * args.steps / (total_ms / 1e3)
-    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": "fput_beta_lyapunov_h0.05" + ("_dop853" if dop else ""),
-                                 "N": Ns, "integrator": "DOP853 (fixed step)" if dop else "RK4",
-                                 "orbits_per_N": n, "steps_per_bench_step": args.chunk,
-                                 "qr_every": args.qr_every,
-                                 "launch": "one CUDA graph, concurrent branches" if args.fput_batch
-                                           else "one launch per N"},
-                      "per_N": per_n,
-                      "fp64_peak": {"measured_tflops": mp["tflops"], "sm_mhz": mp["sm_mhz"],
-                                    "probe": mp["probe"], "formula_tflops": fp64_peak_tflops(2070.0)},
-                      **({} if args.no_cpu_baseline else
-                         {"cpu_baseline": cpu_fput_sample(Ns, args.chunk, qr, args.cpu_budget,
-                                                          args.integrator)})}))
-    return 0
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fput_beta_lyapunov_h0.05" + ("_dop853" if dop else ""),
+                       "N": Ns, "integrator": "DOP853 (fixed step)" if dop else "RK4",
+                       "orbits_per_N": n, "steps_per_bench_step": args.chunk,
+                       "qr_every": args.qr_every,
+                       "launch": "one CUDA graph, concurrent branches" if args.fput_batch
+                                 else "one launch per N"},
+            "per_N": per_n,
+            "fp64_peak": {"measured_tflops": mp["tflops"], "sm_mhz": mp["sm_mhz"],
+                          "probe": mp["probe"], "formula_tflops": fp64_peak_tflops(2070.0)},
+            **({} if args.no_cpu_baseline else
+               {"cpu_baseline": cpu_fput_sample(Ns, args.chunk, qr, args.cpu_budget,
+                                                args.integrator)})}
 
 
 def fput_ens_flops_per_step(N: int, k: int) -> int:
@@ -849,9 +1018,10 @@ def classify_result(n_side: int, final_steps: int, confidence=None) -> dict:
     """Time to classify a Henon-Heiles section grid (E = 1/8, final t = steps * 0.01)
     by the plain form (FP64 vectors, every orbit to the end) and by the fast form
     (FP32 vector frame, early exit, compacted CUDA-graph chunks, and the trained
-    surrogate when its weights are present), with the label agreement; a 2 %
-    random sample of the orbits the surrogate stopped is judged against the plain
-    labels as well."""
+    surrogate when its weights are present), with the label agreement.  The
+    surrogate form's time includes its judge: a 2 % random sample of the orbits
+    the surrogate stopped, re-integrated by the plain form to the final time
+    beside the rest of the fast form, whose labels give the surrogate's error."""
     from paper_2507_00622_gb300 import chs
     from paper_2507_00622_gb300 import classify as CL
     from paper_2507_00622_gb300 import surrogate as SG
@@ -873,17 +1043,23 @@ def classify_result(n_side: int, final_steps: int, confidence=None) -> dict:
             meta = _json.loads(str(z["meta"]))
         sur = SG.Surrogate.load()
         conf = float(confidence or meta.get("confidence", 0.999))
-        fs = CL.run_fast(g, surrogate=sur, confidence=conf)
-        stopped = np.where((fs.n_exec == SG.DECIDE_STEP) & ((fs.status == chs.ORBIT_PREDICTED_REGULAR) |
-                                                            (fs.status == chs.ORBIT_EARLY_CHAOTIC)))[0]
-        rng = np.random.default_rng(0)
-        judge = rng.choice(stopped, max(1, int(0.02 * stopped.size)), replace=False) if stopped.size else stopped
+        fs = CL.run_fast(g, surrogate=sur, confidence=conf, judge_fraction=0.02)
+        # the judge: a 2 % random sample of the orbits the surrogate stopped,
+        # re-integrated by the plain form to the final time on a second stream
+        # beside the rest of the fast form; its cost is inside the surrogate
+        # form's time
+        judge = fs.extra.get("judge_cells", np.zeros(0, dtype=np.int64))
+        jl = fs.extra.get("judge_label")
         out["fast_surrogate"] = {
             "seconds": fs.seconds, "orbit_steps": fs.orbit_steps, "confidence": conf,
             "speedup": plain.seconds / fs.seconds, "agreement": CL.agreement(plain, fs, plain.status),
-            "stopped_by_surrogate": int(stopped.size),
+            "stopped_by_surrogate": int(fs.extra["surrogate_stopped"]),
+            "judge": "plain FP64 re-integration to the final time of a random 2 % of the orbits "
+                     "the surrogate stopped, on a second stream from the decision on",
             "judge_sample": int(judge.size),
-            "judge_agreement": float(np.mean(fs.label[judge] == plain.label[judge])) if judge.size else None,
+            "judge_orbit_steps": int(fs.extra.get("judge_orbit_steps", 0)),
+            "judge_agreement": float(np.mean(fs.label[judge] == jl)) if judge.size else None,
+            "judge_vs_full_plain_run": float(np.mean(jl == plain.label[judge])) if judge.size else None,
             "training": meta}
     return out
 
@@ -904,13 +1080,21 @@ def run_quartic(args):
     per-orbit end times t_end ~ U[1e3, 1e4] with early exit, compacted CUDA-graph
     chunks.  One bench step advances every live orbit by --chunk steps and
     evaluates SALI and GALI_2..6."""
-    import torch
-
     from paper_2507_00622_gb300 import build as cuda_build
     from paper_2507_00622_gb300 import chs
 
     cuda_build.build()
     chs.load()
+    print(json.dumps(quartic_result(args)))
+    return 0
+
+
+def quartic_result(args) -> dict:
+    """The quartic line (see run_quartic) as a dict."""
+    import torch
+
+    from paper_2507_00622_gb300 import chs
+
     n = args.quartic_orbits
     rng = np.random.default_rng(5)
     dirs = torch.from_numpy(rng.standard_normal((6, n))).cuda()
@@ -955,19 +1139,18 @@ def run_quartic(args):
     ms = t0.elapsed_time(t1)
     done = int(ens.n_exec.sum()) - e0
     st = ens.status.cpu().numpy()
-    print(json.dumps({"metric": METRIC, "value": done / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                      "dtype": "f64 orbit + f32 frame", "data": "synthetic",
-                      "config": {"workload": "quartic3_eps0.1_shellE1-10_k6_fp32frame_gali2-6",
-                                 "n_orbits": n, "rk4_steps_per_bench_step": args.chunk,
-                                 "launch": "persistent work queue" if args.persistent
-                                           else "compacted 500-step chunks (CUDA graph)",
-                                 "t_window": [args.warmup * args.chunk * 0.01, step * 0.01],
-                                 "early_exited": int((st == chs.ORBIT_EARLY_CHAOTIC).sum())},
-                      **({} if args.no_cpu_baseline else
-                         {"cpu_baseline": cpu_quartic_sample(100, args.cpu_budget)})}))
-    return 0
+    return {"metric": METRIC, "value": done / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 orbit + f32 frame", "data": "synthetic",
+            "config": {"workload": "quartic3_eps0.1_shellE1-10_k6_fp32frame_gali2-6",
+                       "n_orbits": n, "rk4_steps_per_bench_step": args.chunk,
+                       "launch": "persistent work queue" if args.persistent
+                                 else "compacted 500-step chunks (CUDA graph)",
+                       "t_window": [args.warmup * args.chunk * 0.01, step * 0.01],
+                       "early_exited": int((st == chs.ORBIT_EARLY_CHAOTIC).sum())},
+            **({} if args.no_cpu_baseline else
+               {"cpu_baseline": cpu_quartic_sample(100, args.cpu_budget)})}
 
 
 def run_integrators(args):
@@ -1129,18 +1312,19 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="grid line only: skip the FP32-vector, FPUT and quartic keys")
     ap.add_argument("--ref-sample", type=int, default=4096)
     ap.add_argument("--workload", choices=["grid", "fput", "classify", "quartic", "integrators",
-                                           "saturation", "fput_gali", "peaks"], default="grid")
+                                           "saturation", "fput_gali", "peaks", "mlp"], default="grid")
     ap.add_argument("--quartic-orbits", type=int, default=4_194_304)
     ap.add_argument("--persistent", action="store_true",
                     help="quartic workload: one persistent work-queue launch per bench step")
     ap.add_argument("--final-steps", type=int, default=1_000_000)
     ap.add_argument("--confidence", type=float, default=None)
-    ap.add_argument("--classify-side", type=int, default=256,
+    ap.add_argument("--classify-side", type=int, default=1024,
                     help="grid side of the time-to-classified-grid measurement added to the "
-                         "throughput line (0 = skip); the full 1024 x 1024 measurement is "
-                         "--workload classify --n-side 1024")
+                         "throughput line (0 = skip)")
     ap.add_argument("--fput-n", default="4,8,16,32,64")
     ap.add_argument("--fput-orbits", type=int, default=4096)
     ap.add_argument("--qr-every", default="10", help="QR interval of the FPUT run, or 'auto' (autotuner)")
@@ -1168,6 +1352,8 @@ def main():
         return run_fput_gali(args)
     if args.workload == "peaks":
         return run_peaks(args)
+    if args.workload == "mlp":
+        return run_mlp(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -54,10 +54,13 @@ def grid_ics(energies, side: int):
 
 
 def run_sampled(ics, st, k: int = 2, seed: int = 1, final_step: int = FINAL_STEP, chunk: int = 2000,
-                surrogate=None, E=None, confidence: float = 0.999):
+                surrogate=None, E=None, confidence: float = 0.999, on_decision=None):
     """Fast-form run with SALI samples up to the decision step.  Returns a dict of
     device tensors: series [10][n], ld_dec, status_dec (at the decision step),
-    sali, label (final), n_exec, and the wall time."""
+    sali, label (final), n_exec, and the wall time (to the end of all device
+    work, whatever stream it runs on).  on_decision(status_dec, status), when
+    given, is called right after the surrogate's decision, before the run
+    continues; its return value comes back as "on_decision"."""
     S = chs.System(chs.HENON_HEILES, 2)
     n = ics.shape[1]
     kw = dict(n_dev=k, ld_p=0.5, escape_r2=4.0, seed=seed, sali_threshold=1e-8,
@@ -81,12 +84,13 @@ def run_sampled(ics, st, k: int = 2, seed: int = 1, final_step: int = FINAL_STEP
     status_dec = ens.status.clone()
     if surrogate is not None:
         surrogate.decide(series, ens.ld, ens.status, E, DT * DECIDE_STEP, confidence)
+    side = on_decision(status_dec, ens.status) if on_decision is not None else None
     chs.chs_integrate_compacted(S.h, chs.params(DT, final_step - step, step0=step, **kw), abi, chunk, work)
     chs.chs_indicators(S.h, chs.params(DT, 0, **kw), abi, sali=sali, label=label)
-    torch.cuda.synchronize()
+    torch.cuda.synchronize()  # the whole device: every stream's work is done
     sec = time.perf_counter() - t0
     return dict(series=series, ld_dec=ld_dec, status_dec=status_dec, sali=sali, label=label,
-                status=ens.status, n_exec=ens.n_exec, seconds=sec)
+                status=ens.status, n_exec=ens.n_exec, seconds=sec, on_decision=side)
 
 
 def make_dataset(run, E):
