@@ -11,6 +11,7 @@
 #include <utility>
 
 #include "chs_internal.cuh"
+#include "nvtx_range.cuh"
 #include "k_dop853.cuh"
 
 // Recorded chunk sequence of chs_integrate_compacted and the inputs it was
@@ -269,6 +270,7 @@ chs_status chs_section_grid_ics(chs_system s, double E, double y0, double y1, in
                                 double py1, int32_t npy, double* ics_out, int32_t* status_out,
                                 void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if (s->sp.model != CHS_HENON_HEILES) return fail(CHS_E_UNSUPPORTED, "section grid is for HENON_HEILES");
@@ -286,6 +288,7 @@ chs_status chs_section_grid_ics(chs_system s, double E, double y0, double y1, in
 chs_status chs_fput_mode_ics(chs_system s, int64_t n, const double* Qm, const double* Pm,
                              const double* E, double* ics_out, void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if (s->sp.model != CHS_FPUT) return fail(CHS_E_UNSUPPORTED, "normal-mode ICs are for FPUT");
@@ -300,6 +303,7 @@ chs_status chs_fput_mode_ics(chs_system s, int64_t n, const double* Qm, const do
 chs_status chs_shell_ics(chs_system s, int64_t n, const double* dirs, const double* E,
                          double* ics_out, void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if (s->sp.model != CHS_QUARTIC3) return fail(CHS_E_UNSUPPORTED, "shell ICs are for QUARTIC3");
@@ -314,6 +318,7 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
                              const double* ics, const int32_t* ic_status, const void* w_in,
                              void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
@@ -332,6 +337,7 @@ chs_status chs_ensemble_init(chs_system s, const chs_params* p, const chs_ensemb
 
 chs_status chs_integrate_batch(chs_system s, const chs_params* p, const chs_ensemble* e, void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
@@ -350,6 +356,7 @@ chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_a
                                   const chs_ensemble* e, double* t, double* h, double* err_last,
                                   double* err_max, int64_t* n_rejected, void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
@@ -378,6 +385,7 @@ chs_status chs_integrate_adaptive(chs_system s, const chs_params* p, const chs_a
 chs_status chs_integrate_persistent(chs_system s, const chs_params* p, const chs_ensemble* e, void* work,
                                     size_t work_bytes, void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if (!chs::small_model(s->sp.model))
@@ -404,6 +412,7 @@ size_t chs_compact_work_size(int64_t n_orbits)
 chs_status chs_integrate_compacted(chs_system s, const chs_params* p, const chs_ensemble* e,
                                    int32_t chunk_steps, void* work, size_t work_bytes, void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if (!chs::small_model(s->sp.model))
@@ -479,6 +488,7 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
                           int32_t grid_npy, double* sali_out, double* gali_out, double* ld_ind_out,
                           int8_t* label_out, void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = check_handle(s);
     if (r != CHS_OK) return r;
     if ((r = check_params(p, s->sp)) != CHS_OK) return r;
@@ -537,6 +547,7 @@ static chs_status lyap_launch(chs_system s, const chs_params* p, int64_t n, cons
 
 chs_status chs_lyapunov_batch(const chs_lyap_job* jobs, int32_t n_jobs, void* stream)
 {
+    CHS_NVTX_RANGE();
     constexpr int kMaxJobs = 16;
     if (!jobs || n_jobs < 1 || n_jobs > kMaxJobs) return fail(CHS_E_INVALID, "need 1..16 jobs");
     for (int i = 0; i < n_jobs; ++i) {
@@ -630,6 +641,7 @@ chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n, c
                                  const int32_t* ic_status, double* lambda_out, int32_t* status_out,
                                  void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = lyap_check(s, p, n, ics, lambda_out, status_out);
     if (r != CHS_OK) return r;
     if (n == 0) return ok();
@@ -641,6 +653,7 @@ chs_status chs_lyapunov_adaptive(chs_system s, const chs_params* p, const chs_ad
                                  int32_t* status_out, int64_t* n_steps_out, int64_t* n_rejected_out,
                                  void* stream)
 {
+    CHS_NVTX_RANGE();
     chs_status r = lyap_check(s, p, n, ics, lambda_out, status_out);
     if (r != CHS_OK) return r;
     if (p->integrator != CHS_DOP853) return fail(CHS_E_INVALID, "adaptive runs need integrator = CHS_DOP853");
@@ -666,6 +679,7 @@ chs_status chs_lyapunov_adaptive(chs_system s, const chs_params* p, const chs_ad
 chs_status chs_peak_probe(int32_t kind, int32_t n_blocks, int32_t n_threads, int64_t n_iter, double* sink,
                           void* stream)
 {
+    CHS_NVTX_RANGE();
     if (kind < CHS_PROBE_DFMA || kind > CHS_PROBE_DMMA) return fail(CHS_E_INVALID, "unknown probe kind %d", kind);
     if (n_blocks < 1 || n_blocks > 65535) return fail(CHS_E_INVALID, "n_blocks must be in 1..65535");
     if (n_threads < 32 || n_threads > 1024 || n_threads % 32 != 0)
@@ -686,6 +700,7 @@ size_t chs_mlp_param_count(void) { return chs::mlp_param_count(); }
 chs_status chs_mlp_features(const double* sali_series, int32_t n_samples, const double* ld,
                             double t_decide, const double* E, int64_t n, float* X, void* stream)
 {
+    CHS_NVTX_RANGE();
     if (n < 0 || n_samples < 0 || n_samples > 10) return fail(CHS_E_INVALID, "need n >= 0 and 0 <= n_samples <= 10");
     if (!(t_decide > 0.0)) return fail(CHS_E_INVALID, "t_decide must be > 0");
     if (n == 0) return ok();
@@ -697,6 +712,7 @@ chs_status chs_mlp_features(const double* sali_series, int32_t n_samples, const 
 chs_status chs_mlp_forward(const void* params_bf16, const float* X, int64_t n, float* Y, void* act,
                            void* stream)
 {
+    CHS_NVTX_RANGE();
     if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
     if (n == 0) return ok();
     if (!params_bf16 || !X || !Y) return fail(CHS_E_INVALID, "pointers must be non-NULL");
@@ -707,6 +723,7 @@ chs_status chs_mlp_forward(const void* params_bf16, const float* X, int64_t n, f
 chs_status chs_mlp_loss_grad(const float* Y, const float* label, const float* target, int64_t n,
                              float w_reg, float* dY, float* loss_out, void* stream)
 {
+    CHS_NVTX_RANGE();
     if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");
     if (n == 0) return ok();
     if (!Y || !label || !target || !dY || !loss_out) return fail(CHS_E_INVALID, "pointers must be non-NULL");
@@ -717,6 +734,7 @@ chs_status chs_mlp_loss_grad(const float* Y, const float* label, const float* ta
 chs_status chs_mlp_backward(const void* params_bf16, const float* X, const void* act, const float* dY,
                             int64_t n, float* delta_work, float* grad_out, void* stream)
 {
+    CHS_NVTX_RANGE();
     if (n < 1) return fail(CHS_E_INVALID, "n must be >= 1");
     if (!params_bf16 || !X || !act || !dY || !delta_work || !grad_out)
         return fail(CHS_E_INVALID, "pointers must be non-NULL");
@@ -727,6 +745,7 @@ chs_status chs_mlp_backward(const void* params_bf16, const float* X, const void*
 chs_status chs_mlp_adam(float* master, float* m, float* v, const float* grad, float lr, float beta1,
                         float beta2, float eps, int32_t step, void* params_bf16_out, void* stream)
 {
+    CHS_NVTX_RANGE();
     if (!master || !m || !v || !grad || !params_bf16_out) return fail(CHS_E_INVALID, "pointers must be non-NULL");
     if (step < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f))
         return fail(CHS_E_INVALID, "need step >= 1, lr > 0 and betas in [0, 1)");
@@ -738,6 +757,7 @@ chs_status chs_surrogate_decide(const void* params_bf16, const double* sali_seri
                                 const double* ld, double t_decide, const double* E, double confidence,
                                 int64_t n, int32_t* status_inout, float* prob_out, void* stream)
 {
+    CHS_NVTX_RANGE();
     if (n < 0 || n_samples < 1 || n_samples > 10) return fail(CHS_E_INVALID, "need n >= 0 and 1 <= n_samples <= 10");
     if (!(t_decide > 0.0)) return fail(CHS_E_INVALID, "t_decide must be > 0");
     if (!(confidence > 0.5 && confidence <= 1.0)) return fail(CHS_E_INVALID, "confidence must be in (0.5, 1]");

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "chs_internal.cuh"
+#include "nvtx_range.cuh"
 
 namespace {
 
@@ -93,6 +94,7 @@ extern "C" chs_status chs_integrate_compacted_static(chs_system s, const chs_par
                                                      const chs_ensemble* e, int32_t chunk_steps,
                                                      void* stream)
 {
+    CHS_NVTX_RANGE();
     int device = -1;
     chs_status r = chs::api_validate_run(s, p, e, &device);
     if (r != CHS_OK) return r;

@@ -271,6 +271,50 @@ def test_adaptive_hh_grid_matches_oracle(tol, k):
     assert np.all(g["err_last"][v] < 1.0)
 
 
+@pytest.mark.parametrize("tol,steps", [(1e-10, 300), (1e-7, 60)])
+def test_adaptive_per_step_error_on_unclipped_steps(tol, steps):
+    """The error of each integration step (Sec. Functionalities) on steps that
+    are never clipped: t_final lies out of reach, so every orbit stops after
+    n_steps accepted steps of the controller's own choosing.  There err_last
+    (the scaled error of the last accepted step) and the next step size are
+    compared with the oracle where err_last > 1e-3, to 1e-6 relative on every
+    orbit whose err_last the oracle itself reproduces to 1e-7 when its initial
+    states move by one ulp (two such runs), and elsewhere to 4x the larger of
+    that one-ulp spread and 1e-6.  (At tol = 1e-10 the one-ulp spread stays below
+    3e-7 after 300 steps; at tol = 1e-7 the steps are ~10x longer and after 60 of
+    them it reaches ~3e-6 on about 1 % of the orbits.  With a last step clipped
+    to t_final, err_last is the error of a short step, tiny and dominated by
+    rounding: test_adaptive_hh_grid_matches_oracle.)"""
+    ics, st = O.grid_ics(*_grid(1 / 8, 20, 20))
+    kw = dict(k=2, ld_p=0.5, h_first=0.01, t_final=1e9, rtol=tol, atol=tol, escape_r2=4.0, seed=5)
+    g = _gpu_adaptive(HH, 2, ics, st, calls=[(steps, 1e9)], **kw)
+    prm = O.params(0.01, steps, n_dev=2, ld_p=0.5, escape_r2=4.0, integrator=O.DOP853)
+    runs = []
+    rng = np.random.default_rng(0)
+    for k in range(3):
+        x = ics if k == 0 else np.nextafter(ics, ics + rng.choice([-1.0, 1.0], ics.shape))
+        e = O.Ensemble(O.henon_heiles(), prm, x, st, seed=5)
+        e.integrate_adaptive(prm, 1e9, tol, tol)
+        runs.append(e)
+    r = runs[0]
+    v = st == 0
+    np.testing.assert_array_equal(g["status"], r.status)
+    assert np.all(g["n_exec"][v] == steps) and np.all(r.n_exec[v] == steps)
+    same = v & (g["n_rej"] == r.n_rej) & (runs[1].n_rej == r.n_rej) & (runs[2].n_rej == r.n_rej)
+    assert same.sum() >= 0.98 * v.sum()
+    m = same & (r.err_last > 1e-3)
+    assert m.sum() >= 0.9 * same.sum()
+    for key in ("err_last", "h"):
+        ref = getattr(r, key)[m]
+        spread = np.maximum(*[np.abs(getattr(q, key)[m] - ref) / ref for q in runs[1:]])
+        err = np.abs(g[key][m] - ref) / ref
+        tight = spread <= 1e-7
+        assert tight.mean() >= 0.5
+        assert err[tight].max() <= 1e-6, (key, err[tight].max())
+        assert err.max() <= 4.0 * max(spread.max(), 1e-6), (key, err.max(), spread.max())
+    np.testing.assert_allclose(g["t"][same], r.t[same], rtol=1e-7, atol=0)
+
+
 def test_adaptive_with_step_cap_matches_oracle_ld():
     """With h_max small and a loose tolerance every step is h_max (the last one
     clipped to t_final): both sides take the same step sequence, and the LD
