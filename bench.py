@@ -752,6 +752,14 @@ def run_gpu(args):
     return 0
 
 
+# Flops of one RK4 step of a quartic-3 orbit with k = 6 FP32 frame vectors
+# (FMA = 2): FP64 -- the orbit's four stages (RHS ~12 each), stage inputs and
+# accumulation over 6 components, energy and escape checks amortised (~170);
+# FP32 -- the stage Hessians (12 per stage), the 6 x 6 propagator applied to 6
+# frame vectors, Gram-Schmidt of the frame and the triangle update (~930).
+QUARTIC_FLOPS = (170, 930)
+
+
 def fput_flops_per_orbit_step(N: int, qr_every: int = 10) -> int:
     """Algorithmic FP64 flops of one step of the FPUT Lyapunov run (FMA = 2):
     propagation of the 2N vectors by the banded one-step RK4 propagator, 36 N^2
@@ -1139,7 +1147,19 @@ def quartic_result(args) -> dict:
     ms = t0.elapsed_time(t1)
     done = int(ens.n_exec.sum()) - e0
     st = ens.status.cpu().numpy()
-    return {"metric": METRIC, "value": done / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    p64, p32 = measured_fp64_peak(sms), measured_fp32_peak(sms)
+    rate = done / (ms / 1e3)
+    f64, f32 = QUARTIC_FLOPS
+    return {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 1,
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "window": "whole bench step (integrate + indicators)",
+                         "flops_per_orbit_step": {"fp64": f64, "fp32": f32},
+                         "flops_basis": "estimate: orbit RHS and RK4 on FP64, the k = 6 frame's propagator, "
+                                        "Gram-Schmidt and triangle update on FP32",
+                         "fp64": {"achieved": f64 * rate / 1e12, "peak": p64["tflops"],
+                                  "frac": f64 * rate / 1e12 / p64["tflops"]},
+                         "fp32": {"achieved": f32 * rate / 1e12, "peak": p32["tflops"],
+                                  "frac": f32 * rate / 1e12 / p32["tflops"]}},
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64 orbit + f32 frame", "data": "synthetic",

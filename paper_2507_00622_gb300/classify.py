@@ -88,8 +88,10 @@ def start_plain_cells(g: GridSpec, ics, st, cells: np.ndarray, stream=None) -> d
     """Launches the plain form (FP64 vectors seeded for that set, every orbit to
     the final step, labels from the final SALI) on the grid cells `cells`, taking
     their initial states from the grid arrays ics / st, asynchronously on
-    `stream` (default: the current stream).  Returns the device tensors, valid
-    once that stream has finished."""
+    `stream` (default: the current stream).  It carries no LD: the LD never acts
+    on the orbit or its vectors, and the labels need SALI only, so they are those
+    of the full plain run.  Returns the device tensors, valid once that stream
+    has finished."""
     stream = stream or torch.cuda.current_stream()
     with torch.cuda.stream(stream):
         S = chs.System(chs.HENON_HEILES, 2)
@@ -97,9 +99,9 @@ def start_plain_cells(g: GridSpec, ics, st, cells: np.ndarray, stream=None) -> d
         ics_c = ics[:, idx].contiguous()
         st_c = st[idx].contiguous()
         n = ics_c.shape[1]
-        kw = dict(n_dev=g.k, ld_p=0.5, escape_r2=4.0, seed=g.seed, sali_threshold=g.sali_threshold)
+        kw = dict(n_dev=g.k, ld_p=0.0, escape_r2=4.0, seed=g.seed, sali_threshold=g.sali_threshold)
         ens = chs.DeviceEnsemble.empty(n, 4, g.k)
-        abi = ens.abi()
+        abi = ens.abi(with_ld=False)
         chs.chs_ensemble_init(S.h, chs.params(g.dt, 1, **kw), abi, ics_c, st_c)
         step, chunk = 0, 100_000
         while step < g.n_steps:
