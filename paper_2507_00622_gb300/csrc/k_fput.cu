@@ -48,8 +48,9 @@ struct FputLyapCfg {
     // orbits share an SM and hide the imbalance; the split measured 4 % slower.
     static constexpr int Q = D >= 128 ? D / 32 : 1;
     // doubles per orbit: W, band rows, stage state, stage stiffnesses, 2 scratch,
-    // the QR's double-buffered partial dot products [2][Q][D] and exponent sums [D]
-    static constexpr int PER = D * D + 18 * N + D + 4 * (N + 1) + 2 + (Q > 1 ? 2 * Q * D + D : 0);
+    // the QR's double-buffered partial dot products [2][Q][D], exponent sums [D]
+    // and squared column norms [D]
+    static constexpr int PER = D * D + 18 * N + D + 4 * (N + 1) + 2 + (Q > 1 ? 2 * Q * D + 2 * D : 0);
     static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
 };
 
@@ -171,14 +172,11 @@ __device__ __forceinline__ void apply_phi(double* W, const double* cf, const int
 // the thread's index in its orbit, P the [2][Q][d] partial sums, Sv[c] the
 // exponent sum of column c.  Every thread of the block calls it.
 template <int N>
-__device__ __forceinline__ void qr_split(double* W, double* P, double* Sv, const int t)
+__device__ __forceinline__ void qr_split(double* W, double* P, double* Sv, double* nrm, const int t)
 {
     constexpr int D = 2 * N, Q = D / 32;
     const int w = t / 32, lane = t % 32;
     const int r0 = 32 * w;
-    double inv[Q];
-#pragma unroll
-    for (int m = 0; m < Q; ++m) inv[m] = 1.0;
     for (int j = 0; j < D; ++j) {
         __syncwarp();  // rows of column j in this warp's block are final
         double* Pb = P + (j & 1) * Q * D;
@@ -199,6 +197,8 @@ __device__ __forceinline__ void qr_split(double* W, double* P, double* Sv, const
         double nj = Pb[j];
 #pragma unroll
         for (int q = 1; q < Q; ++q) nj += Pb[q * D + j];
+        const double inv_nj = 1.0 / nj;  // one division per pivot, not per column
+        if (t == j) nrm[j] = nj;
 #pragma unroll
         for (int m = 0; m < Q; ++m) {
             const int c = lane + 32 * m;
@@ -206,21 +206,22 @@ __device__ __forceinline__ void qr_split(double* W, double* P, double* Sv, const
                 double r = Pb[c];
 #pragma unroll
                 for (int q = 1; q < Q; ++q) r += Pb[q * D + c];
-                const double cfac = -r / nj;
+                const double cfac = -r * inv_nj;
 #pragma unroll 4
                 for (int i = 0; i < 32; ++i) W[(r0 + i) * D + c] = fma(cfac, W[(r0 + i) * D + j], W[(r0 + i) * D + c]);
-            } else if (c == j) {
-                inv[m] = rsqrt(nj);
-                if (w == 0) Sv[j] += 0.5 * log(nj);
             }
         }
     }
-    __syncwarp();
+    // the logarithms and reciprocal roots of the column norms after the loop,
+    // one column per thread, instead of one lane's work inside every pivot step
+    __syncthreads();
+    Sv[t] += 0.5 * log(nrm[t]);
 #pragma unroll
     for (int m = 0; m < Q; ++m) {
         const int c = lane + 32 * m;
+        const double inv = rsqrt(nrm[c]);
 #pragma unroll 4
-        for (int i = 0; i < 32; ++i) W[(r0 + i) * D + c] *= inv[m];
+        for (int i = 0; i < 32; ++i) W[(r0 + i) * D + c] *= inv;
     }
 }
 
@@ -243,6 +244,7 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
     double* red = cs + 4 * (N + 1);
     double* qp = red + 2;            // split QR: partial sums [2][Q][D] (d = 128)
     double* Sv = qp + 2 * Cfg::Q * D;  // split QR: exponent sums [D]
+    double* nrm = Sv + D;              // split QR: squared column norms [D]
 
     const FputCoef fc = {sp.kk, 2.0 * sp.alpha, 3.0 * sp.beta, sp.alpha, sp.beta};
     int32_t st = valid ? (ic_status ? ic_status[o] : CHS_ORBIT_OK) : CHS_ORBIT_FORBIDDEN;
@@ -307,9 +309,9 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
             until_qr = a.qr_every;
             __syncthreads();
             if constexpr (Cfg::Q > 1) {
-                qr_split<N>(W, qp, Sv, l);
+                qr_split<N>(W, qp, Sv, nrm, l);
             } else {
-                double inv = 1.0;
+                double n2 = 1.0;  // this thread's column's squared norm
                 for (int j = 0; j < D; ++j) {
                     double r = 0.0;
                     if (l >= j) {
@@ -321,19 +323,23 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
                         }
                         r = r0 + r1;
                     }
-                    if (l == j) red[0] = r;
+                    if (l == j) {
+                        red[0] = r;
+                        n2 = r;
+                    }
                     __syncthreads();
-                    const double nj = red[0];
                     if (l > j) {
-                        const double cfac = -r / nj;
+                        const double cfac = -r / red[0];
 #pragma unroll 4
                         for (int i = 0; i < D; ++i) W[i * D + l] = fma(cfac, W[i * D + j], W[i * D + l]);
-                    } else if (l == j) {
-                        S += 0.5 * log(nj);
-                        inv = rsqrt(nj);
                     }
                     __syncthreads();
                 }
+                // the logarithm and reciprocal root of every column's norm after
+                // the loop, one per thread, instead of one lane's work inside
+                // every pivot step
+                S += 0.5 * log(n2);
+                const double inv = rsqrt(n2);
 #pragma unroll 4
                 for (int i = 0; i < D; ++i) W[i * D + l] *= inv;
             }
