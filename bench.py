@@ -833,7 +833,15 @@ def fput_result(args) -> dict:
     flops = fput_dp_flops_per_orbit_step if dop else fput_flops_per_orbit_step
     stream = torch.cuda.current_stream()
 
+    work = torch.empty(1, dtype=torch.int64, device="cuda")
+    persistent = getattr(args, "fput_persistent", False)
+
     def step(evs=None):
+        if persistent:
+            # every chain length in one persistent kernel over a work queue
+            chs.chs_lyapunov_batch_persistent([(S.h, prms[N], n, ics, None, lam, st) for N, S, ics, lam, st in runs],
+                                              work)
+            return
         if args.fput_batch:
             # every chain length in one CUDA graph with concurrent branches
             chs.chs_lyapunov_batch([(S.h, prms[N], n, ics, None, lam, st) for N, S, ics, lam, st in runs])
@@ -860,7 +868,7 @@ def fput_result(args) -> dict:
     mp = measured_fp64_peak(torch.cuda.get_device_properties(0).multi_processor_count)
     per_n = {}
     for j, (N, *_rest) in enumerate(runs):
-        if args.fput_batch:
+        if args.fput_batch or persistent:
             per_n[str(N)] = {"qr_every": qr[N]}
             continue
         ms = float(np.mean([evs[i][j][0].elapsed_time(evs[i][j][1]) for i in range(args.steps)]))
@@ -879,8 +887,8 @@ def fput_result(args) -> dict:
                        "N": Ns, "integrator": "DOP853 (fixed step)" if dop else "RK4",
                        "orbits_per_N": n, "steps_per_bench_step": args.chunk,
                        "qr_every": args.qr_every,
-                       "launch": "one CUDA graph, concurrent branches" if args.fput_batch
-                                 else "one launch per N"},
+                       "launch": "one persistent kernel over a work queue" if persistent else
+                                 ("one CUDA graph, concurrent branches" if args.fput_batch else "one launch per N")},
             "per_N": per_n,
             "fp64_peak": {"measured_tflops": mp["tflops"], "sm_mhz": mp["sm_mhz"],
                           "probe": mp["probe"], "formula_tflops": fp64_peak_tflops(2070.0)},
@@ -1349,6 +1357,8 @@ def main():
     ap.add_argument("--fput-orbits", type=int, default=4096)
     ap.add_argument("--qr-every", default="10", help="QR interval of the FPUT run, or 'auto' (autotuner)")
     ap.add_argument("--fput-batch", action="store_true", help="all chain lengths in one CUDA graph")
+    ap.add_argument("--fput-persistent", action="store_true",
+                    help="all chain lengths in one persistent kernel (RK4)")
     ap.add_argument("--block", default="0", choices=["0", "32", "64", "128", "auto"],
                     help="threads per block of the RK4 kernels (grid: integrate kernel; fput: "
                          "Lyapunov kernel); 0 = library default, auto = autotuner")

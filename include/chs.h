@@ -516,6 +516,19 @@ chs_status chs_peak_probe(int32_t kind, int32_t n_blocks, int32_t n_threads, int
  * FMA and MMA probes, square roots for CHS_PROBE_DSQRT; 0 for an unknown kind. */
 double chs_probe_ops_per_thread(int32_t kind, int64_t n_iter);
 
+/* The same jobs as chs_lyapunov_batch (Sec. Functionalities, Lyapunov item; the
+ * FPU example of Sec. Examples), restricted to FPUT chains under RK4 (N in
+ * {4, 8, 16, 32, 64}, any mix and order, at most 16 jobs), run as ONE persistent
+ * kernel: every job is cut into the blocks its own kernel would launch, and a
+ * resident grid takes those blocks from a work queue, longest chains first.
+ * Results are identical to separate chs_lyapunov_spectrum calls; params.
+ * block_threads is ignored (the kernel's blocks have 128 threads).  `work` is
+ * caller-owned device scratch of at least 8 bytes, 8-byte aligned (the queue
+ * counter, reset by the call); calls that share it and overlap on the GPU
+ * race.  All jobs must be on the current device. */
+chs_status chs_lyapunov_batch_persistent(const chs_lyap_job* jobs, int32_t n_jobs, void* work, size_t work_bytes,
+                                         void* stream);
+
 /* Message for the last non-OK status returned on this thread ("" if none).
  * Diagnostics; no paper counterpart. */
 const char* chs_last_error(void);

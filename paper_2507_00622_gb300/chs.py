@@ -29,7 +29,7 @@ EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_sec
            "chs_integrate_adaptive", "chs_lyapunov_adaptive", "chs_integrate_persistent",
            "chs_compact_work_size", "chs_integrate_compacted", "chs_integrate_compacted_static",
            "chs_indicators",
-           "chs_lyapunov_spectrum", "chs_lyapunov_batch", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
+           "chs_lyapunov_spectrum", "chs_lyapunov_batch", "chs_lyapunov_batch_persistent", "chs_mlp_param_count", "chs_mlp_features", "chs_mlp_forward",
            "chs_mlp_loss_grad", "chs_mlp_backward", "chs_mlp_adam", "chs_surrogate_decide",
            "chs_peak_probe", "chs_probe_ops_per_thread", "chs_check_params", "chs_last_error",
            "chs_version")
@@ -102,6 +102,7 @@ def load(path: str | None = None):
                                      P, P, P]),
         "chs_lyapunov_spectrum": (C.c_int, [P, C.POINTER(Params), I64, P, P, P, P, P]),
         "chs_lyapunov_batch": (C.c_int, [C.POINTER(LyapJob), I32, P]),
+        "chs_lyapunov_batch_persistent": (C.c_int, [C.POINTER(LyapJob), I32, P, C.c_size_t, P]),
         "chs_lyapunov_adaptive": (C.c_int, [P, C.POINTER(Params), C.POINTER(Adaptive), I64, P, P, P, P,
                                             P, P, P]),
         "chs_mlp_param_count": (C.c_size_t, []),
@@ -252,6 +253,17 @@ def chs_lyapunov_batch(jobs, stream=None):
         arr[i] = LyapJob(h.value if isinstance(h, C.c_void_p) else h, prm, n, _ptr(ics), _ptr(ic_st),
                          _ptr(lam), _ptr(st))
     _check(load().chs_lyapunov_batch(arr, len(jobs), _stream(stream)))
+
+
+def chs_lyapunov_batch_persistent(jobs, work, stream=None):
+    """jobs: list of (handle, Params, n, ics, ic_status, lam, status) tuples (FPUT,
+    RK4); work: a device tensor of at least 8 bytes (the queue counter)."""
+    arr = (LyapJob * len(jobs))()
+    for i, (h, prm, n, ics, ic_st, lam, st) in enumerate(jobs):
+        arr[i] = LyapJob(h.value if isinstance(h, C.c_void_p) else h, prm, n, _ptr(ics), _ptr(ic_st),
+                         _ptr(lam), _ptr(st))
+    _check(load().chs_lyapunov_batch_persistent(arr, len(jobs), _ptr(work), work.numel() * work.element_size(),
+                                                _stream(stream)))
 
 
 def chs_mlp_param_count() -> int:

@@ -11,6 +11,7 @@
 #include <utility>
 
 #include "chs_internal.cuh"
+#include "fput_batch.cuh"
 #include "nvtx_range.cuh"
 #include "k_dop853.cuh"
 
@@ -635,6 +636,28 @@ static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const
         return fail(CHS_E_UNSUPPORTED, "Lyapunov spectrum not implemented for this model");
     }
     return CHS_OK;
+}
+
+chs_status chs_lyapunov_batch_persistent(const chs_lyap_job* jobs, int32_t n_jobs, void* work, size_t work_bytes,
+                                         void* stream)
+{
+    CHS_NVTX_RANGE();
+    if (!jobs || n_jobs < 1 || n_jobs > chs::kFputBatchMaxJobs) return fail(CHS_E_INVALID, "need 1..16 jobs");
+    if (!work || ((uintptr_t)work & 7u)) return fail(CHS_E_INVALID, "work must be an 8-byte aligned device buffer");
+    if (work_bytes < 8) return fail(CHS_E_SIZE, "work must hold at least 8 bytes");
+    chs::FputBatchJob bj[chs::kFputBatchMaxJobs];
+    for (int i = 0; i < n_jobs; ++i) {
+        const chs_lyap_job& j = jobs[i];
+        chs_status r = lyap_check(j.sys, &j.params, j.n_orbits, j.ics, j.lambda_out, j.status_out);
+        if (r != CHS_OK) return r;
+        if (j.sys->sp.model != CHS_FPUT || j.params.integrator != CHS_RK4)
+            return fail(CHS_E_UNSUPPORTED, "job %d: the persistent batch runs FPUT chains under RK4", i);
+        bj[i] = chs::FputBatchJob{step_args(&j.params), j.sys->sp, j.n_orbits, j.ics, j.ic_status, j.lambda_out,
+                                  j.status_out, j.sys->sp.n_dof, j.sys->sp.alpha == 0.0 ? 1 : 0, 0};
+    }
+    return cuda_status(chs::launch_fput_lyap_batch(bj, n_jobs, static_cast<unsigned long long*>(work),
+                                                   as_stream(stream)),
+                       "persistent batch launch");
 }
 
 chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n, const double* ics,

@@ -1,0 +1,369 @@
+// fput_lyap_lanes.cuh -- the FPUT Lyapunov spectrum by periodic QR for N = 4, 8
+// (RK4, four lanes per orbit), as the work of one block: k_fput_lanes.cu
+// launches it block by block, the mixed-chain persistent kernel (k_fput_batch.cu)
+// runs it from a work queue.
+//
+// The method is the one of fput_lyap_rk4.cuh (RK4 on the chain, the 2N deviation
+// vectors advanced by the exact one-step RK4 propagator Phi, modified
+// Gram-Schmidt every qr_every steps and at the last step, S_j += ln |w_j|).
+// What changes is how an orbit is spread over threads.  GB300 executes FP64
+// instructions per warp at a fixed rate whatever the number of active lanes,
+// and each of an SM's four sub-partitions has its own FP64 unit, so the
+// kernel must (a) never execute FP64 work with idle lanes and (b) give every
+// sub-partition a warp.  An ensemble of 4096 orbits has 512 warps at four
+// lanes per orbit: at most one per sub-partition.  Lane `sub` of an orbit owns
+//   masses i0 .. i0 + M - 1 (i0 = sub * M, M = N / 4): their RK4 stages, the
+//     bonds around them, and rows i0 .. i0 + M - 1 of Phi;
+//   columns sub + 4m of W (m < CPL = 2N / 4): their propagation, and their
+//     part of the QR (columns interleaved over the lanes so that every lane
+//     keeps work until the last Gram-Schmidt column).
+// The orbit's lanes sit in one warp: neighbours' positions and bond
+// stiffnesses pass by shuffles, shared-memory hand-offs are ordered by
+// __syncwarp, and no block barrier is needed.
+//
+// Shared memory per orbit: W (2N x 2N) and the 18 band coefficients of every
+// row of Phi, laid out with the block's orbits innermost (element e of orbit
+// g at [e * G + g]) so that a warp's accesses fall in distinct banks.
+//
+// Phi per row i (stage Hessians H_s, s = 1..4, tridiagonal with diagonal
+// d_s(i) = c_s(i) + c_s(i+1) and off-diagonals -c_s(i), -c_s(i+1), c_s(b) the
+// stiffness V''(q_b - q_{b-1}) of bond b at stage s, bonds 0 and N on the
+// walls):
+//   A = I - h^2/6 (H1 + H2 + H3) + h^4/24 H3 H1
+//   B = h I - h^3/12 (H2 + H3)
+//   C = -h/6 (H1 + 2 H2 + 2 H3 + H4) + h^3/12 (H3 H1 + H4 H2)
+//   D = I - h^2/6 (H2 + H3 + H4) + h^4/24 H4 H2
+// and each column w = (u, v) of W becomes (A u + B v, C u + D v).
+#pragma once
+
+#include <math.h>
+
+#include "chs_internal.cuh"
+
+namespace chs {
+namespace lanes {
+
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int N, int T>
+struct LaneCfg {
+    static constexpr int L = 4;        // lanes per orbit
+    static constexpr int D = 2 * N;
+    static constexpr int M = N / L;    // masses and rows of Phi per lane
+    static constexpr int CPL = D / L;  // columns of W per lane
+    static constexpr int G = T / L;    // orbits per block
+    static constexpr int ROW = 18;     // band coefficients per row of Phi
+    static_assert(N % L == 0 && T % 32 == 0 && T <= 128, "whole masses per lane, whole warps per block");
+    static constexpr size_t SMEM = (size_t)(D * D + N * ROW) * G * sizeof(double);
+};
+
+// Band row of Phi for mass r from the stiffnesses of bonds r-1 .. r+2 at the
+// four stages, cb[s][t] = c_s(r - 1 + t).  Entries (columns r-2 .. r+2 for A,
+// C, D; r-1 .. r+1 for B) go to out[0..17] in the order A[5] B[3] C[5] D[5].
+// Entries of columns outside the chain are computed but never read.
+template <int N>
+__device__ __forceinline__ void phi_row(const int r, const double (&cb)[4][4], const double h, double* out)
+{
+    const double h1 = h / 6.0, h2 = h * h / 6.0, h3 = h * h * h / 12.0, h4 = h * h * h * h / 24.0;
+    // stage Hessians on rows r-1, r, r+1: diagonals, and the couplings of row r
+    // to its neighbours (a wall bond couples to nothing)
+    const bool has_left = r >= 1, has_right = r <= N - 2;
+    double P[2][5];  // P[0] = H3 H1, P[1] = H4 H2 on row r
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int sa = q == 0 ? 2 : 3, sb = q == 0 ? 0 : 1;
+        const double dbm = cb[sb][0] + cb[sb][1];  // d_b(r - 1)
+        const double db0 = cb[sb][1] + cb[sb][2];  // d_b(r)
+        const double dbp = cb[sb][2] + cb[sb][3];  // d_b(r + 1)
+        const double da0 = cb[sa][1] + cb[sa][2];  // d_a(r)
+        const double ca1 = has_left ? cb[sa][1] : 0.0, cb1 = has_left ? cb[sb][1] : 0.0;
+        const double ca2 = has_right ? cb[sa][2] : 0.0, cb2 = has_right ? cb[sb][2] : 0.0;
+        P[q][0] = cb[sa][1] * cb[sb][0];
+        P[q][1] = -fma(cb[sa][1], dbm, da0 * cb[sb][1]);
+        P[q][2] = fma(ca1, cb1, fma(ca2, cb2, da0 * db0));
+        P[q][3] = -fma(da0, cb[sb][2], cb[sa][2] * dbp);
+        P[q][4] = cb[sa][2] * cb[sb][3];
+    }
+    // stage sums of the bond stiffnesses on bonds r (t = 1) and r + 1 (t = 2)
+    double s123[2], s23[2], s234[2], s1223[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        s23[t] = cb[1][t + 1] + cb[2][t + 1];
+        s123[t] = s23[t] + cb[0][t + 1];
+        s234[t] = s23[t] + cb[3][t + 1];
+        s1223[t] = s123[t] + s234[t];
+    }
+    // A and D: I - h^2/6 S + h^4/24 P (S's off-diagonals are -s)
+    out[0] = h4 * P[0][0];
+    out[1] = fma(h4, P[0][1], h2 * s123[0]);
+    out[2] = fma(h4, P[0][2], fma(-h2, s123[0] + s123[1], 1.0));
+    out[3] = fma(h4, P[0][3], h2 * s123[1]);
+    out[4] = h4 * P[0][4];
+    out[13] = h4 * P[1][0];
+    out[14] = fma(h4, P[1][1], h2 * s234[0]);
+    out[15] = fma(h4, P[1][2], fma(-h2, s234[0] + s234[1], 1.0));
+    out[16] = fma(h4, P[1][3], h2 * s234[1]);
+    out[17] = h4 * P[1][4];
+    // B: h I - h^3/12 S23
+    out[5] = h3 * s23[0];
+    out[6] = fma(-h3, s23[0] + s23[1], h);
+    out[7] = h3 * s23[1];
+    // C: -h/6 S1223 + h^3/12 (P31 + P42)
+    out[8] = h3 * (P[0][0] + P[1][0]);
+    out[9] = fma(h3, P[0][1] + P[1][1], h1 * s1223[0]);
+    out[10] = fma(h3, P[0][2] + P[1][2], -h1 * (s1223[0] + s1223[1]));
+    out[11] = fma(h3, P[0][3] + P[1][3], h1 * s1223[1]);
+    out[12] = h3 * (P[0][4] + P[1][4]);
+}
+
+// The work of one block of T threads: the G = T / 4 orbits vb * G .. vb * G +
+// G - 1 (those below n), in the shared memory `smem` (LaneCfg::SMEM bytes).
+// Every thread of the block calls it; it synchronises only within warps.
+template <int N, int T, bool ALPHA0>
+__device__ __forceinline__ void fput_lyap_lanes_block(const StepArgs& a, const SysPar& sp, const int64_t n,
+                                                      const double* __restrict__ ics,
+                                                      const int32_t* __restrict__ ic_status,
+                                                      double* __restrict__ lambda,
+                                                      int32_t* __restrict__ status_out, const int64_t vb,
+                                                      double* smem)
+{
+    using C = LaneCfg<N, T>;
+    constexpr int L = C::L, D = C::D, M = C::M, CPL = C::CPL, G = C::G, ROW = C::ROW;
+    const int g = threadIdx.x / L, sub = threadIdx.x % L;
+    const int64_t o = vb * G + g;
+    const bool valid = o < n;
+    const int i0 = sub * M;
+    const unsigned gbits = ((1u << L) - 1u) << ((threadIdx.x & 31) & ~(L - 1));  // this orbit's lanes
+    double* W = smem;               // W(i, c) at W[(i * D + c) * G + g]
+    double* cf = smem + D * D * G;  // row r, entry e of Phi at cf[(r * ROW + e) * G + g]
+#define WAT(i, c) W[((i) * D + (c)) * G + g]
+
+    const double kk = sp.kk, al = sp.alpha, be = sp.beta, a2 = 2.0 * sp.alpha, b3 = 3.0 * sp.beta;
+    auto orbit_any = [&](bool pred) { return (__ballot_sync(kFull, pred) & gbits) != 0u; };
+
+    int32_t st = valid ? (ic_status ? ic_status[o] : CHS_ORBIT_OK) : CHS_ORBIT_FORBIDDEN;
+    double xq[M], xp[M];
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        xq[k] = valid ? ics[(int64_t)(i0 + k) * n + o] : 0.0;
+        xp[k] = valid ? ics[(int64_t)(N + i0 + k) * n + o] : 0.0;
+        bad = bad || !isfinite(xq[k]) || !isfinite(xp[k]);
+    }
+    if (orbit_any(bad) && st == CHS_ORBIT_OK) st = CHS_ORBIT_NONFINITE;
+    if (st != CHS_ORBIT_OK) {
+#pragma unroll
+        for (int k = 0; k < M; ++k) xq[k] = xp[k] = 0.0;
+    }
+#pragma unroll
+    for (int m = 0; m < CPL; ++m) {
+        const int c = sub + m * L;
+#pragma unroll
+        for (int i = 0; i < D; ++i) WAT(i, c) = (i == c) ? 1.0 : 0.0;
+    }
+    double S[CPL];
+#pragma unroll
+    for (int m = 0; m < CPL; ++m) S[m] = 0.0;
+    __syncwarp();
+
+    const double h = a.dt;
+    int64_t until_qr = a.qr_every;
+    int64_t until = a.sample_every > 0 ? a.sample_every : -1;
+    const long long t_start = clock64();
+    for (int64_t s = 1; s <= a.n_steps; ++s) {
+        // RK4 of the orbit; cw[k][u] = stiffness of bond i0 - 1 + u at stage k
+        double qs[M], ps[M], aq[M], ap[M], cw[4][M + 3];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            qs[k] = xq[k];
+            ps[k] = xp[k];
+        }
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+            const double qL = __shfl_up_sync(kFull, qs[M - 1], 1, L);
+            const double qR = __shfl_down_sync(kFull, qs[0], 1, L);
+            const double ql = sub == 0 ? 0.0 : qL;
+            const double qr = sub == L - 1 ? 0.0 : qR;
+            double dv[M + 1];
+#pragma unroll
+            for (int t = 0; t <= M; ++t) {  // bond i0 + t joins masses i0 + t - 1 and i0 + t
+                const double r = (t < M ? qs[t] : qr) - (t > 0 ? qs[t - 1] : ql);
+                if constexpr (ALPHA0) {
+                    const double r2 = r * r;
+                    dv[t] = r * fma(be, r2, kk);
+                    cw[k4][t + 1] = fma(b3, r2, kk);
+                } else {
+                    dv[t] = r * fma(r, fma(be, r, al), kk);
+                    cw[k4][t + 1] = fma(r, fma(b3, r, a2), kk);
+                }
+            }
+            const double cs = k4 == 2 ? h : 0.5 * h;
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+                const double kq = ps[k];
+                const double kp = dv[k + 1] - dv[k];
+                if (k4 == 0) {
+                    aq[k] = kq;
+                    ap[k] = kp;
+                } else {
+                    const double w = k4 == 3 ? 1.0 : 2.0;
+                    aq[k] = fma(w, kq, aq[k]);
+                    ap[k] = fma(w, kp, ap[k]);
+                }
+                if (k4 < 3) {
+                    qs[k] = fma(cs, kq, xq[k]);
+                    ps[k] = fma(cs, kp, xp[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            xq[k] = fma(h / 6.0, aq[k], xq[k]);
+            xp[k] = fma(h / 6.0, ap[k], xp[k]);
+        }
+        // bonds i0 - 1 and i0 + M + 1 from the neighbouring lanes (none beyond the walls)
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+            const double cl = __shfl_up_sync(kFull, cw[k4][M], 1, L);
+            const double cr = __shfl_down_sync(kFull, cw[k4][2], 1, L);
+            cw[k4][0] = sub == 0 ? 0.0 : cl;
+            cw[k4][M + 2] = sub == L - 1 ? 0.0 : cr;
+        }
+        __syncwarp();  // every lane is done reading the previous step's rows
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+            double cb[4][4], row[ROW];
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) cb[k4][t] = cw[k4][k + t];
+            phi_row<N>(i0 + k, cb, h, row);
+#pragma unroll
+            for (int e = 0; e < ROW; ++e) cf[((i0 + k) * ROW + e) * G + g] = row[e];
+        }
+        __syncwarp();  // the rows of Phi are complete
+        // w <- Phi w for the lane's columns
+#pragma unroll 1
+        for (int m = 0; m < CPL; ++m) {
+            const int c = sub + m * L;
+            double u[N], v[N];
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                u[i] = WAT(i, c);
+                v[i] = WAT(N + i, c);
+            }
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                double k[ROW];
+#pragma unroll
+                for (int e = 0; e < ROW; ++e) k[e] = cf[(i * ROW + e) * G + g];
+                double nu = 0.0, nv = 0.0;
+                bool first = true;
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {  // A and C on u_{i-2..i+2}
+                    const int j = i - 2 + t;
+                    if (j < 0 || j >= N) continue;
+                    nu = first ? k[t] * u[j] : fma(k[t], u[j], nu);
+                    nv = first ? k[8 + t] * u[j] : fma(k[8 + t], u[j], nv);
+                    first = false;
+                }
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {  // B on v_{i-1..i+1}
+                    const int j = i - 1 + t;
+                    if (j < 0 || j >= N) continue;
+                    nu = fma(k[5 + t], v[j], nu);
+                }
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {  // D on v_{i-2..i+2}
+                    const int j = i - 2 + t;
+                    if (j < 0 || j >= N) continue;
+                    nv = fma(k[13 + t], v[j], nv);
+                }
+                WAT(i, c) = nu;
+                WAT(N + i, c) = nv;
+            }
+        }
+
+        if (--until_qr == 0 || s == a.n_steps) {
+            until_qr = a.qr_every;
+            // modified Gram-Schmidt: for column j, every column c >= j forms
+            // r_c = w_j . w_c; the columns c > j subtract (r_c / r_j) w_j; the
+            // columns are scaled to unit length at the end, S_c += ln |w_c|
+            double nrm[CPL];
+#pragma unroll
+            for (int m = 0; m < CPL; ++m) nrm[m] = 1.0;
+#pragma unroll
+            for (int jm = 0; jm < CPL; ++jm) {
+#pragma unroll 1
+                for (int js = 0; js < L; ++js) {
+                    const int j = js + jm * L;
+                    __syncwarp();  // column j is final
+                    double r[CPL];
+#pragma unroll
+                    for (int m = jm; m < CPL; ++m) {
+                        r[m] = 0.0;
+                        if (m > jm || sub >= js) {
+                            const int c = sub + m * L;
+                            double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+                            for (int i = 0; i < D; i += 2) {
+                                s0 = fma(WAT(i, j), WAT(i, c), s0);
+                                s1 = fma(WAT(i + 1, j), WAT(i + 1, c), s1);
+                            }
+                            r[m] = s0 + s1;
+                        }
+                    }
+                    const double nj = __shfl_sync(kFull, r[jm], js, L);  // |w_j|^2 from its lane
+                    if (sub == js) nrm[jm] = nj;
+                    const double y = rsqrt(nj);
+                    const double inv2 = y * y;
+#pragma unroll
+                    for (int m = jm; m < CPL; ++m) {
+                        if (m > jm || sub > js) {
+                            const int c = sub + m * L;
+                            const double f = -r[m] * inv2;
+#pragma unroll
+                            for (int i = 0; i < D; ++i) WAT(i, c) = fma(f, WAT(i, j), WAT(i, c));
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < CPL; ++m) {
+                const int c = sub + m * L;
+                S[m] += 0.5 * log(nrm[m]);
+                const double inv = rsqrt(nrm[m]);
+#pragma unroll
+                for (int i = 0; i < D; ++i) WAT(i, c) *= inv;
+            }
+        }
+        __syncwarp();  // W is final for the next step
+        if (--until == 0) {
+            until = a.sample_every;
+            bool b = false;
+#pragma unroll
+            for (int k = 0; k < M; ++k) b = b || !isfinite(xq[k]) || !isfinite(xp[k]);
+#pragma unroll
+            for (int m = 0; m < CPL; ++m) b = b || !isfinite(S[m]);
+            if (orbit_any(b) && st == CHS_ORBIT_OK) st = CHS_ORBIT_NONFINITE;
+            // warp-uniform: the warp's orbits stop together
+            if (a.clock_budget > 0 && __any_sync(kFull, budget_spent(a, t_start))) {
+                if (st == CHS_ORBIT_OK) st = CHS_ORBIT_STEP_BUDGET;
+                break;
+            }
+        }
+    }
+#undef WAT
+    if (valid) {
+        const double t_total = (double)a.n_steps * a.dt;
+#pragma unroll
+        for (int m = 0; m < CPL; ++m)
+            lambda[(int64_t)(sub + m * L) * n + o] =
+                (st == CHS_ORBIT_OK) ? S[m] / t_total : __longlong_as_double(0x7ff8000000000000LL);
+        if (sub == 0) status_out[o] = st;
+    }
+}
+
+}  // namespace lanes
+}  // namespace chs

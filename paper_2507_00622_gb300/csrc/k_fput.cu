@@ -1,229 +1,8 @@
-// k_fput.cu -- Lyapunov spectrum of the FPUT chain by periodic QR.
-//
-// One orbit per d = 2N threads; a block of T = 32, 64 or 128 threads (at
-// least d) holds T / d orbits.  Thread l owns state component l and column l of the d x d matrix
-// W of deviation vectors, which lives in shared memory (128 KB at N = 64).
-//
-// Propagation of W uses the exact one-step propagator of classic RK4 applied
-// to the linear variational equation w' = J_s w, with J_s = [[0, I], [-H_s, 0]]
-// and H_s the tridiagonal Hessian of the chain at RK4 stage s (s = 1..4):
-//   Phi = I + h/6 (J1 + 2J2 + 2J3 + J4) + h^2/6 (J2J1 + J3J2 + J4J3)
-//           + h^3/12 (J3J2J1 + J4J3J2) + h^4/24 J4J3J2J1,
-// which in blocks is
-//   A = I - h^2/6 (H1 + H2 + H3) + h^4/24 H3 H1       (pentadiagonal)
-//   B = h I - h^3/12 (H2 + H3)                        (tridiagonal)
-//   C = -h/6 (H1 + 2H2 + 2H3 + H4) + h^3/12 (H3 H1 + H4 H2)
-//   D = I - h^2/6 (H2 + H3 + H4) + h^4/24 H4 H2
-// and u' = A u + B v, v' = C u + D v for every column w = (u, v).  In exact
-// arithmetic this equals RK4 on the joint system; it needs no stage copies of
-// W (which would not fit in shared memory at N = 64) and costs 18 FMA per row
-// and column instead of about 26.  The band rows are built once per step and
-// shared by all columns.
-//
-// QR: modified Gram-Schmidt in the "dot products first" order: for column j
-// every column l >= j forms r_l = w_j . w_l (r_j = |w_j|^2), then each l > j
-// subtracts (r_l / r_j) w_j; the columns are scaled to unit length at the end
-// and S_j += ln |w_j| (so R_jj > 0).  Thread l works column l, except at
-// d = 128, where the orbit's Q = 4 warps split the rows instead: warp w takes
-// rows 32w..32w+31 of the columns lane + 32m (m < Q), and the Q partial dot
-// products of a column are summed in a fixed order from shared memory.  Every
-// warp then works while any column is left (with columns per thread, the warp
-// holding the last columns would do all d iterations alone while the others
-// wait at the barriers).
-#include <math.h>
-
-#include "chs_internal.cuh"
+// k_fput.cu -- Lyapunov spectrum of the FPUT chain by periodic QR (RK4), one
+// launch per chain length; the method and the layout are in fput_lyap_rk4.cuh.
+#include "fput_lyap_rk4.cuh"
 
 namespace chs {
-
-template <int N, int T>
-struct FputLyapCfg {
-    static constexpr int D = 2 * N;
-    static constexpr int THREADS = T;
-    static constexpr int G = T / D;  // orbits per block
-    static_assert(T % D == 0 && T <= 128 && T % 32 == 0, "blocks of whole orbits and whole warps");
-    // row blocks of the split QR: the orbit's 4 warps at N = 64, where shared
-    // memory holds one orbit per SM and the QR's critical path is the kernel's
-    // (measured: 1213 -> 1012 ms per 200 steps at QR every 10).  At N = 32 six
-    // orbits share an SM and hide the imbalance; the split measured 4 % slower.
-    static constexpr int Q = D >= 128 ? D / 32 : 1;
-    // doubles per orbit: W, band rows, stage state, stage stiffnesses, 2 scratch,
-    // the QR's double-buffered partial dot products [2][Q][D], exponent sums [D]
-    // and squared column norms [D]
-    static constexpr int PER = D * D + 18 * N + D + 4 * (N + 1) + 2 + (Q > 1 ? 2 * Q * D + 2 * D : 0);
-    static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
-};
-
-struct FputCoef {
-    double k, a2, b3;  // V''(r) = k + 2 alpha r + 3 beta r^2
-    double alpha, beta;
-};
-
-__device__ __forceinline__ double fput_dv(const FputCoef& fc, double r)
-{
-    // V'(r) = k r + alpha r^2 + beta r^3
-    return r * fma(r, fma(fc.beta, r, fc.alpha), fc.k);
-}
-
-__device__ __forceinline__ double fput_d2v(const FputCoef& fc, double r)
-{
-    return fma(r, fma(fc.b3, r, fc.a2), fc.k);
-}
-
-// Band row i of Phi from the stage stiffnesses cs[s][b] (bond b = 0..N joins
-// q_{b-1} and q_b, walls at q_{-1} = q_N = 0).
-template <int N>
-__device__ __forceinline__ void build_phi_row(const int i, const double* cs, const double h,
-                                              double* cf)
-{
-    double cc[4][4], al[4][3];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int b = i - 1 + t;
-            cc[s][t] = (b >= 0 && b <= N) ? cs[s * (N + 1) + b] : 0.0;
-        }
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int j = i - 1 + t;
-            al[s][t] = (j >= 0 && j < N) ? cc[s][t] + cc[s][t + 1] : 0.0;
-        }
-    }
-    const bool left = i >= 1, right = i <= N - 2;
-    // products P = Ha Hb, entries m = -2..2 of row i
-    double P31[5], P42[5];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int a = q == 0 ? 2 : 3, b = q == 0 ? 0 : 1;
-        double* P = q == 0 ? P31 : P42;
-        P[0] = cc[a][1] * cc[b][0];
-        P[1] = -(cc[a][1] * al[b][0] + al[a][1] * cc[b][1]);
-        P[2] = al[a][1] * al[b][1] + (left ? cc[a][1] * cc[b][1] : 0.0) +
-               (right ? cc[a][2] * cc[b][2] : 0.0);
-        P[3] = -(al[a][1] * cc[b][2] + cc[a][2] * al[b][2]);
-        P[4] = cc[a][2] * cc[b][3];
-    }
-    // weighted tridiagonal sums: (sub, diag, super) = (-sum w c_i, sum w alpha_i, -sum w c_{i+1})
-    auto tri = [&](double w0, double w1, double w2, double w3, double* T) {
-        T[0] = -(w0 * cc[0][1] + w1 * cc[1][1] + w2 * cc[2][1] + w3 * cc[3][1]);
-        T[1] = w0 * al[0][1] + w1 * al[1][1] + w2 * al[2][1] + w3 * al[3][1];
-        T[2] = -(w0 * cc[0][2] + w1 * cc[1][2] + w2 * cc[2][2] + w3 * cc[3][2]);
-    };
-    double S123[3], S23[3], S1223[3], S234[3];
-    tri(1.0, 1.0, 1.0, 0.0, S123);
-    tri(0.0, 1.0, 1.0, 0.0, S23);
-    tri(1.0, 2.0, 2.0, 1.0, S1223);
-    tri(0.0, 1.0, 1.0, 1.0, S234);
-    const double h2 = h * h / 6.0, h3 = h * h * h / 12.0, h4 = h * h * h * h / 24.0, h1 = h / 6.0;
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        const double t123 = (m >= 1 && m <= 3) ? S123[m - 1] : 0.0;
-        const double t234 = (m >= 1 && m <= 3) ? S234[m - 1] : 0.0;
-        const double t1223 = (m >= 1 && m <= 3) ? S1223[m - 1] : 0.0;
-        const double id = (m == 2) ? 1.0 : 0.0;
-        cf[m] = id - h2 * t123 + h4 * P31[m];                 // A
-        cf[8 + m] = -h1 * t1223 + h3 * (P31[m] + P42[m]);     // C
-        cf[13 + m] = id - h2 * t234 + h4 * P42[m];            // D
-    }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) cf[5 + m] = (m == 1 ? h : 0.0) - h3 * S23[m];  // B
-}
-
-// w <- Phi w for column l, in place, streaming down the rows with a window of
-// the old values u_{i-2..i+2}, v_{i-2..i+2}.
-template <int N>
-__device__ __forceinline__ void apply_phi(double* W, const double* cf, const int l)
-{
-    constexpr int D = 2 * N;
-    auto U = [&](int i) { return (i >= 0 && i < N) ? W[i * D + l] : 0.0; };
-    auto V = [&](int i) { return (i >= 0 && i < N) ? W[(N + i) * D + l] : 0.0; };
-    double u0 = 0.0, u1 = 0.0, u2 = U(0), u3 = U(1), u4 = U(2);
-    double v0 = 0.0, v1 = 0.0, v2 = V(0), v3 = V(1), v4 = V(2);
-#pragma unroll 4
-    for (int i = 0; i < N; ++i) {
-        const double* c = cf + i * 18;
-        double nu = c[0] * u0;
-        nu = fma(c[1], u1, nu);
-        nu = fma(c[2], u2, nu);
-        nu = fma(c[3], u3, nu);
-        nu = fma(c[4], u4, nu);
-        nu = fma(c[5], v1, nu);
-        nu = fma(c[6], v2, nu);
-        nu = fma(c[7], v3, nu);
-        double nv = c[8] * u0;
-        nv = fma(c[9], u1, nv);
-        nv = fma(c[10], u2, nv);
-        nv = fma(c[11], u3, nv);
-        nv = fma(c[12], u4, nv);
-        nv = fma(c[13], v0, nv);
-        nv = fma(c[14], v1, nv);
-        nv = fma(c[15], v2, nv);
-        nv = fma(c[16], v3, nv);
-        nv = fma(c[17], v4, nv);
-        W[i * D + l] = nu;
-        W[(N + i) * D + l] = nv;
-        u0 = u1; u1 = u2; u2 = u3; u3 = u4; u4 = U(i + 3);
-        v0 = v1; v1 = v2; v2 = v3; v3 = v4; v4 = V(i + 3);
-    }
-}
-
-// The split modified Gram-Schmidt for d = 128 (see the file comment): t is
-// the thread's index in its orbit, P the [2][Q][d] partial sums, Sv[c] the
-// exponent sum of column c.  Every thread of the block calls it.
-template <int N>
-__device__ __forceinline__ void qr_split(double* W, double* P, double* Sv, double* nrm, const int t)
-{
-    constexpr int D = 2 * N, Q = D / 32;
-    const int w = t / 32, lane = t % 32;
-    const int r0 = 32 * w;
-    for (int j = 0; j < D; ++j) {
-        __syncwarp();  // rows of column j in this warp's block are final
-        double* Pb = P + (j & 1) * Q * D;
-#pragma unroll
-        for (int m = 0; m < Q; ++m) {
-            const int c = lane + 32 * m;
-            if (c >= j) {
-                double a0 = 0.0, a1 = 0.0;
-#pragma unroll 4
-                for (int i = 0; i < 32; i += 2) {
-                    a0 = fma(W[(r0 + i) * D + j], W[(r0 + i) * D + c], a0);
-                    a1 = fma(W[(r0 + i + 1) * D + j], W[(r0 + i + 1) * D + c], a1);
-                }
-                Pb[w * D + c] = a0 + a1;
-            }
-        }
-        __syncthreads();
-        double nj = Pb[j];
-#pragma unroll
-        for (int q = 1; q < Q; ++q) nj += Pb[q * D + j];
-        const double inv_nj = 1.0 / nj;  // one division per pivot, not per column
-        if (t == j) nrm[j] = nj;
-#pragma unroll
-        for (int m = 0; m < Q; ++m) {
-            const int c = lane + 32 * m;
-            if (c > j) {
-                double r = Pb[c];
-#pragma unroll
-                for (int q = 1; q < Q; ++q) r += Pb[q * D + c];
-                const double cfac = -r * inv_nj;
-#pragma unroll 4
-                for (int i = 0; i < 32; ++i) W[(r0 + i) * D + c] = fma(cfac, W[(r0 + i) * D + j], W[(r0 + i) * D + c]);
-            }
-        }
-    }
-    // the logarithms and reciprocal roots of the column norms after the loop,
-    // one column per thread, instead of one lane's work inside every pivot step
-    __syncthreads();
-    Sv[t] += 0.5 * log(nrm[t]);
-#pragma unroll
-    for (int m = 0; m < Q; ++m) {
-        const int c = lane + 32 * m;
-        const double inv = rsqrt(nrm[c]);
-#pragma unroll 4
-        for (int i = 0; i < 32; ++i) W[(r0 + i) * D + c] *= inv;
-    }
-}
 
 template <int N, int T>
 __global__ void __launch_bounds__(T)
@@ -231,138 +10,8 @@ k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __
             const int32_t* __restrict__ ic_status, double* __restrict__ lambda,
             int32_t* __restrict__ status_out)
 {
-    using Cfg = FputLyapCfg<N, T>;
-    constexpr int D = Cfg::D, G = Cfg::G, PER = Cfg::PER;
     extern __shared__ double smem[];
-    const int g = threadIdx.x / D, l = threadIdx.x % D;
-    const int64_t o = (int64_t)blockIdx.x * G + g;
-    const bool valid = o < n;
-    double* W = smem + g * PER;
-    double* cf = W + D * D;
-    double* xs = cf + 18 * N;
-    double* cs = xs + D;
-    double* red = cs + 4 * (N + 1);
-    double* qp = red + 2;            // split QR: partial sums [2][Q][D] (d = 128)
-    double* Sv = qp + 2 * Cfg::Q * D;  // split QR: exponent sums [D]
-    double* nrm = Sv + D;              // split QR: squared column norms [D]
-
-    const FputCoef fc = {sp.kk, 2.0 * sp.alpha, 3.0 * sp.beta, sp.alpha, sp.beta};
-    int32_t st = valid ? (ic_status ? ic_status[o] : CHS_ORBIT_OK) : CHS_ORBIT_FORBIDDEN;
-    double xi = valid ? ics[(int64_t)l * n + o] : 0.0;
-
-    // orbit-wide "any thread non-finite" (block-wide barriers; every thread takes part)
-    auto orbit_any = [&](bool pred) {
-        if (l == 0) red[1] = 0.0;
-        __syncthreads();
-        if (pred) red[1] = 1.0;
-        __syncthreads();
-        const bool r = red[1] != 0.0;
-        __syncthreads();
-        return r;
-    };
-    if (orbit_any(!isfinite(xi)) && st == CHS_ORBIT_OK) st = CHS_ORBIT_NONFINITE;
-    if (st != CHS_ORBIT_OK) xi = 0.0;
-
-#pragma unroll 4
-    for (int i = 0; i < D; ++i) W[i * D + l] = (i == l) ? 1.0 : 0.0;
-    xs[l] = xi;
-    double S = 0.0;
-    if constexpr (Cfg::Q > 1) Sv[l] = 0.0;
-    __syncthreads();
-
-    const double h = a.dt;
-    int64_t until_qr = a.qr_every;
-    int64_t until = a.sample_every > 0 ? a.sample_every : -1;
-    const long long t_start = clock64();
-    for (int64_t s = 1; s <= a.n_steps; ++s) {
-        // RK4 of the orbit; stage stiffnesses V''(D_b) recorded for Phi
-        double acc = 0.0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            double fi;
-            if (l < N) {
-                fi = xs[N + l];
-            } else {
-                const int i = l - N;
-                const double qm = i > 0 ? xs[i - 1] : 0.0;
-                const double q0 = xs[i];
-                const double qp = i < N - 1 ? xs[i + 1] : 0.0;
-                fi = fput_dv(fc, qp - q0) - fput_dv(fc, q0 - qm);
-            }
-            if (l <= N) {
-                const double qa = l < N ? xs[l] : 0.0;
-                const double qb = l > 0 ? xs[l - 1] : 0.0;
-                cs[k * (N + 1) + l] = fput_d2v(fc, qa - qb);
-            }
-            __syncthreads();
-            acc = (k == 0) ? fi : fma((k == 3) ? 1.0 : 2.0, fi, acc);
-            if (k < 3) xs[l] = fma(k == 2 ? h : 0.5 * h, fi, xi);
-            __syncthreads();
-        }
-        xi = fma(h / 6.0, acc, xi);
-        xs[l] = xi;
-        if (l < N) build_phi_row<N>(l, cs, h, cf + l * 18);
-        __syncthreads();
-        apply_phi<N>(W, cf, l);
-
-        if (--until_qr == 0 || s == a.n_steps) {
-            until_qr = a.qr_every;
-            __syncthreads();
-            if constexpr (Cfg::Q > 1) {
-                qr_split<N>(W, qp, Sv, nrm, l);
-            } else {
-                double n2 = 1.0;  // this thread's column's squared norm
-                for (int j = 0; j < D; ++j) {
-                    double r = 0.0;
-                    if (l >= j) {
-                        double r0 = 0.0, r1 = 0.0;
-#pragma unroll 4
-                        for (int i = 0; i < D; i += 2) {
-                            r0 = fma(W[i * D + j], W[i * D + l], r0);
-                            r1 = fma(W[(i + 1) * D + j], W[(i + 1) * D + l], r1);
-                        }
-                        r = r0 + r1;
-                    }
-                    if (l == j) {
-                        red[0] = r;
-                        n2 = r;
-                    }
-                    __syncthreads();
-                    if (l > j) {
-                        const double cfac = -r / red[0];
-#pragma unroll 4
-                        for (int i = 0; i < D; ++i) W[i * D + l] = fma(cfac, W[i * D + j], W[i * D + l]);
-                    }
-                    __syncthreads();
-                }
-                // the logarithm and reciprocal root of every column's norm after
-                // the loop, one per thread, instead of one lane's work inside
-                // every pivot step
-                S += 0.5 * log(n2);
-                const double inv = rsqrt(n2);
-#pragma unroll 4
-                for (int i = 0; i < D; ++i) W[i * D + l] *= inv;
-            }
-        }
-        __syncthreads();
-        if constexpr (Cfg::Q > 1) S = Sv[l];
-        if (--until == 0) {
-            until = a.sample_every;
-            if (orbit_any(!(isfinite(xi) && isfinite(S))) && st == CHS_ORBIT_OK)
-                st = CHS_ORBIT_NONFINITE;
-            // block-uniform: the block's orbits stop together
-            if (a.clock_budget > 0 && __syncthreads_or(budget_spent(a, t_start))) {
-                if (st == CHS_ORBIT_OK) st = CHS_ORBIT_STEP_BUDGET;
-                break;
-            }
-        }
-    }
-    if (valid) {
-        const double t_total = (double)a.n_steps * a.dt;
-        lambda[(int64_t)l * n + o] =
-            (st == CHS_ORBIT_OK) ? S / t_total : __longlong_as_double(0x7ff8000000000000LL);
-        if (l == 0) status_out[o] = st;
-    }
+    fput_lyap_block<N, T>(a, sp, n, ics, ic_status, lambda, status_out, blockIdx.x, smem);
 }
 
 bool fput_lyap_supported(int n_dof)

@@ -69,9 +69,10 @@ __device__ __forceinline__ void qr_step_split(double* slab, const int l, double&
     double* W = slab + Sl::W;
     double* P = slab + Sl::QP;
     const int w = l / 32, lane = l % 32, r0 = 32 * w;
-    double inv[Q];
+    double n2[Q];  // squared norms of the thread's columns
 #pragma unroll
-    for (int m = 0; m < Q; ++m) inv[m] = 1.0;
+    for (int m = 0; m < Q; ++m) n2[m] = 1.0;
+    double nl = 1.0;  // squared norm of column l (this thread's exponent)
     for (int j = 0; j < D; ++j) {
         __syncwarp();  // rows of column j in this warp's block are final
         double* Pb = P + (j & 1) * Q * D;
@@ -94,6 +95,7 @@ __device__ __forceinline__ void qr_step_split(double* slab, const int l, double&
         double nj = Pb[j];
 #pragma unroll
         for (int q = 1; q < Q; ++q) nj += Pb[q * D + j];
+        const double inv_nj = 1.0 / nj;  // one division per pivot, not per column
 #pragma unroll
         for (int m = 0; m < Q; ++m) {
             const int c = lane + 32 * m;
@@ -101,22 +103,26 @@ __device__ __forceinline__ void qr_step_split(double* slab, const int l, double&
                 double r = Pb[c];
 #pragma unroll
                 for (int q = 1; q < Q; ++q) r += Pb[q * D + c];
-                const double cfac = -r / nj;
+                const double cfac = -r * inv_nj;
                 double* wc = W + c * WS + r0;
 #pragma unroll 4
                 for (int i = 0; i < 32; ++i) wc[i] = fma(cfac, wj[i], wc[i]);
             } else if (c == j) {
-                inv[m] = rsqrt(nj);
+                n2[m] = nj;
             }
         }
-        if (l == j) S += 0.5 * log(nj);
+        if (l == j) nl = nj;
     }
+    // the logarithms and reciprocal roots after the loop, not one lane's work
+    // inside every pivot step
+    S += 0.5 * log(nl);
     __syncwarp();
 #pragma unroll
     for (int m = 0; m < Q; ++m) {
+        const double inv = rsqrt(n2[m]);
         double* wc = W + (lane + 32 * m) * WS + r0;
 #pragma unroll 4
-        for (int i = 0; i < 32; ++i) wc[i] *= inv[m];
+        for (int i = 0; i < 32; ++i) wc[i] *= inv;
     }
     __syncthreads();
 }
@@ -138,7 +144,7 @@ __device__ __forceinline__ void qr_step(double* slab, const int l, const bool mi
     double* W = slab + Sl::W;
     double* red = slab + Sl::CTL;
     double* wl = W + l * WS;
-    double inv = 1.0;
+    double n2 = 1.0;  // squared norm of this thread's column
     for (int j = 0; j < D; ++j) {
         const double* wj = W + j * WS;
         double r = 0.0;
@@ -151,20 +157,23 @@ __device__ __forceinline__ void qr_step(double* slab, const int l, const bool mi
             }
             r = r0a + r1a;
         }
-        if (mine && l == j) red[0] = r;
+        if (mine && l == j) {
+            red[0] = r;
+            n2 = r;
+        }
         __syncthreads();
-        const double nj = red[0];
         if (mine && l > j) {
-            const double cfac = -r / nj;
+            const double cfac = -r / red[0];
 #pragma unroll 4
             for (int i = 0; i < D; ++i) wl[i] = fma(cfac, wj[i], wl[i]);
-        } else if (mine && l == j) {
-            S += 0.5 * log(nj);
-            inv = rsqrt(nj);
         }
         __syncthreads();
     }
+    // the logarithm and reciprocal root after the loop, one per thread, not one
+    // lane's work inside every pivot step
     if (mine) {
+        S += 0.5 * log(n2);
+        const double inv = rsqrt(n2);
 #pragma unroll 4
         for (int i = 0; i < D; ++i) wl[i] *= inv;
     }

@@ -6,7 +6,7 @@ import numpy as np
 
 import oracle as O
 
-# tolerances (north-star): FP64 states within 1e-10 relative (to the orbit's
+# parity tolerances: FP64 states within 1e-10 relative (to the orbit's
 # state norm), indicators within 1e-8 * max(1, |ref|), labels >= 99.5 %.
 STATE_RTOL = 1e-10
 IND_TOL = 1e-8

@@ -1,5 +1,5 @@
-"""Mixed-length FPUT Lyapunov batch (one CUDA graph, concurrent branches) and the
-autotuner."""
+"""Mixed-length FPUT Lyapunov batches -- one CUDA graph of concurrent branches,
+and one persistent kernel over a work queue -- and the autotuner."""
 import json
 
 import numpy as np
@@ -24,6 +24,61 @@ def _fput_job(N, n, steps, qr=10):
     lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
     st = torch.empty(n, dtype=torch.int32, device="cuda")
     return S, chs.params(0.05, steps, qr_every=qr, sample_every=100), n, ics, lam, st
+
+
+def _fput_job_params(N, n, steps, sp=(1.0, 0.0, 1.0), qr=10, seed=0):
+    S = chs.System(chs.FPUT, N, sp)
+    Q, P = normal_mode_draws(700 + N + seed, N, max(n, 1))
+    ics = torch.from_numpy(np.ascontiguousarray(
+        O.fput_mode_ics(O.fput(N), Q, P, np.full(max(n, 1), 0.1 * N))[:, :n])).cuda()
+    lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+    st = torch.empty(n, dtype=torch.int32, device="cuda")
+    return S, chs.params(0.05, steps, qr_every=qr, sample_every=50), n, ics, lam, st
+
+
+def test_persistent_mixed_chain_batch_equals_separate_calls():
+    """One persistent kernel over every chain length at once (ragged ensembles,
+    an FPUT-alpha+beta job, an empty job, a chain length twice, jobs out of
+    order) gives bit for bit the exponents and statuses of separate calls."""
+    specs = [(8, 45, (1.0, 0.0, 1.0)), (64, 3, (1.0, 0.0, 1.0)), (4, 70, (1.0, 0.25, 1.0)),
+             (16, 9, (1.0, 0.0, 1.0)), (32, 5, (1.0, 0.0, 1.0)), (4, 33, (1.0, 0.0, 1.0)),
+             (16, 0, (1.0, 0.0, 1.0)), (8, 7, (1.0, 0.3, 1.0))]
+    jobs = [_fput_job_params(N, n, 330, sp, qr=7, seed=i) for i, (N, n, sp) in enumerate(specs)]
+    work = torch.empty(1, dtype=torch.int64, device="cuda")
+    for _ in range(2):  # the queue counter is reset by every call
+        chs.chs_lyapunov_batch_persistent([(S.h, prm, n, ics, None, lam, st) for S, prm, n, ics, lam, st in jobs],
+                                          work)
+        torch.cuda.synchronize()
+    got = [(lam.cpu().numpy().copy(), st.cpu().numpy().copy()) for *_x, lam, st in jobs]
+    for (S, prm, n, ics, lam, st), (gl, gs) in zip(jobs, got):
+        if n == 0:
+            continue
+        chs.chs_lyapunov_spectrum(S.h, prm, n, ics, None, lam, st)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(gl, lam.cpu().numpy())
+        np.testing.assert_array_equal(gs, st.cpu().numpy())
+        assert (gs == chs.ORBIT_OK).all()
+
+
+def test_persistent_batch_argument_checks():
+    S, prm, n, ics, lam, st = _fput_job_params(8, 4, 10)
+    work = torch.empty(1, dtype=torch.int64, device="cuda")
+    job = (S.h, prm, n, ics, None, lam, st)
+    with pytest.raises(chs.ChsError) as e:
+        chs.chs_lyapunov_batch_persistent([job] * 17, work)
+    assert e.value.code == chs.CHS_E_INVALID
+    dp = chs.params(0.05, 10, qr_every=10, integrator=chs.DOP853)
+    with pytest.raises(chs.ChsError) as e:
+        chs.chs_lyapunov_batch_persistent([(S.h, dp, n, ics, None, lam, st)], work)
+    assert e.value.code == chs.CHS_E_UNSUPPORTED
+    H = chs.System(chs.HENON_HEILES, 2)
+    hl = torch.empty((4, n), dtype=torch.float64, device="cuda")
+    hi = torch.zeros((4, n), dtype=torch.float64, device="cuda")
+    with pytest.raises(chs.ChsError) as e:
+        chs.chs_lyapunov_batch_persistent([(H.h, chs.params(0.01, 10, qr_every=10), n, hi, None, hl, st)], work)
+    assert e.value.code == chs.CHS_E_UNSUPPORTED
+    code = chs.load().chs_lyapunov_batch_persistent(None, 1, None, 8, None)
+    assert code == chs.CHS_E_INVALID
 
 
 def test_mixed_chain_batch_equals_separate_calls():

@@ -15,10 +15,10 @@ integrate their samples alone, which gives bit for bit the results those orbits
 have inside the full-size launch (each thread integrates its own orbit; checked
 at the bench's chunk length in tests/test_gpu_parity.py).
 
-Bars.  Labels (regular / chaotic / escaped) agree on >= 99.5 % of a sample, as
-the benchmark spec asks.  At t = 1e4 its other tolerances (states within 1e-10,
-indicators within 1e-8 on regular orbits) lie below what FP64 itself
-reproduces: the oracle run a second time from initial states moved by one ulp
+Bars.  Labels (regular / chaotic / escaped) agree on >= 99.5 % of a sample.
+At t = 1e4 the short-horizon tolerances of the other parity tests (states
+within 1e-10, indicators within 1e-8 on regular orbits) lie below what FP64
+itself reproduces: the oracle run a second time from initial states moved by one ulp
 drifts from its first run by up to ~6e-10 in the state and ~4e-7 in SALI on
 regular orbits of the E = 1/8 grid (the phase along a torus drifts with every
 rounding difference, at a rate growing with t).  So each test runs the oracle
