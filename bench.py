@@ -48,7 +48,7 @@ FP64_FLOP_PER_CLK_SM = 4  # 2 DFMA lanes per SM per clock (measured 1.20 TFLOP/s
 # and writes the ensemble state once whatever its step count), valid while the
 # kernel sources hash to the recorded value.
 TRAFFIC_SOURCES = ("k_small.cu", "rk4_common.cuh", "fastmath.cuh", "systems.cuh", "chs_internal.cuh")
-TRAFFIC_RECORD = {"sha256_16": "c182f5c4a97e3bd0", "bytes_per_launch": 146491904.0 + 78790912.0,
+TRAFFIC_RECORD = {"sha256_16": "2c471b190a09231c", "bytes_per_launch": 146702848.0 + 78981888.0,
                   "n_side": 1024}
 
 
@@ -819,17 +819,23 @@ def fput_result(args) -> dict:
         else:
             qr[N] = int(args.qr_every)
     dop = args.integrator == "dop853"
-    blk = {}
+    blk, lanes = {}, {}
     for N in Ns:
+        lanes[N] = 0
         if dop:
             blk[N] = 0  # the DOP853 kernel keeps its own block shape
+        elif args.block == "auto" and N in (4, 8):
+            from paper_2507_00622_gb300 import autotune
+            t = autotune.tune_fput_lanes(N, qr_every=qr[N], n_orbits=n)
+            blk[N], lanes[N] = t["block_threads"], t["threads_per_orbit"]
         elif args.block == "auto":
             from paper_2507_00622_gb300 import autotune
             blk[N] = autotune.tune_fput_block(N, qr_every=qr[N])["block_threads"]
         else:
             blk[N] = int(args.block)
     prms = {N: chs.params(0.05, args.chunk, qr_every=qr[N], sample_every=100,
-                          integrator=chs.DOP853 if dop else chs.RK4, block_threads=blk[N]) for N in Ns}
+                          integrator=chs.DOP853 if dop else chs.RK4, block_threads=blk[N],
+                          threads_per_orbit=lanes[N]) for N in Ns}
     flops = fput_dp_flops_per_orbit_step if dop else fput_flops_per_orbit_step
     stream = torch.cuda.current_stream()
 
@@ -877,7 +883,7 @@ def fput_result(args) -> dict:
         per_n[str(N)] = {"orbit_steps_per_s": os_, "kernel_ms": ms, "fp64_tflops": tf,
                          "frac_of_fp64_peak": tf / mp["tflops"],
                          "frac_of_fp64_formula": tf / fp64_peak_tflops(2070.0), "qr_every": qr[N],
-                         "block_threads": blk[N] or None}
+                         "block_threads": blk[N] or None, "threads_per_orbit": lanes[N] or None}
     value = len(runs) * n * args.chunk * args.steps / (total_ms / 1e3)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,

@@ -128,6 +128,11 @@ typedef struct {
                                 together.  Needs sample_every > 0 to take effect; the
                                 kernels never wait or trap on it.  Not a method step: a
                                 bound on the time one call can take. */
+    int32_t threads_per_orbit; /* threads that integrate one orbit, where a kernel offers the
+                                choice: 0 (the library's default) or, for the RK4 FPUT
+                                Lyapunov spectrum, 1, 2 or 4 at N = 4 and 2 or 4 at N = 8
+                                (default 4); other calls take 0 only.  Results never depend
+                                on it (see chs_lyapunov_spectrum). */
 } chs_params;
 
 /* Checks a parameter block for a system of the given model and n_dof the way
@@ -391,8 +396,10 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
  * propagator, DOP853 column by column with the stages in registers), and
  * HENON_HEILES, HARMONIC, INVERTED.  FP64 throughout.  For FPUT under RK4,
  * p->block_threads (0, or 32, 64, 128 and at least 2N) sets the block size
- * (block_threads / 2N orbits per block; default: the smallest allowed); the
- * results do not depend on it. */
+ * (block_threads / 2N orbits per block for N >= 16, block_threads /
+ * threads_per_orbit at N = 4, 8; default: the smallest allowed), and at N = 4, 8
+ * p->threads_per_orbit the lanes that share one orbit; the results depend on
+ * neither. */
 chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n,
                                  const double* ics, const int32_t* ic_status,
                                  double* lambda_out, int32_t* status_out, void* stream);
@@ -522,7 +529,8 @@ double chs_probe_ops_per_thread(int32_t kind, int64_t n_iter);
  * kernel: every job is cut into the blocks its own kernel would launch, and a
  * resident grid takes those blocks from a work queue, longest chains first.
  * Results are identical to separate chs_lyapunov_spectrum calls; params.
- * block_threads is ignored (the kernel's blocks have 128 threads).  `work` is
+ * block_threads and params.threads_per_orbit are ignored (the kernel's blocks
+ * have 128 threads, four per orbit at N = 4, 8).  `work` is
  * caller-owned device scratch of at least 8 bytes, 8-byte aligned (the queue
  * counter, reset by the call); calls that share it and overlap on the GPU
  * race.  All jobs must be on the current device. */

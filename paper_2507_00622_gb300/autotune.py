@@ -16,10 +16,16 @@ Tuned parameters:
 - block_threads (threads per block) of the one-orbit-per-thread RK4 integrate
   kernels and of the RK4 FPUT Lyapunov kernel (orbits per block = threads / 2N):
   the fastest of 32, 64 and 128 on a sample.  Results do not depend on the block
-  size, so no accuracy guard is needed.  Orbits per thread stay at one: a thread
-  holds its orbit's whole joint state in registers (168 for Henon-Heiles with
-  four vectors and the LD), and the kernels are bound by the FP64 pipe, which a
-  second interleaved orbit per thread could not feed any faster.
+  size, so no accuracy guard is needed.  Orbits per thread stay at one in the
+  one-orbit-per-thread kernels: a thread holds its orbit's whole joint state in
+  registers (168 for Henon-Heiles with four vectors and the LD), and the kernels
+  are bound by the FP64 pipe, which a second interleaved orbit per thread could
+  not feed any faster.
+- threads_per_orbit and block_threads together of the FPUT Lyapunov kernel of
+  the short chains (N = 4: 1, 2 or 4 lanes per orbit; N = 8: 2 or 4): fewer lanes
+  per orbit do less redundant bond work and exchange less, more lanes give an
+  ensemble more warps to spread over the SMs' sub-partitions; the best choice
+  depends on the ensemble size.  Results do not depend on either.
 """
 from __future__ import annotations
 
@@ -214,5 +220,39 @@ def tune_fput_block(N: int, qr_every: int = 10, n_orbits: int = 4096, steps: int
     choice = min(cands, key=lambda b: times[b])
     out = {"block_threads": int(choice), "seconds": {str(b): times[b] for b in cands},
            "n_orbits": n_orbits, "steps": steps}
+    _store(key, out)
+    return out
+
+
+def tune_fput_lanes(N: int, qr_every: int = 10, n_orbits: int = 4096, steps: int = 200,
+                    refresh: bool = False) -> dict:
+    """Pick threads_per_orbit and block_threads of the RK4 FPUT Lyapunov kernel of
+    the short chains (N = 4: 1, 2, 4 lanes per orbit; N = 8: 2, 4) on an ensemble
+    of n_orbits, measuring every pair with the block sizes 32, 64 and 128."""
+    lanes = {4: (1, 2, 4), 8: (2, 4)}[N]
+    blocks = (32, 64, 128)
+    key = f"lanes_fput|{_gpu()}|N={N}|qr={qr_every}|n={n_orbits}"
+    if not refresh:
+        hit = _load().get(key)
+        if hit:
+            return hit
+    S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
+    Q, P = normal_mode_draws(4444 + N, N, n_orbits)
+    ics = torch.empty((2 * N, n_orbits), dtype=torch.float64, device="cuda")
+    chs.chs_fput_mode_ics(S.h, n_orbits, torch.from_numpy(Q).cuda(), torch.from_numpy(P).cuda(),
+                          torch.full((n_orbits,), 0.1 * N, dtype=torch.float64, device="cuda"), ics)
+    lam = torch.empty((2 * N, n_orbits), dtype=torch.float64, device="cuda")
+    st = torch.empty(n_orbits, dtype=torch.int32, device="cuda")
+    times = {}
+    for L in lanes:
+        for b in blocks:
+            prm = chs.params(0.05, steps, qr_every=qr_every, sample_every=100, block_threads=b,
+                             threads_per_orbit=L)
+            run = lambda: chs.chs_lyapunov_spectrum(S.h, prm, n_orbits, ics, None, lam, st)  # noqa: E731
+            run()  # warm-up
+            times[(L, b)] = _best_time(run)
+    L, b = min(times, key=times.get)
+    out = {"threads_per_orbit": int(L), "block_threads": int(b),
+           "seconds": {f"{k[0]}x{k[1]}": v for k, v in times.items()}, "n_orbits": n_orbits, "steps": steps}
     _store(key, out)
     return out

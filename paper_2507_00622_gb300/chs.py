@@ -48,7 +48,7 @@ class Params(C.Structure):
                 ("qr_every", C.c_int32), ("vec_precision", C.c_int32), ("early_exit", C.c_int32),
                 ("ld_p", C.c_double), ("escape_r2", C.c_double), ("dh_limit", C.c_double),
                 ("sali_threshold", C.c_double), ("seed", C.c_uint64), ("integrator", C.c_int32),
-                ("block_threads", C.c_int32), ("clock_budget", C.c_int64)]
+                ("block_threads", C.c_int32), ("clock_budget", C.c_int64), ("threads_per_orbit", C.c_int32)]
 
 
 class Adaptive(C.Structure):
@@ -152,10 +152,11 @@ def params(dt: float, n_steps: int, *, step0: int = 0, n_dev: int = 0, renorm: b
            sample_every: int = 100, qr_every: int = 10, vec_precision: int = VEC_FP64,
            ld_p: float = 0.0, escape_r2: float = 0.0, dh_limit: float = 0.0,
            sali_threshold: float = 1e-8, seed: int = 1, early_exit: bool = False,
-           integrator: int = RK4, block_threads: int = 0, clock_budget: int = 0) -> Params:
+           integrator: int = RK4, block_threads: int = 0, clock_budget: int = 0,
+           threads_per_orbit: int = 0) -> Params:
     return Params(dt, n_steps, step0, n_dev, int(renorm), sample_every, qr_every, vec_precision,
                   int(early_exit), ld_p, escape_r2, dh_limit, sali_threshold, seed, integrator,
-                  block_threads, clock_budget)
+                  block_threads, clock_budget, threads_per_orbit)
 
 
 # ----------------------------------------------------------------------------

@@ -117,6 +117,9 @@ chs_status check_params(const chs_params* p, const chs::SysPar& sp)
     if (p->block_threads != 0 && p->block_threads != 32 && p->block_threads != 64 && p->block_threads != 128)
         return fail(CHS_E_INVALID, "block_threads must be 0, 32, 64 or 128");
     if (p->clock_budget < 0) return fail(CHS_E_INVALID, "clock_budget must be >= 0 (0 = no limit)");
+    if (p->threads_per_orbit != 0)
+        return fail(CHS_E_UNSUPPORTED,
+                    "threads_per_orbit applies to the RK4 FPUT Lyapunov spectrum only (chs_lyapunov_spectrum)");
     return ok();
 }
 
@@ -150,6 +153,7 @@ chs::StepArgs step_args(const chs_params* p)
     a.sali_threshold = p->sali_threshold;
     a.block = p->block_threads;
     a.clock_budget = p->clock_budget;
+    a.threads_per_orbit = p->threads_per_orbit;
     return a;
 }
 
@@ -624,6 +628,11 @@ static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const
     if (p->block_threads != 0 && p->block_threads != 32 && p->block_threads != 64 && p->block_threads != 128)
         return fail(CHS_E_INVALID, "block_threads must be 0, 32, 64 or 128");
     if (p->clock_budget < 0) return fail(CHS_E_INVALID, "clock_budget must be >= 0 (0 = no limit)");
+    if (p->threads_per_orbit != 0 &&
+        !(s->sp.model == CHS_FPUT && p->integrator == CHS_RK4 &&
+          chs::fput_lanes_per_orbit_supported(s->sp.n_dof, p->threads_per_orbit)))
+        return fail(CHS_E_UNSUPPORTED,
+                    "threads_per_orbit: 0, or for the RK4 FPUT spectrum 1, 2, 4 at N = 4 and 2, 4 at N = 8");
     if (s->sp.model == CHS_FPUT && p->block_threads != 0 && p->block_threads < 2 * s->sp.n_dof)
         return fail(CHS_E_INVALID, "FPUT: block_threads must be 0 or at least 2N");
     if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");

@@ -67,6 +67,7 @@ struct StepArgs {
     double sali_threshold;
     int32_t block;         // threads per block requested (0: the kernel's default)
     int64_t clock_budget;  // SM clock cycles an orbit may run in this call (0: no limit)
+    int32_t threads_per_orbit;  // FPUT Lyapunov, N = 4, 8: lanes per orbit (0: the default)
 };
 
 // True once more than a.clock_budget cycles of the SM clock have passed since
@@ -124,6 +125,7 @@ cudaError_t launch_fput_lyap(const SysPar& sp, const StepArgs& a, int64_t n, con
 cudaError_t prepare_fput_lyap(int n_dof);  // sets the shared-memory attribute once
 // Short chains (N = 4, 8): four lanes per orbit (k_fput_lanes.cu).
 bool fput_lyap_lanes_supported(int n_dof);
+bool fput_lanes_per_orbit_supported(int n_dof, int lanes);  // 0 (the default) always
 cudaError_t launch_fput_lyap_lanes(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
                                    const int32_t* ic_status, double* lambda, int32_t* status,
                                    cudaStream_t st);

@@ -6,7 +6,13 @@
 // The method is the one of fput_lyap_rk4.cuh (RK4 on the chain, the 2N deviation
 // vectors advanced by the exact one-step RK4 propagator Phi, modified
 // Gram-Schmidt every qr_every steps and at the last step, S_j += ln |w_j|).
-// What changes is how an orbit is spread over threads.  GB300 executes FP64
+// What changes is how an orbit is spread over threads (L lanes per orbit, four
+// by default; one or two at N = 4 and two at N = 8 are offered to the tuner,
+// and every choice gives the same results bit for bit: each bond, row and
+// column is computed by the same operations whichever lane owns it, and the
+// products that feed a sum are rounded explicitly (__dmul_rn), so that the
+// compiler cannot fuse them into a multiply-add in one instantiation and not
+// in another).  GB300 executes FP64
 // instructions per warp at a fixed rate whatever the number of active lanes,
 // and each of an SM's four sub-partitions has its own FP64 unit, so the
 // kernel must (a) never execute FP64 work with idle lanes and (b) give every
@@ -46,15 +52,16 @@ namespace lanes {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-template <int N, int T>
+template <int N, int T, int L_ = 4>
 struct LaneCfg {
-    static constexpr int L = 4;        // lanes per orbit
+    static constexpr int L = L_;       // lanes per orbit
     static constexpr int D = 2 * N;
     static constexpr int M = N / L;    // masses and rows of Phi per lane
     static constexpr int CPL = D / L;  // columns of W per lane
     static constexpr int G = T / L;    // orbits per block
     static constexpr int ROW = 18;     // band coefficients per row of Phi
-    static_assert(N % L == 0 && T % 32 == 0 && T <= 128, "whole masses per lane, whole warps per block");
+    static_assert(N % L == 0 && 32 % L == 0 && T % 32 == 0 && T <= 128,
+                  "whole masses per lane, an orbit's lanes in one warp, whole warps per block");
     static constexpr size_t SMEM = (size_t)(D * D + N * ROW) * G * sizeof(double);
 };
 
@@ -79,11 +86,14 @@ __device__ __forceinline__ void phi_row(const int r, const double (&cb)[4][4], c
         const double da0 = cb[sa][1] + cb[sa][2];  // d_a(r)
         const double ca1 = has_left ? cb[sa][1] : 0.0, cb1 = has_left ? cb[sb][1] : 0.0;
         const double ca2 = has_right ? cb[sa][2] : 0.0, cb2 = has_right ? cb[sb][2] : 0.0;
-        P[q][0] = cb[sa][1] * cb[sb][0];
-        P[q][1] = -fma(cb[sa][1], dbm, da0 * cb[sb][1]);
-        P[q][2] = fma(ca1, cb1, fma(ca2, cb2, da0 * db0));
-        P[q][3] = -fma(da0, cb[sb][2], cb[sa][2] * dbp);
-        P[q][4] = cb[sa][2] * cb[sb][3];
+        // products that are later summed are rounded on their own (__dmul_rn is
+        // never fused into a following addition), so every instantiation of the
+        // kernel -- whatever its lanes per orbit -- computes the same numbers
+        P[q][0] = __dmul_rn(cb[sa][1], cb[sb][0]);
+        P[q][1] = -fma(cb[sa][1], dbm, __dmul_rn(da0, cb[sb][1]));
+        P[q][2] = fma(ca1, cb1, fma(ca2, cb2, __dmul_rn(da0, db0)));
+        P[q][3] = -fma(da0, cb[sb][2], __dmul_rn(cb[sa][2], dbp));
+        P[q][4] = __dmul_rn(cb[sa][2], cb[sb][3]);
     }
     // stage sums of the bond stiffnesses on bonds r (t = 1) and r + 1 (t = 2)
     double s123[2], s23[2], s234[2], s1223[2];
@@ -120,7 +130,7 @@ __device__ __forceinline__ void phi_row(const int r, const double (&cb)[4][4], c
 // The work of one block of T threads: the G = T / 4 orbits vb * G .. vb * G +
 // G - 1 (those below n), in the shared memory `smem` (LaneCfg::SMEM bytes).
 // Every thread of the block calls it; it synchronises only within warps.
-template <int N, int T, bool ALPHA0>
+template <int N, int T, bool ALPHA0, int LL = 4>
 __device__ __forceinline__ void fput_lyap_lanes_block(const StepArgs& a, const SysPar& sp, const int64_t n,
                                                       const double* __restrict__ ics,
                                                       const int32_t* __restrict__ ic_status,
@@ -128,7 +138,7 @@ __device__ __forceinline__ void fput_lyap_lanes_block(const StepArgs& a, const S
                                                       int32_t* __restrict__ status_out, const int64_t vb,
                                                       double* smem)
 {
-    using C = LaneCfg<N, T>;
+    using C = LaneCfg<N, T, LL>;
     constexpr int L = C::L, D = C::D, M = C::M, CPL = C::CPL, G = C::G, ROW = C::ROW;
     const int g = threadIdx.x / L, sub = threadIdx.x % L;
     const int64_t o = vb * G + g;
@@ -189,12 +199,14 @@ __device__ __forceinline__ void fput_lyap_lanes_block(const StepArgs& a, const S
 #pragma unroll
             for (int t = 0; t <= M; ++t) {  // bond i0 + t joins masses i0 + t - 1 and i0 + t
                 const double r = (t < M ? qs[t] : qr) - (t > 0 ? qs[t - 1] : ql);
+                // V'(r) rounded on its own before the force difference (no fused
+                // multiply-subtract), the same in every instantiation
                 if constexpr (ALPHA0) {
-                    const double r2 = r * r;
-                    dv[t] = r * fma(be, r2, kk);
+                    const double r2 = __dmul_rn(r, r);
+                    dv[t] = __dmul_rn(r, fma(be, r2, kk));
                     cw[k4][t + 1] = fma(b3, r2, kk);
                 } else {
-                    dv[t] = r * fma(r, fma(be, r, al), kk);
+                    dv[t] = __dmul_rn(r, fma(r, fma(be, r, al), kk));
                     cw[k4][t + 1] = fma(r, fma(b3, r, a2), kk);
                 }
             }
@@ -264,8 +276,8 @@ __device__ __forceinline__ void fput_lyap_lanes_block(const StepArgs& a, const S
                 for (int t = 0; t < 5; ++t) {  // A and C on u_{i-2..i+2}
                     const int j = i - 2 + t;
                     if (j < 0 || j >= N) continue;
-                    nu = first ? k[t] * u[j] : fma(k[t], u[j], nu);
-                    nv = first ? k[8 + t] * u[j] : fma(k[8 + t], u[j], nv);
+                    nu = first ? __dmul_rn(k[t], u[j]) : fma(k[t], u[j], nu);
+                    nv = first ? __dmul_rn(k[8 + t], u[j]) : fma(k[8 + t], u[j], nv);
                     first = false;
                 }
 #pragma unroll

@@ -8,71 +8,71 @@ namespace {
 
 using lanes::LaneCfg;
 
-template <int N, int T, bool ALPHA0>
-__global__ void __launch_bounds__(T)
+template <int N, int T, bool ALPHA0, int L>
+__global__ void __launch_bounds__(T, 1)
 k_fput_lyap_lanes(const StepArgs a, const SysPar sp, const int64_t n, const double* __restrict__ ics,
                   const int32_t* __restrict__ ic_status, double* __restrict__ lambda,
                   int32_t* __restrict__ status_out)
 {
     extern __shared__ double smem[];
-    lanes::fput_lyap_lanes_block<N, T, ALPHA0>(a, sp, n, ics, ic_status, lambda, status_out, blockIdx.x, smem);
+    lanes::fput_lyap_lanes_block<N, T, ALPHA0, L>(a, sp, n, ics, ic_status, lambda, status_out, blockIdx.x, smem);
 }
 
-template <int N, int T, bool A0>
+template <int N, int T, bool A0, int L>
 cudaError_t prepare_nta()
 {
     static bool done[kCacheDevices] = {};  // per device; set before any stream capture
     const int dev = cache_device();
     if (done[dev]) return cudaSuccess;
-    const cudaError_t err = cudaFuncSetAttribute(k_fput_lyap_lanes<N, T, A0>,
+    const cudaError_t err = cudaFuncSetAttribute(k_fput_lyap_lanes<N, T, A0, L>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)LaneCfg<N, T>::SMEM);
+                                                 (int)LaneCfg<N, T, L>::SMEM);
     if (err == cudaSuccess) done[dev] = true;
     return err;
 }
 
-template <int N, int T>
-cudaError_t prepare_nt()
+template <int N, int T, int L>
+cudaError_t prepare_ntl()
 {
-    cudaError_t err = prepare_nta<N, T, true>();
-    if (err == cudaSuccess) err = prepare_nta<N, T, false>();
+    cudaError_t err = prepare_nta<N, T, true, L>();
+    if (err == cudaSuccess) err = prepare_nta<N, T, false, L>();
     return err;
 }
 
-template <int N, int T>
-cudaError_t launch_nt(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics, const int32_t* ic_status,
-                      double* lambda, int32_t* status, cudaStream_t st)
+template <int N, int T, int L>
+cudaError_t launch_ntl(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics, const int32_t* ic_status,
+                       double* lambda, int32_t* status, cudaStream_t st)
 {
-    using Cfg = LaneCfg<N, T>;
-    cudaError_t err = prepare_nt<N, T>();
+    using Cfg = LaneCfg<N, T, L>;
+    cudaError_t err = prepare_ntl<N, T, L>();
     if (err != cudaSuccess) return err;
     if (sp.alpha == 0.0)
-        k_fput_lyap_lanes<N, T, true><<<blocks_for(n, Cfg::G), T, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status,
-                                                                                 lambda, status);
+        k_fput_lyap_lanes<N, T, true, L><<<blocks_for(n, Cfg::G), T, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status,
+                                                                                    lambda, status);
     else
-        k_fput_lyap_lanes<N, T, false><<<blocks_for(n, Cfg::G), T, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status,
-                                                                                  lambda, status);
+        k_fput_lyap_lanes<N, T, false, L><<<blocks_for(n, Cfg::G), T, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status,
+                                                                                     lambda, status);
     return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t launch_n(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics, const int32_t* ic_status,
-                     double* lambda, int32_t* status, cudaStream_t st)
+template <int N, int L>
+cudaError_t launch_nl(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics, const int32_t* ic_status,
+                      double* lambda, int32_t* status, cudaStream_t st)
 {
     switch (a.block > 0 ? a.block : 32) {
-    case 32: return launch_nt<N, 32>(sp, a, n, ics, ic_status, lambda, status, st);
-    case 64: return launch_nt<N, 64>(sp, a, n, ics, ic_status, lambda, status, st);
-    case 128: return launch_nt<N, 128>(sp, a, n, ics, ic_status, lambda, status, st);
+    case 32: return launch_ntl<N, 32, L>(sp, a, n, ics, ic_status, lambda, status, st);
+    case 64: return launch_ntl<N, 64, L>(sp, a, n, ics, ic_status, lambda, status, st);
+    case 128: return launch_ntl<N, 128, L>(sp, a, n, ics, ic_status, lambda, status, st);
     }
     return cudaErrorInvalidValue;
 }
 
-template <int N>
-cudaError_t prepare_n()
+template <int N, int L>
+cudaError_t prepare_nl()
 {
-    cudaError_t err = prepare_nt<N, 32>();
-    if (err == cudaSuccess) err = prepare_nt<N, 64>();
-    if (err == cudaSuccess) err = prepare_nt<N, 128>();
+    cudaError_t err = prepare_ntl<N, 32, L>();
+    if (err == cudaSuccess) err = prepare_ntl<N, 64, L>();
+    if (err == cudaSuccess) err = prepare_ntl<N, 128, L>();
     return err;
 }
 
@@ -80,24 +80,50 @@ cudaError_t prepare_n()
 
 bool fput_lyap_lanes_supported(int n_dof) { return n_dof == 4 || n_dof == 8; }
 
-cudaError_t prepare_fput_lyap_lanes(int n_dof)
+bool fput_lanes_per_orbit_supported(int n_dof, int lanes)
 {
-    switch (n_dof) {
-    case 4: return prepare_n<4>();
-    case 8: return prepare_n<8>();
-    }
-    return cudaErrorInvalidValue;
+    if (lanes == 0) return true;
+    if (n_dof == 4) return lanes == 1 || lanes == 2 || lanes == 4;
+    if (n_dof == 8) return lanes == 2 || lanes == 4;
+    return false;
 }
 
-// Default block: one warp (8 orbits), whose accesses to the block's shared
-// arrays are conflict-free; 64 and 128 threads are offered to the tuner.
+cudaError_t prepare_fput_lyap_lanes(int n_dof)
+{
+    cudaError_t err = cudaErrorInvalidValue;
+    switch (n_dof) {
+    case 4:
+        err = prepare_nl<4, 4>();
+        if (err == cudaSuccess) err = prepare_nl<4, 2>();
+        if (err == cudaSuccess) err = prepare_nl<4, 1>();
+        break;
+    case 8:
+        err = prepare_nl<8, 4>();
+        if (err == cudaSuccess) err = prepare_nl<8, 2>();
+        break;
+    }
+    return err;
+}
+
+// Default: four lanes per orbit and one-warp blocks (8 orbits), whose accesses to
+// the block's shared arrays are conflict-free; the other lane counts and 64 and
+// 128 threads are offered to the tuner.
 cudaError_t launch_fput_lyap_lanes(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
                                    const int32_t* ic_status, double* lambda, int32_t* status, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    switch (sp.n_dof) {
-    case 4: return launch_n<4>(sp, a, n, ics, ic_status, lambda, status, st);
-    case 8: return launch_n<8>(sp, a, n, ics, ic_status, lambda, status, st);
+    const int lanes = a.threads_per_orbit > 0 ? a.threads_per_orbit : 4;
+    if (sp.n_dof == 4) {
+        switch (lanes) {
+        case 4: return launch_nl<4, 4>(sp, a, n, ics, ic_status, lambda, status, st);
+        case 2: return launch_nl<4, 2>(sp, a, n, ics, ic_status, lambda, status, st);
+        case 1: return launch_nl<4, 1>(sp, a, n, ics, ic_status, lambda, status, st);
+        }
+    } else if (sp.n_dof == 8) {
+        switch (lanes) {
+        case 4: return launch_nl<8, 4>(sp, a, n, ics, ic_status, lambda, status, st);
+        case 2: return launch_nl<8, 2>(sp, a, n, ics, ic_status, lambda, status, st);
+        }
     }
     return cudaErrorInvalidValue;
 }

@@ -82,7 +82,7 @@ def test_struct_layouts_match_header(lib, tmp_path):
         for f, _ in py._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
     assert int(got["chs_lyap_job"]) == C.sizeof(chs.LyapJob)
-    assert C.sizeof(chs.Params) == 104 and C.sizeof(chs.Ensemble) == 72
+    assert C.sizeof(chs.Params) == 112 and C.sizeof(chs.Ensemble) == 72
 
 
 def test_binding_refuses_host_tensors(lib):
@@ -129,6 +129,10 @@ def test_params_checks_need_no_device(lib):
             chs.chs_check_params(prm, chs.HENON_HEILES, 2)
         assert word in str(e.value)
     assert lib.chs_check_params(None, chs.HENON_HEILES, 2) == chs.CHS_E_INVALID
+    # threads per orbit is a choice of the FPUT Lyapunov kernels only
+    with pytest.raises(chs.ChsError) as e:
+        chs.chs_check_params(chs.params(0.01, 10, threads_per_orbit=2), chs.HENON_HEILES, 2)
+    assert e.value.code == chs.CHS_E_UNSUPPORTED and "threads_per_orbit" in str(e.value)
 
 
 def test_static_scratch_entry_point_names_no_allocation():

@@ -57,6 +57,58 @@ def test_fput_lyapunov_block_size_is_bit_identical():
         S.close()
 
 
+@pytest.mark.parametrize("N,lanes", [(4, (1, 2, 4)), (8, (2, 4))])
+def test_fput_lyapunov_lanes_per_orbit_is_bit_identical(N, lanes):
+    """The short chains' kernel with 1, 2 or 4 lanes per orbit (N = 4) or 2 or 4
+    (N = 8), at every block size, FPUT-beta and FPUT-alpha+beta, a ragged last
+    block and a health check: identical exponents and statuses."""
+    n = 45
+    Q, P = normal_mode_draws(17 + N, N, n)
+    ics = torch.from_numpy(O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))).cuda()
+    for sp in ((1.0, 0.0, 1.0), (1.0, 0.25, 1.0)):
+        S = chs.System(chs.FPUT, N, sp)
+        outs = []
+        for L in (0,) + lanes:
+            for b in (0, 32, 64, 128):
+                lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+                sto = torch.empty(n, dtype=torch.int32, device="cuda")
+                chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, 130, qr_every=7, sample_every=20, block_threads=b,
+                                                          threads_per_orbit=L), n, ics, None, lam, sto)
+                outs.append((lam.cpu().numpy(), sto.cpu().numpy()))
+        for lam, sto in outs[1:]:
+            np.testing.assert_array_equal(lam, outs[0][0])
+            np.testing.assert_array_equal(sto, outs[0][1])
+        S.close()
+
+
+def test_fput_lanes_argument_checks():
+    S = chs.System(chs.FPUT, 8, (1.0, 0.0, 1.0))
+    ics = torch.zeros((16, 4), dtype=torch.float64, device="cuda")
+    lam = torch.empty((16, 4), dtype=torch.float64, device="cuda")
+    sto = torch.empty(4, dtype=torch.int32, device="cuda")
+    for L in (1, 3, 8):
+        with pytest.raises(chs.ChsError) as e:
+            chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, 10, qr_every=10, threads_per_orbit=L), 4, ics, None,
+                                      lam, sto)
+        assert e.value.code == chs.CHS_E_UNSUPPORTED
+    with pytest.raises(chs.ChsError):
+        chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, 10, qr_every=10, threads_per_orbit=2,
+                                                  integrator=chs.DOP853), 4, ics, None, lam, sto)
+    H = chs.System(chs.FPUT, 16, (1.0, 0.0, 1.0))
+    with pytest.raises(chs.ChsError):
+        chs.chs_lyapunov_spectrum(H.h, chs.params(0.05, 10, qr_every=10, threads_per_orbit=4), 0, None, None,
+                                  None, None)
+
+
+def test_fput_lanes_autotuner_picks_and_caches(tmp_path, monkeypatch):
+    monkeypatch.setenv("CHS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    from paper_2507_00622_gb300 import autotune
+    r = autotune.tune_fput_lanes(4, n_orbits=1024, steps=40)
+    assert r["threads_per_orbit"] in (1, 2, 4) and r["block_threads"] in (32, 64, 128)
+    assert len(r["seconds"]) == 9
+    assert autotune.tune_fput_lanes(4, n_orbits=1024, steps=40) == r
+
+
 def test_block_threads_argument_checks():
     S = chs.System(chs.HENON_HEILES, 2)
     ens = chs.DeviceEnsemble.empty(8, 4, 2)
