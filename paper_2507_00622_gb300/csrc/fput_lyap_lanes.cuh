@@ -31,24 +31,16 @@
 // row of Phi, laid out with the block's orbits innermost (element e of orbit
 // g at [e * G + g]) so that a warp's accesses fall in distinct banks.
 //
-// Phi per row i (stage Hessians H_s, s = 1..4, tridiagonal with diagonal
-// d_s(i) = c_s(i) + c_s(i+1) and off-diagonals -c_s(i), -c_s(i+1), c_s(b) the
-// stiffness V''(q_b - q_{b-1}) of bond b at stage s, bonds 0 and N on the
-// walls):
-//   A = I - h^2/6 (H1 + H2 + H3) + h^4/24 H3 H1
-//   B = h I - h^3/12 (H2 + H3)
-//   C = -h/6 (H1 + 2 H2 + 2 H3 + H4) + h^3/12 (H3 H1 + H4 H2)
-//   D = I - h^2/6 (H2 + H3 + H4) + h^4/24 H4 H2
-// and each column w = (u, v) of W becomes (A u + B v, C u + D v).
+// The band rows of Phi come from fput_phi.cuh.
 #pragma once
 
 #include <math.h>
 
 #include "chs_internal.cuh"
+#include "fput_phi.cuh"
 
 namespace chs {
 namespace lanes {
-
 
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -64,68 +56,6 @@ struct LaneCfg {
                   "whole masses per lane, an orbit's lanes in one warp, whole warps per block");
     static constexpr size_t SMEM = (size_t)(D * D + N * ROW) * G * sizeof(double);
 };
-
-// Band row of Phi for mass r from the stiffnesses of bonds r-1 .. r+2 at the
-// four stages, cb[s][t] = c_s(r - 1 + t).  Entries (columns r-2 .. r+2 for A,
-// C, D; r-1 .. r+1 for B) go to out[0..17] in the order A[5] B[3] C[5] D[5].
-// Entries of columns outside the chain are computed but never read.
-template <int N>
-__device__ __forceinline__ void phi_row(const int r, const double (&cb)[4][4], const double h, double* out)
-{
-    const double h1 = h / 6.0, h2 = h * h / 6.0, h3 = h * h * h / 12.0, h4 = h * h * h * h / 24.0;
-    // stage Hessians on rows r-1, r, r+1: diagonals, and the couplings of row r
-    // to its neighbours (a wall bond couples to nothing)
-    const bool has_left = r >= 1, has_right = r <= N - 2;
-    double P[2][5];  // P[0] = H3 H1, P[1] = H4 H2 on row r
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int sa = q == 0 ? 2 : 3, sb = q == 0 ? 0 : 1;
-        const double dbm = cb[sb][0] + cb[sb][1];  // d_b(r - 1)
-        const double db0 = cb[sb][1] + cb[sb][2];  // d_b(r)
-        const double dbp = cb[sb][2] + cb[sb][3];  // d_b(r + 1)
-        const double da0 = cb[sa][1] + cb[sa][2];  // d_a(r)
-        const double ca1 = has_left ? cb[sa][1] : 0.0, cb1 = has_left ? cb[sb][1] : 0.0;
-        const double ca2 = has_right ? cb[sa][2] : 0.0, cb2 = has_right ? cb[sb][2] : 0.0;
-        // products that are later summed are rounded on their own (__dmul_rn is
-        // never fused into a following addition), so every instantiation of the
-        // kernel -- whatever its lanes per orbit -- computes the same numbers
-        P[q][0] = __dmul_rn(cb[sa][1], cb[sb][0]);
-        P[q][1] = -fma(cb[sa][1], dbm, __dmul_rn(da0, cb[sb][1]));
-        P[q][2] = fma(ca1, cb1, fma(ca2, cb2, __dmul_rn(da0, db0)));
-        P[q][3] = -fma(da0, cb[sb][2], __dmul_rn(cb[sa][2], dbp));
-        P[q][4] = __dmul_rn(cb[sa][2], cb[sb][3]);
-    }
-    // stage sums of the bond stiffnesses on bonds r (t = 1) and r + 1 (t = 2)
-    double s123[2], s23[2], s234[2], s1223[2];
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        s23[t] = cb[1][t + 1] + cb[2][t + 1];
-        s123[t] = s23[t] + cb[0][t + 1];
-        s234[t] = s23[t] + cb[3][t + 1];
-        s1223[t] = s123[t] + s234[t];
-    }
-    // A and D: I - h^2/6 S + h^4/24 P (S's off-diagonals are -s)
-    out[0] = h4 * P[0][0];
-    out[1] = fma(h4, P[0][1], h2 * s123[0]);
-    out[2] = fma(h4, P[0][2], fma(-h2, s123[0] + s123[1], 1.0));
-    out[3] = fma(h4, P[0][3], h2 * s123[1]);
-    out[4] = h4 * P[0][4];
-    out[13] = h4 * P[1][0];
-    out[14] = fma(h4, P[1][1], h2 * s234[0]);
-    out[15] = fma(h4, P[1][2], fma(-h2, s234[0] + s234[1], 1.0));
-    out[16] = fma(h4, P[1][3], h2 * s234[1]);
-    out[17] = h4 * P[1][4];
-    // B: h I - h^3/12 S23
-    out[5] = h3 * s23[0];
-    out[6] = fma(-h3, s23[0] + s23[1], h);
-    out[7] = h3 * s23[1];
-    // C: -h/6 S1223 + h^3/12 (P31 + P42)
-    out[8] = h3 * (P[0][0] + P[1][0]);
-    out[9] = fma(h3, P[0][1] + P[1][1], h1 * s1223[0]);
-    out[10] = fma(h3, P[0][2] + P[1][2], -h1 * (s1223[0] + s1223[1]));
-    out[11] = fma(h3, P[0][3] + P[1][3], h1 * s1223[1]);
-    out[12] = h3 * (P[0][4] + P[1][4]);
-}
 
 // The work of one block of T threads: the G = T / 4 orbits vb * G .. vb * G +
 // G - 1 (those below n), in the shared memory `smem` (LaneCfg::SMEM bytes).
@@ -195,18 +125,17 @@ __device__ __forceinline__ void fput_lyap_lanes_block(const StepArgs& a, const S
             const double qR = __shfl_down_sync(kFull, qs[0], 1, L);
             const double ql = sub == 0 ? 0.0 : qL;
             const double qr = sub == L - 1 ? 0.0 : qR;
-            double dv[M + 1];
+            double rb[M + 1], xb[M + 1];  // bond stretch r and V'(r) / r
 #pragma unroll
             for (int t = 0; t <= M; ++t) {  // bond i0 + t joins masses i0 + t - 1 and i0 + t
                 const double r = (t < M ? qs[t] : qr) - (t > 0 ? qs[t - 1] : ql);
-                // V'(r) rounded on its own before the force difference (no fused
-                // multiply-subtract), the same in every instantiation
+                rb[t] = r;
                 if constexpr (ALPHA0) {
-                    const double r2 = __dmul_rn(r, r);
-                    dv[t] = __dmul_rn(r, fma(be, r2, kk));
+                    const double r2 = r * r;
+                    xb[t] = fma(be, r2, kk);
                     cw[k4][t + 1] = fma(b3, r2, kk);
                 } else {
-                    dv[t] = __dmul_rn(r, fma(r, fma(be, r, al), kk));
+                    xb[t] = fma(r, fma(be, r, al), kk);
                     cw[k4][t + 1] = fma(r, fma(b3, r, a2), kk);
                 }
             }
@@ -214,7 +143,9 @@ __device__ __forceinline__ void fput_lyap_lanes_block(const StepArgs& a, const S
 #pragma unroll
             for (int k = 0; k < M; ++k) {
                 const double kq = ps[k];
-                const double kp = dv[k + 1] - dv[k];
+                // force V'(r_right) - V'(r_left), the left term rounded on its own
+                // and the right one fused: one form whatever the lane count
+                const double kp = fma(rb[k + 1], xb[k + 1], -__dmul_rn(rb[k], xb[k]));
                 if (k4 == 0) {
                     aq[k] = kq;
                     ap[k] = kp;
@@ -250,7 +181,7 @@ __device__ __forceinline__ void fput_lyap_lanes_block(const StepArgs& a, const S
             for (int k4 = 0; k4 < 4; ++k4)
 #pragma unroll
                 for (int t = 0; t < 4; ++t) cb[k4][t] = cw[k4][k + t];
-            phi_row<N>(i0 + k, cb, h, row);
+            fput_phi::phi_row<N>(i0 + k, cb, h, row);
 #pragma unroll
             for (int e = 0; e < ROW; ++e) cf[((i0 + k) * ROW + e) * G + g] = row[e];
         }

@@ -37,6 +37,7 @@
 #include <math.h>
 
 #include "chs_internal.cuh"
+#include "fput_phi.cuh"
 
 namespace chs {
 
@@ -51,10 +52,13 @@ struct FputLyapCfg {
     // (measured: 1213 -> 1012 ms per 200 steps at QR every 10).  At N = 32 six
     // orbits share an SM and hide the imbalance; the split measured 4 % slower.
     static constexpr int Q = D >= 128 ? D / 32 : 1;
-    // doubles per orbit: W, band rows, stage state, stage stiffnesses, 2 scratch,
+    // row stride of W: at d = 32 one padding column, so that the row blocks of
+    // the in-warp QR (qr_warp32) fall in distinct shared-memory banks
+    static constexpr int WS = D == 32 ? D + 1 : D;
+    // doubles per orbit: W (D rows of WS), band rows, stage state, stage stiffnesses, 2 scratch,
     // the QR's double-buffered partial dot products [2][Q][D], exponent sums [D]
     // and squared column norms [D]
-    static constexpr int PER = D * D + 18 * N + D + 4 * (N + 1) + 2 + (Q > 1 ? 2 * Q * D + 2 * D : 0);
+    static constexpr int PER = D * WS + 18 * N + D + 4 * (N + 1) + 2 + (Q > 1 ? 2 * Q * D + 2 * D : 0);
     static constexpr size_t SMEM = (size_t)G * PER * sizeof(double);
 };
 
@@ -63,10 +67,10 @@ struct FputCoef {
     double alpha, beta;
 };
 
-__device__ __forceinline__ double fput_dv(const FputCoef& fc, double r)
+__device__ __forceinline__ double fput_dv_over_r(const FputCoef& fc, double r)
 {
-    // V'(r) = k r + alpha r^2 + beta r^3
-    return r * fma(r, fma(fc.beta, r, fc.alpha), fc.k);
+    // V'(r) / r = k + alpha r + beta r^2
+    return fma(r, fma(fc.beta, r, fc.alpha), fc.k);
 }
 
 __device__ __forceinline__ double fput_d2v(const FputCoef& fc, double r)
@@ -74,74 +78,13 @@ __device__ __forceinline__ double fput_d2v(const FputCoef& fc, double r)
     return fma(r, fma(fc.b3, r, fc.a2), fc.k);
 }
 
-// Band row i of Phi from the stage stiffnesses cs[s][b] (bond b = 0..N joins
-// q_{b-1} and q_b, walls at q_{-1} = q_N = 0).
-template <int N>
-__device__ __forceinline__ void build_phi_row(const int i, const double* cs, const double h,
-                                              double* cf)
-{
-    double cc[4][4], al[4][3];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int b = i - 1 + t;
-            cc[s][t] = (b >= 0 && b <= N) ? cs[s * (N + 1) + b] : 0.0;
-        }
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-            const int j = i - 1 + t;
-            al[s][t] = (j >= 0 && j < N) ? cc[s][t] + cc[s][t + 1] : 0.0;
-        }
-    }
-    const bool left = i >= 1, right = i <= N - 2;
-    // products P = Ha Hb, entries m = -2..2 of row i
-    double P31[5], P42[5];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int a = q == 0 ? 2 : 3, b = q == 0 ? 0 : 1;
-        double* P = q == 0 ? P31 : P42;
-        P[0] = cc[a][1] * cc[b][0];
-        P[1] = -(cc[a][1] * al[b][0] + al[a][1] * cc[b][1]);
-        P[2] = al[a][1] * al[b][1] + (left ? cc[a][1] * cc[b][1] : 0.0) +
-               (right ? cc[a][2] * cc[b][2] : 0.0);
-        P[3] = -(al[a][1] * cc[b][2] + cc[a][2] * al[b][2]);
-        P[4] = cc[a][2] * cc[b][3];
-    }
-    // weighted tridiagonal sums: (sub, diag, super) = (-sum w c_i, sum w alpha_i, -sum w c_{i+1})
-    auto tri = [&](double w0, double w1, double w2, double w3, double* T) {
-        T[0] = -(w0 * cc[0][1] + w1 * cc[1][1] + w2 * cc[2][1] + w3 * cc[3][1]);
-        T[1] = w0 * al[0][1] + w1 * al[1][1] + w2 * al[2][1] + w3 * al[3][1];
-        T[2] = -(w0 * cc[0][2] + w1 * cc[1][2] + w2 * cc[2][2] + w3 * cc[3][2]);
-    };
-    double S123[3], S23[3], S1223[3], S234[3];
-    tri(1.0, 1.0, 1.0, 0.0, S123);
-    tri(0.0, 1.0, 1.0, 0.0, S23);
-    tri(1.0, 2.0, 2.0, 1.0, S1223);
-    tri(0.0, 1.0, 1.0, 1.0, S234);
-    const double h2 = h * h / 6.0, h3 = h * h * h / 12.0, h4 = h * h * h * h / 24.0, h1 = h / 6.0;
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        const double t123 = (m >= 1 && m <= 3) ? S123[m - 1] : 0.0;
-        const double t234 = (m >= 1 && m <= 3) ? S234[m - 1] : 0.0;
-        const double t1223 = (m >= 1 && m <= 3) ? S1223[m - 1] : 0.0;
-        const double id = (m == 2) ? 1.0 : 0.0;
-        cf[m] = id - h2 * t123 + h4 * P31[m];                 // A
-        cf[8 + m] = -h1 * t1223 + h3 * (P31[m] + P42[m]);     // C
-        cf[13 + m] = id - h2 * t234 + h4 * P42[m];            // D
-    }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) cf[5 + m] = (m == 1 ? h : 0.0) - h3 * S23[m];  // B
-}
-
 // w <- Phi w for column l, in place, streaming down the rows with a window of
 // the old values u_{i-2..i+2}, v_{i-2..i+2}.
-template <int N>
+template <int N, int WS>
 __device__ __forceinline__ void apply_phi(double* W, const double* cf, const int l)
 {
-    constexpr int D = 2 * N;
-    auto U = [&](int i) { return (i >= 0 && i < N) ? W[i * D + l] : 0.0; };
-    auto V = [&](int i) { return (i >= 0 && i < N) ? W[(N + i) * D + l] : 0.0; };
+    auto U = [&](int i) { return (i >= 0 && i < N) ? W[i * WS + l] : 0.0; };
+    auto V = [&](int i) { return (i >= 0 && i < N) ? W[(N + i) * WS + l] : 0.0; };
     double u0 = 0.0, u1 = 0.0, u2 = U(0), u3 = U(1), u4 = U(2);
     double v0 = 0.0, v1 = 0.0, v2 = V(0), v3 = V(1), v4 = V(2);
 #pragma unroll 4
@@ -165,8 +108,8 @@ __device__ __forceinline__ void apply_phi(double* W, const double* cf, const int
         nv = fma(c[15], v2, nv);
         nv = fma(c[16], v3, nv);
         nv = fma(c[17], v4, nv);
-        W[i * D + l] = nu;
-        W[(N + i) * D + l] = nv;
+        W[i * WS + l] = nu;
+        W[(N + i) * WS + l] = nv;
         u0 = u1; u1 = u2; u2 = u3; u3 = u4; u4 = U(i + 3);
         v0 = v1; v1 = v2; v2 = v3; v3 = v4; v4 = V(i + 3);
     }
@@ -229,6 +172,64 @@ __device__ __forceinline__ void qr_split(double* W, double* P, double* Sv, doubl
     }
 }
 
+// The modified Gram-Schmidt for d = 32, where an orbit is one warp: lane
+// l = 8 b + p takes rows 8b .. 8b + 7 of the columns p + 8m (m < 4), so that
+// every lane keeps work until the last column group (one column per lane
+// leaves lanes l < j idle at pivot j, and an idle lane costs an FP64 slot).  A
+// column's four partial dot products are summed by a butterfly over the lanes
+// p, p + 8, p + 16, p + 24, which gives the same sum in all four.  W's rows are
+// WS = 33 apart, so the row blocks of a half-warp fall in distinct banks.
+// Returns, in lane l, the squared norm of column l before normalisation.
+template <int N, int WS>
+__device__ __forceinline__ double qr_warp32(double* W, const int l)
+{
+    constexpr int D = 2 * N, CG = D / 8;  // column groups
+    static_assert(D == 32, "one warp per orbit");
+    const int p = l % 8;
+    double* Wb = W + (l / 8) * 8 * WS;  // this lane's row block
+    double n2 = 1.0;
+#pragma unroll
+    for (int jm = 0; jm < CG; ++jm) {
+#pragma unroll 1
+        for (int jp = 0; jp < 8; ++jp) {
+            const int j = jp + 8 * jm;
+            __syncwarp();  // column j is final
+            double r[CG];
+#pragma unroll
+            for (int m = jm; m < CG; ++m) {
+                double part = 0.0;
+                if (m > jm || p >= jp) {
+                    const int c = p + 8 * m;
+                    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+                    for (int i = 0; i < 8; i += 2) {
+                        s0 = fma(Wb[i * WS + j], Wb[i * WS + c], s0);
+                        s1 = fma(Wb[(i + 1) * WS + j], Wb[(i + 1) * WS + c], s1);
+                    }
+                    part = s0 + s1;
+                }
+                part += __shfl_xor_sync(0xffffffffu, part, 8);
+                part += __shfl_xor_sync(0xffffffffu, part, 16);
+                r[m] = part;
+            }
+            const double nj = __shfl_sync(0xffffffffu, r[jm], jp);  // |w_j|^2
+            if (l == j) n2 = nj;
+            const double inv_nj = 1.0 / nj;  // one division per pivot
+#pragma unroll
+            for (int m = jm; m < CG; ++m) {
+                if (m > jm || p > jp) {
+                    const int c = p + 8 * m;
+                    const double f = -r[m] * inv_nj;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) Wb[i * WS + c] = fma(f, Wb[i * WS + j], Wb[i * WS + c]);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    return n2;
+}
+
 // The work of one block of T threads: the G = T / 2N orbits vb * G .. vb * G +
 // G - 1 (those below n), in the shared memory `smem` (FputLyapCfg::SMEM bytes).
 // Every thread of the block calls it; it contains block barriers.
@@ -240,12 +241,12 @@ __device__ __forceinline__ void fput_lyap_block(const StepArgs& a, const SysPar&
                                                 const int64_t vb, double* smem)
 {
     using Cfg = FputLyapCfg<N, T>;
-    constexpr int D = Cfg::D, G = Cfg::G, PER = Cfg::PER;
+    constexpr int D = Cfg::D, G = Cfg::G, PER = Cfg::PER, WS = Cfg::WS;
     const int g = threadIdx.x / D, l = threadIdx.x % D;
     const int64_t o = vb * G + g;
     const bool valid = o < n;
     double* W = smem + g * PER;
-    double* cf = W + D * D;
+    double* cf = W + D * WS;
     double* xs = cf + 18 * N;
     double* cs = xs + D;
     double* red = cs + 4 * (N + 1);
@@ -271,7 +272,7 @@ __device__ __forceinline__ void fput_lyap_block(const StepArgs& a, const SysPar&
     if (st != CHS_ORBIT_OK) xi = 0.0;
 
 #pragma unroll 4
-    for (int i = 0; i < D; ++i) W[i * D + l] = (i == l) ? 1.0 : 0.0;
+    for (int i = 0; i < D; ++i) W[i * WS + l] = (i == l) ? 1.0 : 0.0;
     xs[l] = xi;
     double S = 0.0;
     if constexpr (Cfg::Q > 1) Sv[l] = 0.0;
@@ -294,7 +295,10 @@ __device__ __forceinline__ void fput_lyap_block(const StepArgs& a, const SysPar&
                 const double qm = i > 0 ? xs[i - 1] : 0.0;
                 const double q0 = xs[i];
                 const double qp = i < N - 1 ? xs[i + 1] : 0.0;
-                fi = fput_dv(fc, qp - q0) - fput_dv(fc, q0 - qm);
+                // V'(r_right) - V'(r_left), the left term rounded on its own and the
+                // right one fused (the form of the short chains' kernel)
+                const double rr = qp - q0, rl = q0 - qm;
+                fi = fma(rr, fput_dv_over_r(fc, rr), -__dmul_rn(rl, fput_dv_over_r(fc, rl)));
             }
             if (l <= N) {
                 const double qa = l < N ? xs[l] : 0.0;
@@ -308,15 +312,31 @@ __device__ __forceinline__ void fput_lyap_block(const StepArgs& a, const SysPar&
         }
         xi = fma(h / 6.0, acc, xi);
         xs[l] = xi;
-        if (l < N) build_phi_row<N>(l, cs, h, cf + l * 18);
+        if (l < N) {
+            double cb[4][4];  // stiffnesses of bonds l - 1 .. l + 2 (none beyond the walls)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int b = l - 1 + t;
+                    cb[k][t] = (b >= 0 && b <= N) ? cs[k * (N + 1) + b] : 0.0;
+                }
+            fput_phi::phi_row<N>(l, cb, h, cf + l * 18);
+        }
         __syncthreads();
-        apply_phi<N>(W, cf, l);
+        apply_phi<N, WS>(W, cf, l);
 
         if (--until_qr == 0 || s == a.n_steps) {
             until_qr = a.qr_every;
             __syncthreads();
             if constexpr (Cfg::Q > 1) {
                 qr_split<N>(W, qp, Sv, nrm, l);
+            } else if constexpr (D == 32) {
+                const double n2 = qr_warp32<N, WS>(W, l);
+                S += 0.5 * log(n2);
+                const double inv = rsqrt(n2);
+#pragma unroll 4
+                for (int i = 0; i < D; ++i) W[i * WS + l] *= inv;
             } else {
                 double n2 = 1.0;  // this thread's column's squared norm
                 for (int j = 0; j < D; ++j) {

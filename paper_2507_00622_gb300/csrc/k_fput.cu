@@ -5,7 +5,7 @@
 namespace chs {
 
 template <int N, int T>
-__global__ void __launch_bounds__(T)
+__global__ void __launch_bounds__(T, 1)
 k_fput_lyap(const StepArgs a, const SysPar sp, const int64_t n, const double* __restrict__ ics,
             const int32_t* __restrict__ ic_status, double* __restrict__ lambda,
             int32_t* __restrict__ status_out)
