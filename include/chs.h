@@ -395,10 +395,11 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
  * vectors live in shared memory; RK4 propagates them by its exact one-step
  * propagator, DOP853 column by column with the stages in registers), and
  * HENON_HEILES, HARMONIC, INVERTED.  FP64 throughout.  For FPUT under RK4,
- * p->block_threads (0, or 32, 64, 128 and at least 2N) sets the block size
- * (block_threads / 2N orbits per block for N >= 16, block_threads /
- * threads_per_orbit at N = 4, 8; default: 64 at N = 4, else the smallest
- * allowed), and at N = 4, 8
+ * p->block_threads (0, or 32, 64, 128 and at least 2N; at N = 64 also 256)
+ * sets the block size (block_threads / 2N orbits per block for N = 16, 32,
+ * block_threads / threads_per_orbit at N = 4, 8; one orbit at N = 64, with two
+ * threads per vector at 256; default: 64 at N = 4, 256 at N = 64, else the
+ * smallest allowed), and at N = 4, 8
  * p->threads_per_orbit the lanes that share one orbit; the results depend on
  * neither. */
 chs_status chs_lyapunov_spectrum(chs_system s, const chs_params* p, int64_t n,

@@ -197,8 +197,9 @@ def tune_block_integrate(k: int = 4, ld: bool = True, vec_fp32: bool = False, si
 def tune_fput_block(N: int, qr_every: int = 10, n_orbits: int = 4096, steps: int = 200,
                     refresh: bool = False) -> dict:
     """Pick block_threads of the RK4 FPUT Lyapunov kernel for chains of N sites
-    (every multiple of 2N among 32, 64, 128)."""
-    cands = [b for b in (32, 64, 128) if b >= 2 * N]
+    (every multiple of 2N among 32, 64, 128; at N = 64 also 256, two threads per
+    vector)."""
+    cands = [b for b in (32, 64, 128) if b >= 2 * N] + ([256] if N == 64 else [])
     key = f"block_fput|{_gpu()}|N={N}|qr={qr_every}|n={n_orbits}|cand={','.join(map(str, cands))}"
     if not refresh:
         hit = _load().get(key)

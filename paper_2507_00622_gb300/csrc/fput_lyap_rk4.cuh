@@ -81,7 +81,7 @@ __device__ __forceinline__ double fput_d2v(const FputCoef& fc, double r)
 // w <- Phi w for column l, in place, streaming down the rows with a window of
 // the old values u_{i-2..i+2}, v_{i-2..i+2}.
 template <int N, int WS>
-__device__ __forceinline__ void apply_phi(double* W, const double* cf, const int l)
+__device__ __forceinline__ void apply_phi(double* __restrict__ W, const double* __restrict__ cf, const int l)
 {
     auto U = [&](int i) { return (i >= 0 && i < N) ? W[i * WS + l] : 0.0; };
     auto V = [&](int i) { return (i >= 0 && i < N) ? W[(N + i) * WS + l] : 0.0; };
@@ -115,6 +115,63 @@ __device__ __forceinline__ void apply_phi(double* W, const double* cf, const int
     }
 }
 
+// One pivot step of the split modified Gram-Schmidt for d = 128, for the
+// column groups m >= M0 (columns lane + 32 m; the groups below are finished:
+// M0 = j / 32).  The groups' dot products run in one block of code, sharing the
+// loads of the pivot column and giving the warp independent FMA chains; lanes
+// whose column is below j compute too but store only into sums nobody reads.
+template <int N, int M0>
+__device__ __forceinline__ void split_dots(const double* __restrict__ W, double* __restrict__ Pb, const int j,
+                                           const int w, const int lane)
+{
+    constexpr int D = 2 * N, Q = D / 32;
+    const int r0 = 32 * w;
+    double a0[Q], a1[Q];
+#pragma unroll
+    for (int m = M0; m < Q; ++m) a0[m] = a1[m] = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < 32; i += 2) {
+        const double wj0 = W[(r0 + i) * D + j], wj1 = W[(r0 + i + 1) * D + j];
+#pragma unroll
+        for (int m = M0; m < Q; ++m) {
+            const int c = lane + 32 * m;
+            a0[m] = fma(wj0, W[(r0 + i) * D + c], a0[m]);
+            a1[m] = fma(wj1, W[(r0 + i + 1) * D + c], a1[m]);
+        }
+    }
+#pragma unroll
+    for (int m = M0; m < Q; ++m) Pb[w * D + lane + 32 * m] = a0[m] + a1[m];
+}
+
+// The update of the columns c > j of this warp's rows, groups m >= M0.
+template <int N, int M0>
+__device__ __forceinline__ void split_axpy(double* __restrict__ W, const double* __restrict__ Pb, const int j,
+                                           const double inv_nj, const int w, const int lane)
+{
+    constexpr int D = 2 * N, Q = D / 32;
+    const int r0 = 32 * w;
+    double f[Q];
+#pragma unroll
+    for (int m = M0; m < Q; ++m) {
+        const int c = lane + 32 * m;
+        double r = Pb[c];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) r += Pb[q * D + c];
+        f[m] = -r * inv_nj;
+    }
+    const bool diag_active = lane + 32 * M0 > j;  // groups above M0 lie wholly right of j
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+        const double wj = W[(r0 + i) * D + j];
+#pragma unroll
+        for (int m = M0; m < Q; ++m) {
+            const int c = lane + 32 * m;
+            const double v = fma(f[m], wj, W[(r0 + i) * D + c]);
+            if (m > M0 || diag_active) W[(r0 + i) * D + c] = v;
+        }
+    }
+}
+
 // The split modified Gram-Schmidt for d = 128 (see the file comment): t is
 // the thread's index in its orbit, P the [2][Q][d] partial sums, Sv[c] the
 // exponent sum of column c.  Every thread of the block calls it.
@@ -122,23 +179,17 @@ template <int N>
 __device__ __forceinline__ void qr_split(double* W, double* P, double* Sv, double* nrm, const int t)
 {
     constexpr int D = 2 * N, Q = D / 32;
+    static_assert(Q == 4, "four row blocks");
     const int w = t / 32, lane = t % 32;
     const int r0 = 32 * w;
     for (int j = 0; j < D; ++j) {
         __syncwarp();  // rows of column j in this warp's block are final
         double* Pb = P + (j & 1) * Q * D;
-#pragma unroll
-        for (int m = 0; m < Q; ++m) {
-            const int c = lane + 32 * m;
-            if (c >= j) {
-                double a0 = 0.0, a1 = 0.0;
-#pragma unroll 4
-                for (int i = 0; i < 32; i += 2) {
-                    a0 = fma(W[(r0 + i) * D + j], W[(r0 + i) * D + c], a0);
-                    a1 = fma(W[(r0 + i + 1) * D + j], W[(r0 + i + 1) * D + c], a1);
-                }
-                Pb[w * D + c] = a0 + a1;
-            }
+        switch (j >> 5) {  // block-uniform
+        case 0: split_dots<N, 0>(W, Pb, j, w, lane); break;
+        case 1: split_dots<N, 1>(W, Pb, j, w, lane); break;
+        case 2: split_dots<N, 2>(W, Pb, j, w, lane); break;
+        default: split_dots<N, 3>(W, Pb, j, w, lane); break;
         }
         __syncthreads();
         double nj = Pb[j];
@@ -146,17 +197,11 @@ __device__ __forceinline__ void qr_split(double* W, double* P, double* Sv, doubl
         for (int q = 1; q < Q; ++q) nj += Pb[q * D + j];
         const double inv_nj = 1.0 / nj;  // one division per pivot, not per column
         if (t == j) nrm[j] = nj;
-#pragma unroll
-        for (int m = 0; m < Q; ++m) {
-            const int c = lane + 32 * m;
-            if (c > j) {
-                double r = Pb[c];
-#pragma unroll
-                for (int q = 1; q < Q; ++q) r += Pb[q * D + c];
-                const double cfac = -r * inv_nj;
-#pragma unroll 4
-                for (int i = 0; i < 32; ++i) W[(r0 + i) * D + c] = fma(cfac, W[(r0 + i) * D + j], W[(r0 + i) * D + c]);
-            }
+        switch (j >> 5) {
+        case 0: split_axpy<N, 0>(W, Pb, j, inv_nj, w, lane); break;
+        case 1: split_axpy<N, 1>(W, Pb, j, inv_nj, w, lane); break;
+        case 2: split_axpy<N, 2>(W, Pb, j, inv_nj, w, lane); break;
+        default: split_axpy<N, 3>(W, Pb, j, inv_nj, w, lane); break;
         }
     }
     // the logarithms and reciprocal roots of the column norms after the loop,

@@ -45,7 +45,7 @@ def test_fput_lyapunov_block_size_is_bit_identical():
         ics = torch.from_numpy(O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))).cuda()
         S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
         outs = []
-        for b in [0] + [b for b in (32, 64, 128) if b >= 2 * N]:
+        for b in [0] + [b for b in (32, 64, 128) if b >= 2 * N] + ([256] if N == 64 else []):
             lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
             sto = torch.empty(n, dtype=torch.int32, device="cuda")
             chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, 60, qr_every=10, block_threads=b), n, ics, None,
@@ -78,6 +78,45 @@ def test_fput_lyapunov_lanes_per_orbit_is_bit_identical(N, lanes):
         for lam, sto in outs[1:]:
             np.testing.assert_array_equal(lam, outs[0][0])
             np.testing.assert_array_equal(sto, outs[0][1])
+        S.close()
+
+
+def test_fput_n64_two_threads_per_vector_is_bit_identical():
+    """N = 64 with 256 threads per orbit (two per deviation vector) against the
+    128-thread body: FPUT-alpha+beta, QR every 7 steps with a last partial
+    interval, health checks, and one orbit made NONFINITE: identical exponents
+    and statuses."""
+    N, n = 64, 7
+    Q, P = normal_mode_draws(640, N, n)
+    ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))
+    ics[N + 3, 4] = np.nan
+    ics = torch.from_numpy(ics).cuda()
+    for sp in ((1.0, 0.0, 1.0), (1.0, 0.25, 1.0)):
+        S = chs.System(chs.FPUT, N, sp)
+        outs = []
+        for b in (0, 256, 128):
+            lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+            sto = torch.empty(n, dtype=torch.int32, device="cuda")
+            chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, 130, qr_every=7, sample_every=20, block_threads=b),
+                                      n, ics, None, lam, sto)
+            outs.append((lam.cpu().numpy(), sto.cpu().numpy()))
+        assert outs[0][1][4] == chs.ORBIT_NONFINITE and (outs[0][1] == chs.ORBIT_OK).sum() == n - 1
+        for lam, sto in outs[1:]:
+            np.testing.assert_array_equal(lam, outs[0][0])
+            np.testing.assert_array_equal(sto, outs[0][1])
+        S.close()
+
+
+def test_fput_block_256_only_at_n64_rk4():
+    for N, integ in ((32, chs.RK4), (64, chs.DOP853)):
+        S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
+        ics = torch.zeros((2 * N, 2), dtype=torch.float64, device="cuda")
+        lam = torch.empty((2 * N, 2), dtype=torch.float64, device="cuda")
+        sto = torch.empty(2, dtype=torch.int32, device="cuda")
+        with pytest.raises(chs.ChsError) as e:
+            chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, 10, qr_every=10, block_threads=256, integrator=integ),
+                                      2, ics, None, lam, sto)
+        assert e.value.code == chs.CHS_E_INVALID
         S.close()
 
 

@@ -360,7 +360,7 @@ def test_fput_alpha_beta_lyapunov_matches_oracle(N):
     assert np.abs(g - r).max() < 1e-8
 
 
-@pytest.mark.parametrize("N", [4, 8])
+@pytest.mark.parametrize("N", [4, 8, 64])
 def test_fput_lyapunov_nonfinite_orbit(N):
     """A NaN in one component of one orbit (a component of the third of the
     orbit's lanes) makes that orbit NONFINITE with NaN exponents and leaves its
