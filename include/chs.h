@@ -130,8 +130,8 @@ typedef struct {
                                 bound on the time one call can take. */
     int32_t threads_per_orbit; /* threads that integrate one orbit, where a kernel offers the
                                 choice: 0 (the library's default) or, for the RK4 FPUT
-                                Lyapunov spectrum, 1, 2 or 4 at N = 4 and 2 or 4 at N = 8
-                                (default 4); other calls take 0 only.  Results never depend
+                                Lyapunov spectrum, 1, 2 or 4 at N = 4 (default 4) and 2, 4
+                                or 8 at N = 8 (default 8); other calls take 0 only.  Results never depend
                                 on it (see chs_lyapunov_spectrum). */
 } chs_params;
 

@@ -22,7 +22,7 @@ Tuned parameters:
   are bound by the FP64 pipe, which a second interleaved orbit per thread could
   not feed any faster.
 - threads_per_orbit and block_threads together of the FPUT Lyapunov kernel of
-  the short chains (N = 4: 1, 2 or 4 lanes per orbit; N = 8: 2 or 4): fewer lanes
+  the short chains (N = 4: 1, 2 or 4 lanes per orbit; N = 8: 2, 4 or 8): fewer lanes
   per orbit do less redundant bond work and exchange less, more lanes give an
   ensemble more warps to spread over the SMs' sub-partitions; the best choice
   depends on the ensemble size.  Results do not depend on either.
@@ -228,9 +228,9 @@ def tune_fput_block(N: int, qr_every: int = 10, n_orbits: int = 4096, steps: int
 def tune_fput_lanes(N: int, qr_every: int = 10, n_orbits: int = 4096, steps: int = 200,
                     refresh: bool = False) -> dict:
     """Pick threads_per_orbit and block_threads of the RK4 FPUT Lyapunov kernel of
-    the short chains (N = 4: 1, 2, 4 lanes per orbit; N = 8: 2, 4) on an ensemble
+    the short chains (N = 4: 1, 2, 4 lanes per orbit; N = 8: 2, 4, 8) on an ensemble
     of n_orbits, measuring every pair with the block sizes 32, 64 and 128."""
-    lanes = {4: (1, 2, 4), 8: (2, 4)}[N]
+    lanes = {4: (1, 2, 4), 8: (2, 4, 8)}[N]
     blocks = (32, 64, 128)
     key = f"lanes_fput|{_gpu()}|N={N}|qr={qr_every}|n={n_orbits}"
     if not refresh:

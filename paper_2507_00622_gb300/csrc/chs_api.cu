@@ -634,7 +634,7 @@ static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const
         !(s->sp.model == CHS_FPUT && p->integrator == CHS_RK4 &&
           chs::fput_lanes_per_orbit_supported(s->sp.n_dof, p->threads_per_orbit)))
         return fail(CHS_E_UNSUPPORTED,
-                    "threads_per_orbit: 0, or for the RK4 FPUT spectrum 1, 2, 4 at N = 4 and 2, 4 at N = 8");
+                    "threads_per_orbit: 0, or for the RK4 FPUT spectrum 1, 2, 4 at N = 4 and 2, 4, 8 at N = 8");
     if (s->sp.model == CHS_FPUT && p->block_threads != 0 && p->block_threads < 2 * s->sp.n_dof)
         return fail(CHS_E_INVALID, "FPUT: block_threads must be 0 or at least 2N");
     if (n < 0) return fail(CHS_E_INVALID, "n must be >= 0");

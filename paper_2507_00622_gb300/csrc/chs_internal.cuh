@@ -123,7 +123,7 @@ cudaError_t launch_fput_lyap(const SysPar& sp, const StepArgs& a, int64_t n, con
                              const int32_t* ic_status, double* lambda, int32_t* status,
                              cudaStream_t st);
 cudaError_t prepare_fput_lyap(int n_dof);  // sets the shared-memory attribute once
-// Short chains (N = 4, 8): four lanes per orbit (k_fput_lanes.cu).
+// Short chains (N = 4, 8): several lanes of one warp per orbit (k_fput_lanes.cu).
 bool fput_lyap_lanes_supported(int n_dof);
 bool fput_lanes_per_orbit_supported(int n_dof, int lanes);  // 0 (the default) always
 cudaError_t launch_fput_lyap_lanes(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,

@@ -1,26 +1,28 @@
 // fput_lyap_lanes.cuh -- the FPUT Lyapunov spectrum by periodic QR for N = 4, 8
-// (RK4, four lanes per orbit), as the work of one block: k_fput_lanes.cu
-// launches it block by block, the mixed-chain persistent kernel (k_fput_batch.cu)
-// runs it from a work queue.
+// (RK4, L lanes of one warp per orbit), as the work of one block:
+// k_fput_lanes.cu launches it block by block, the mixed-chain persistent kernel
+// (k_fput_batch.cu) runs it from a work queue.
 //
 // The method is the one of fput_lyap_rk4.cuh (RK4 on the chain, the 2N deviation
 // vectors advanced by the exact one-step RK4 propagator Phi, modified
 // Gram-Schmidt every qr_every steps and at the last step, S_j += ln |w_j|).
-// What changes is how an orbit is spread over threads (L lanes per orbit, four
-// by default; one or two at N = 4 and two at N = 8 are offered to the tuner,
-// and every choice gives the same results bit for bit: each bond, row and
-// column is computed by the same operations whichever lane owns it, and the
-// products that feed a sum are rounded explicitly (__dmul_rn), so that the
-// compiler cannot fuse them into a multiply-add in one instantiation and not
-// in another).  GB300 executes FP64
+// What changes is how an orbit is spread over threads: L lanes per orbit (four
+// at N = 4 and eight at N = 8 by default; one or two at N = 4 and two or four at
+// N = 8 are offered to the tuner), and every choice gives the same results bit
+// for bit: each bond, row and column is computed by the same operations
+// whichever lane owns it, and the products that feed a sum are rounded
+// explicitly (__dmul_rn), so that the compiler cannot fuse them into a
+// multiply-add in one instantiation and not in another.  GB300 executes FP64
 // instructions per warp at a fixed rate whatever the number of active lanes,
 // and each of an SM's four sub-partitions has its own FP64 unit, so the
 // kernel must (a) never execute FP64 work with idle lanes and (b) give every
-// sub-partition a warp.  An ensemble of 4096 orbits has 512 warps at four
-// lanes per orbit: at most one per sub-partition.  Lane `sub` of an orbit owns
-//   masses i0 .. i0 + M - 1 (i0 = sub * M, M = N / 4): their RK4 stages, the
+// sub-partition a warp, two where it can (a warp's own shared-memory loads and
+// address arithmetic then overlap the other warp's FP64 work).  An ensemble of
+// 4096 orbits has 512 warps at four lanes per orbit (N = 4) and 1024 at eight
+// (N = 8).  Lane `sub` of an orbit owns
+//   masses i0 .. i0 + M - 1 (i0 = sub * M, M = N / L): their RK4 stages, the
 //     bonds around them, and rows i0 .. i0 + M - 1 of Phi;
-//   columns sub + 4m of W (m < CPL = 2N / 4): their propagation, and their
+//   columns sub + L m of W (m < CPL = 2N / L): their propagation, and their
 //     part of the QR (columns interleaved over the lanes so that every lane
 //     keeps work until the last Gram-Schmidt column).
 // The orbit's lanes sit in one warp: neighbours' positions and bond
@@ -57,7 +59,7 @@ struct LaneCfg {
     static constexpr size_t SMEM = (size_t)(D * D + N * ROW) * G * sizeof(double);
 };
 
-// The work of one block of T threads: the G = T / 4 orbits vb * G .. vb * G +
+// The work of one block of T threads: the G = T / L orbits vb * G .. vb * G +
 // G - 1 (those below n), in the shared memory `smem` (LaneCfg::SMEM bytes).
 // Every thread of the block calls it; it synchronises only within warps.
 template <int N, int T, bool ALPHA0, int LL = 4>
@@ -186,45 +188,54 @@ __device__ __forceinline__ void fput_lyap_lanes_block(const StepArgs& a, const S
             for (int e = 0; e < ROW; ++e) cf[((i0 + k) * ROW + e) * G + g] = row[e];
         }
         __syncwarp();  // the rows of Phi are complete
-        // w <- Phi w for the lane's columns
+        // w <- Phi w for the lane's columns, AC at a time: each row's band
+        // coefficients are loaded once for the AC columns (the arithmetic of
+        // every column is the same whatever AC).  Two where the two columns'
+        // u and v fit the registers beside the rest (N = 4, or two columns per
+        // lane), else one.
+        constexpr int AC = (CPL % 2 == 0 && (N <= 4 || CPL <= 2)) ? 2 : 1;
 #pragma unroll 1
-        for (int m = 0; m < CPL; ++m) {
-            const int c = sub + m * L;
-            double u[N], v[N];
+        for (int m0 = 0; m0 < CPL; m0 += AC) {
+            double u[AC][N], v[AC][N];
 #pragma unroll
-            for (int i = 0; i < N; ++i) {
-                u[i] = WAT(i, c);
-                v[i] = WAT(N + i, c);
-            }
+            for (int q = 0; q < AC; ++q)
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    u[q][i] = WAT(i, sub + (m0 + q) * L);
+                    v[q][i] = WAT(N + i, sub + (m0 + q) * L);
+                }
 #pragma unroll
             for (int i = 0; i < N; ++i) {
                 double k[ROW];
 #pragma unroll
                 for (int e = 0; e < ROW; ++e) k[e] = cf[(i * ROW + e) * G + g];
-                double nu = 0.0, nv = 0.0;
-                bool first = true;
 #pragma unroll
-                for (int t = 0; t < 5; ++t) {  // A and C on u_{i-2..i+2}
-                    const int j = i - 2 + t;
-                    if (j < 0 || j >= N) continue;
-                    nu = first ? __dmul_rn(k[t], u[j]) : fma(k[t], u[j], nu);
-                    nv = first ? __dmul_rn(k[8 + t], u[j]) : fma(k[8 + t], u[j], nv);
-                    first = false;
-                }
+                for (int q = 0; q < AC; ++q) {
+                    double nu = 0.0, nv = 0.0;
+                    bool first = true;
 #pragma unroll
-                for (int t = 0; t < 3; ++t) {  // B on v_{i-1..i+1}
-                    const int j = i - 1 + t;
-                    if (j < 0 || j >= N) continue;
-                    nu = fma(k[5 + t], v[j], nu);
-                }
+                    for (int t = 0; t < 5; ++t) {  // A and C on u_{i-2..i+2}
+                        const int j = i - 2 + t;
+                        if (j < 0 || j >= N) continue;
+                        nu = first ? __dmul_rn(k[t], u[q][j]) : fma(k[t], u[q][j], nu);
+                        nv = first ? __dmul_rn(k[8 + t], u[q][j]) : fma(k[8 + t], u[q][j], nv);
+                        first = false;
+                    }
 #pragma unroll
-                for (int t = 0; t < 5; ++t) {  // D on v_{i-2..i+2}
-                    const int j = i - 2 + t;
-                    if (j < 0 || j >= N) continue;
-                    nv = fma(k[13 + t], v[j], nv);
+                    for (int t = 0; t < 3; ++t) {  // B on v_{i-1..i+1}
+                        const int j = i - 1 + t;
+                        if (j < 0 || j >= N) continue;
+                        nu = fma(k[5 + t], v[q][j], nu);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) {  // D on v_{i-2..i+2}
+                        const int j = i - 2 + t;
+                        if (j < 0 || j >= N) continue;
+                        nv = fma(k[13 + t], v[q][j], nv);
+                    }
+                    WAT(i, sub + (m0 + q) * L) = nu;
+                    WAT(N + i, sub + (m0 + q) * L) = nv;
                 }
-                WAT(i, c) = nu;
-                WAT(N + i, c) = nv;
             }
         }
 

@@ -1,6 +1,6 @@
 // k_fput_lanes.cu -- Lyapunov spectrum of short FPUT chains (N = 4, 8) by
-// periodic QR, four lanes per orbit, one launch per chain length; the method
-// and the layout are in fput_lyap_lanes.cuh.
+// periodic QR, several lanes of one warp per orbit, one launch per chain
+// length; the method and the layout are in fput_lyap_lanes.cuh.
 #include "fput_lyap_lanes.cuh"
 
 namespace chs {
@@ -84,7 +84,7 @@ bool fput_lanes_per_orbit_supported(int n_dof, int lanes)
 {
     if (lanes == 0) return true;
     if (n_dof == 4) return lanes == 1 || lanes == 2 || lanes == 4;
-    if (n_dof == 8) return lanes == 2 || lanes == 4;
+    if (n_dof == 8) return lanes == 2 || lanes == 4 || lanes == 8;
     return false;
 }
 
@@ -100,20 +100,22 @@ cudaError_t prepare_fput_lyap_lanes(int n_dof)
     case 8:
         err = prepare_nl<8, 4>();
         if (err == cudaSuccess) err = prepare_nl<8, 2>();
+        if (err == cudaSuccess) err = prepare_nl<8, 8>();
         break;
     }
     return err;
 }
 
-// Default: four lanes per orbit, blocks of two warps at N = 4 (16 orbits) and of
-// one warp at N = 8 (the faster on 4096-orbit ensembles: 2.06 against 2.14 ms per
-// 200 steps at N = 4, 7.34 against 7.36 at N = 8); the other lane counts and
-// block sizes are offered to the tuner.
+// Default: four lanes per orbit in blocks of two warps at N = 4 (16 orbits per
+// block), eight lanes (one mass, two columns each) in one-warp blocks at N = 8;
+// the faster on 4096-orbit ensembles (ms per 200 steps at QR every 10: N = 4
+// 2.06-2.09 with 4 lanes, 3.65 with 2; N = 8 5.51 with 8 lanes, 7.33 with 4).
+// The other lane counts and block sizes are offered to the tuner.
 cudaError_t launch_fput_lyap_lanes(const SysPar& sp, const StepArgs& a, int64_t n, const double* ics,
                                    const int32_t* ic_status, double* lambda, int32_t* status, cudaStream_t st)
 {
     if (n == 0) return cudaSuccess;
-    const int lanes = a.threads_per_orbit > 0 ? a.threads_per_orbit : 4;
+    const int lanes = a.threads_per_orbit > 0 ? a.threads_per_orbit : (sp.n_dof == 8 ? 8 : 4);
     if (sp.n_dof == 4) {
         switch (lanes) {
         case 4: return launch_nl<4, 4>(sp, a, n, ics, ic_status, lambda, status, st);
@@ -124,6 +126,7 @@ cudaError_t launch_fput_lyap_lanes(const SysPar& sp, const StepArgs& a, int64_t 
         switch (lanes) {
         case 4: return launch_nl<8, 4>(sp, a, n, ics, ic_status, lambda, status, st);
         case 2: return launch_nl<8, 2>(sp, a, n, ics, ic_status, lambda, status, st);
+        case 8: return launch_nl<8, 8>(sp, a, n, ics, ic_status, lambda, status, st);
         }
     }
     return cudaErrorInvalidValue;

@@ -57,10 +57,10 @@ def test_fput_lyapunov_block_size_is_bit_identical():
         S.close()
 
 
-@pytest.mark.parametrize("N,lanes", [(4, (1, 2, 4)), (8, (2, 4))])
+@pytest.mark.parametrize("N,lanes", [(4, (1, 2, 4)), (8, (2, 4, 8))])
 def test_fput_lyapunov_lanes_per_orbit_is_bit_identical(N, lanes):
-    """The short chains' kernel with 1, 2 or 4 lanes per orbit (N = 4) or 2 or 4
-    (N = 8), at every block size, FPUT-beta and FPUT-alpha+beta, a ragged last
+    """The short chains' kernel with 1, 2 or 4 lanes per orbit (N = 4) or 2, 4
+    or 8 (N = 8), at every block size, FPUT-beta and FPUT-alpha+beta, a ragged last
     block and a health check: identical exponents and statuses."""
     n = 45
     Q, P = normal_mode_draws(17 + N, N, n)
@@ -125,7 +125,7 @@ def test_fput_lanes_argument_checks():
     ics = torch.zeros((16, 4), dtype=torch.float64, device="cuda")
     lam = torch.empty((16, 4), dtype=torch.float64, device="cuda")
     sto = torch.empty(4, dtype=torch.int32, device="cuda")
-    for L in (1, 3, 8):
+    for L in (1, 3, 16):
         with pytest.raises(chs.ChsError) as e:
             chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, 10, qr_every=10, threads_per_orbit=L), 4, ics, None,
                                       lam, sto)
