@@ -819,7 +819,7 @@ def fput_result(args) -> dict:
         else:
             qr[N] = int(args.qr_every)
     dop = args.integrator == "dop853"
-    blk, lanes = {}, {}
+    blk, lanes, tuned = {}, {}, {}
     for N in Ns:
         lanes[N] = 0
         if dop:
@@ -828,9 +828,12 @@ def fput_result(args) -> dict:
             from paper_2507_00622_gb300 import autotune
             t = autotune.tune_fput_lanes(N, qr_every=qr[N], n_orbits=n)
             blk[N], lanes[N] = t["block_threads"], t["threads_per_orbit"]
+            tuned[N] = t
         elif args.block == "auto":
             from paper_2507_00622_gb300 import autotune
-            blk[N] = autotune.tune_fput_block(N, qr_every=qr[N])["block_threads"]
+            t = autotune.tune_fput_block(N, qr_every=qr[N])
+            blk[N] = t["block_threads"]
+            tuned[N] = t
         else:
             blk[N] = int(args.block)
     prms = {N: chs.params(0.05, args.chunk, qr_every=qr[N], sample_every=100,
@@ -884,6 +887,9 @@ def fput_result(args) -> dict:
                          "frac_of_fp64_peak": tf / mp["tflops"],
                          "frac_of_fp64_formula": tf / fp64_peak_tflops(2070.0), "qr_every": qr[N],
                          "block_threads": blk[N] or None, "threads_per_orbit": lanes[N] or None}
+        if N in tuned:  # the tuner's timings (s per run; "lanes x block" or block)
+            per_n[str(N)]["tuner"] = {"seconds": tuned[N]["seconds"], "steps": tuned[N]["steps"],
+                                      "n_orbits": tuned[N]["n_orbits"]}
     value = len(runs) * n * args.chunk * args.steps / (total_ms / 1e3)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
