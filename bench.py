@@ -425,7 +425,8 @@ def run_peaks(args):
     full = {"dfma": probe_rate(chs.PROBE_DFMA, sms * 4, 256, 1 << 17),
             "ffma": probe_rate(chs.PROBE_FFMA, sms * 4, 256, 1 << 21),
             "dsqrt": probe_rate(chs.PROBE_DSQRT, sms * 4, 256, 1 << 12),
-            "dmma": probe_rate(chs.PROBE_DMMA, sms * 4, 256, 1 << 14)}
+            "dmma": probe_rate(chs.PROBE_DMMA, sms * 4, 256, 1 << 14),
+            "dfma_dmma": probe_rate(chs.PROBE_DFMA_DMMA, sms * 4, 256, 1 << 15)}
     sweep = []
     for w in (1, 2, 3, 4, 6, 8, 12, 16, 32):
         r = probe_rate(chs.PROBE_DFMA, sms * w, 32, max(4096, (1 << 20) // w))
@@ -439,6 +440,9 @@ def run_peaks(args):
             "fp32_fma_tflops": full["ffma"]["ops_per_s"] / 1e12,
             "fp64_sqrt_per_s": full["dsqrt"]["ops_per_s"],
             "fp64_mma_m8n8k4_tflops": full["dmma"]["ops_per_s"] / 1e12,
+            # FMA and MMA interleaved in one kernel: the sum stays at either's rate
+            # when the two share the FP64 pipe
+            "fp64_fma_plus_mma_tflops": full["dfma_dmma"]["ops_per_s"] / 1e12,
             "fp64_formula_tflops": fp64_peak_tflops(mhz),
             "fp64_fma_lanes_per_sm_per_clock": full["dfma"]["ops_per_s"] / 2 / (sms * mhz * 1e6),
             "fp64_vs_warps_per_sm": sweep,

@@ -509,7 +509,10 @@ typedef enum {
     CHS_PROBE_DFMA_DEP = 2, /* FP64 fma, one dependent chain per thread */
     CHS_PROBE_FFMA = 3,     /* FP32 fma, 8 independent chains per thread */
     CHS_PROBE_DSQRT = 4,    /* FP64 sqrt (with one fma), 8 chains per thread */
-    CHS_PROBE_DMMA = 5      /* FP64 mma.sync m8n8k4, 8 accumulators per warp */
+    CHS_PROBE_DMMA = 5,     /* FP64 mma.sync m8n8k4, 8 accumulators per warp */
+    CHS_PROBE_DFMA_DMMA = 6 /* both at once: 4 fma chains per thread and 4 mma.sync
+                               accumulators per warp, interleaved (shows whether
+                               the two share a pipe) */
 } chs_probe_kind;
 
 /* Launches one probe kernel of n_blocks x n_threads threads (n_threads a
@@ -522,7 +525,8 @@ chs_status chs_peak_probe(int32_t kind, int32_t n_blocks, int32_t n_threads, int
                           void* stream);
 
 /* Operations one thread of chs_peak_probe performs: flops (FMA = 2) for the
- * FMA and MMA probes, square roots for CHS_PROBE_DSQRT; 0 for an unknown kind. */
+ * FMA and MMA probes (their sum for CHS_PROBE_DFMA_DMMA), square roots for
+ * CHS_PROBE_DSQRT; 0 for an unknown kind. */
 double chs_probe_ops_per_thread(int32_t kind, int64_t n_iter);
 
 /* The same jobs as chs_lyapunov_batch (Sec. Functionalities, Lyapunov item; the

@@ -33,7 +33,7 @@ EXPORTS = ("chs_create_system", "chs_destroy_system", "chs_system_dim", "chs_sec
            "chs_mlp_loss_grad", "chs_mlp_backward", "chs_mlp_adam", "chs_surrogate_decide",
            "chs_peak_probe", "chs_probe_ops_per_thread", "chs_check_params", "chs_last_error",
            "chs_version")
-PROBE_DFMA, PROBE_DFMA_DEP, PROBE_FFMA, PROBE_DSQRT, PROBE_DMMA = 1, 2, 3, 4, 5
+PROBE_DFMA, PROBE_DFMA_DEP, PROBE_FFMA, PROBE_DSQRT, PROBE_DMMA, PROBE_DFMA_DMMA = 1, 2, 3, 4, 5, 6
 
 
 class ChsError(RuntimeError):

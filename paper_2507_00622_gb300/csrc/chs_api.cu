@@ -714,7 +714,7 @@ chs_status chs_peak_probe(int32_t kind, int32_t n_blocks, int32_t n_threads, int
                           void* stream)
 {
     CHS_NVTX_RANGE();
-    if (kind < CHS_PROBE_DFMA || kind > CHS_PROBE_DMMA) return fail(CHS_E_INVALID, "unknown probe kind %d", kind);
+    if (kind < CHS_PROBE_DFMA || kind > CHS_PROBE_DFMA_DMMA) return fail(CHS_E_INVALID, "unknown probe kind %d", kind);
     if (n_blocks < 1 || n_blocks > 65535) return fail(CHS_E_INVALID, "n_blocks must be in 1..65535");
     if (n_threads < 32 || n_threads > 1024 || n_threads % 32 != 0)
         return fail(CHS_E_INVALID, "n_threads must be a multiple of 32 in 32..1024");

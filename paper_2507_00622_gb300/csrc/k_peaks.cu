@@ -12,6 +12,9 @@
 //                       rounded sqrt), kChains chains
 //   CHS_PROBE_DMMA      D <- A B + D by mma.sync m8n8k4 in FP64, kChains
 //                       independent accumulators per warp
+//   CHS_PROBE_DFMA_DMMA kMix FMA chains per thread and kMix MMA accumulators
+//                       per warp in one loop: if the two used separate pipes
+//                       their rates would add (on GB300 they do not)
 // The operation count per thread is chs_probe_ops_per_thread(kind, n_iter).
 #include "chs_internal.cuh"
 
@@ -103,6 +106,32 @@ __global__ void k_probe_dmma(int64_t n_iter, double a, double b, double* __restr
     sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+constexpr int kMix = 4;
+
+__global__ void k_probe_dfma_dmma(int64_t n_iter, double a, double b, double ma, double* __restrict__ sink)
+{
+    double x[kMix], d0[kMix], d1[kMix];
+#pragma unroll
+    for (int c = 0; c < kMix; ++c) {
+        x[c] = 1e-3 * threadIdx.x + c;
+        d0[c] = 1e-3 * threadIdx.x + c;
+        d1[c] = 0.5 * c;
+    }
+    const double av = ma * (1.0 + 1e-3 * (threadIdx.x & 31));
+#pragma unroll 1
+    for (int64_t it = 0; it < n_iter; ++it) {
+#pragma unroll
+        for (int c = 0; c < kMix; ++c) {
+            x[c] = fma(x[c], a, b);
+            mma_m8n8k4(d0[c], d1[c], av, ma);
+        }
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < kMix; ++c) s += x[c] + d0[c] + d1[c];
+    sink[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 
 cudaError_t launch_peak_probe(int kind, int n_blocks, int n_threads, int64_t n_iter, double* sink,
@@ -124,6 +153,9 @@ cudaError_t launch_peak_probe(int kind, int n_blocks, int n_threads, int64_t n_i
     case CHS_PROBE_DMMA:
         k_probe_dmma<<<n_blocks, n_threads, 0, st>>>(n_iter, 0.03, 0.03, sink);
         break;
+    case CHS_PROBE_DFMA_DMMA:
+        k_probe_dfma_dmma<<<n_blocks, n_threads, 0, st>>>(n_iter, 0.999999, 1e-6, 0.03, sink);
+        break;
     default:
         return cudaErrorInvalidValue;
     }
@@ -144,6 +176,8 @@ double probe_ops_per_thread(int kind, int64_t n_iter)
         return (double)kChains * (double)n_iter;  // square roots (each with one FMA)
     case CHS_PROBE_DMMA:
         return 2.0 * 8 * 8 * 4 * kChains * (double)n_iter / 32.0;  // flops per lane
+    case CHS_PROBE_DFMA_DMMA:
+        return (2.0 * kMix + 2.0 * 8 * 8 * 4 * kMix / 32.0) * (double)n_iter;
     }
     return 0.0;
 }

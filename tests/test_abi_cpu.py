@@ -105,6 +105,9 @@ def test_peak_probe_validates_before_cuda(lib):
     assert chs.chs_probe_ops_per_thread(chs.PROBE_DFMA, 1001) == 16 * 1004.0
     assert chs.chs_probe_ops_per_thread(chs.PROBE_DFMA_DEP, 1000) == 2000.0
     assert chs.chs_probe_ops_per_thread(chs.PROBE_DSQRT, 1000) == 8000.0
+    # 4 FMA chains (8 flops) and 4 MMAs per warp (4 x 512 flops / 32 lanes) per iteration
+    assert chs.chs_probe_ops_per_thread(chs.PROBE_DFMA_DMMA, 1000) == (8 + 64) * 1000.0
+    assert lib.chs_peak_probe(7, 1, 32, 10, None, None) == chs.CHS_E_INVALID
     # m8n8k4: 512 flops per MMA and warp, 8 MMAs per iteration, per lane
     assert chs.chs_probe_ops_per_thread(chs.PROBE_DMMA, 1000) == 512 * 8 * 1000 / 32
     assert chs.chs_probe_ops_per_thread(99, 1000) == 0.0
