@@ -3,8 +3,9 @@
 // mixed-chain persistent kernel (k_fput_batch.cu) runs it from a work queue.
 //
 // One orbit per d = 2N threads; a block of T = 32, 64 or 128 threads (at
-// least d) holds T / d orbits.  Thread l owns state component l and column l of the d x d matrix
-// W of deviation vectors, which lives in shared memory (128 KB at N = 64).
+// least d) holds T / d orbits.  Thread l owns state component l and, for the
+// propagation, column l of the d x d matrix W of deviation vectors, which lives
+// in shared memory (128 KB at N = 64; rows padded to 33 doubles at d = 32).
 //
 // Propagation of W uses the exact one-step propagator of classic RK4 applied
 // to the linear variational equation w' = J_s w, with J_s = [[0, I], [-H_s, 0]]
@@ -25,13 +26,18 @@
 // QR: modified Gram-Schmidt in the "dot products first" order: for column j
 // every column l >= j forms r_l = w_j . w_l (r_j = |w_j|^2), then each l > j
 // subtracts (r_l / r_j) w_j; the columns are scaled to unit length at the end
-// and S_j += ln |w_j| (so R_jj > 0).  Thread l works column l, except at
-// d = 128, where the orbit's Q = 4 warps split the rows instead: warp w takes
+// and S_j += ln |w_j| (so R_jj > 0).  Thread l works column l at d = 64.  At
+// d = 32 (one warp per orbit) lane 8b + p takes rows 8b .. 8b + 7 of the columns
+// p + 8m, and the four partial dot products of a column are joined by shuffles
+// (qr_warp32).  At d = 128 the orbit's Q = 4 warps split the rows: warp w takes
 // rows 32w..32w+31 of the columns lane + 32m (m < Q), and the Q partial dot
-// products of a column are summed in a fixed order from shared memory.  Every
-// warp then works while any column is left (with columns per thread, the warp
-// holding the last columns would do all d iterations alone while the others
-// wait at the barriers).
+// products of a column are summed in a fixed order from shared memory
+// (qr_split).  Every lane then works while its column group is left (with one
+// column per thread, the lanes holding the first columns would idle through
+// most pivots, and an idle lane costs an FP64 slot).  At N = 64 the library's
+// default is the 256-thread form of fput_lyap_n64.cuh (two threads per column,
+// the same arithmetic); this 128-thread body is the block size 128 and the
+// mixed-chain persistent kernel's.
 #pragma once
 
 #include <math.h>
