@@ -171,27 +171,44 @@ def train(X, label, target, *, epochs: int = 40, batch: int = 4096, lr: float = 
     return net
 
 
+CONFIDENCES = (0.9, 0.92, 0.94, 0.95, 0.96, 0.97, 0.98, 0.99, 0.995, 0.998, 0.999, 0.9995, 0.9999)
+
+
+def confidence_table(prob: np.ndarray, label: np.ndarray) -> dict:
+    """Per candidate confidence c: the fraction of samples decided (p >= c or
+    p <= 1 - c) and the fraction decided wrongly, both over all samples."""
+    pred = prob >= 0.5
+    out = {}
+    for c in CONFIDENCES:
+        dec = (prob >= c) | (prob <= 1 - c)
+        out[str(c)] = (float(dec.mean()), float(np.mean(dec & (pred != (label > 0.5)))))
+    return out
+
+
 def choose_confidence(prob: np.ndarray, label: np.ndarray, max_error: float) -> tuple[float, float, float]:
     """Smallest confidence c whose confident decisions (p >= c or p <= 1 - c) err
     on at most max_error of all samples; returns (c, decided fraction, error fraction)."""
-    best = (0.9999, 0.0, 0.0)
-    for c in (0.9, 0.95, 0.98, 0.99, 0.995, 0.998, 0.999, 0.9995, 0.9999):
-        dec = (prob >= c) | (prob <= 1 - c)
-        pred = prob >= 0.5
-        err = float(np.mean(dec & (pred != (label > 0.5))))
+    table = confidence_table(prob, label)
+    for c in CONFIDENCES:
+        frac, err = table[str(c)]
         if err <= max_error:
-            return c, float(dec.mean()), err
-    return best
+            return c, frac, err
+    return 0.9999, 0.0, 0.0
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--out", default=WEIGHTS)
-    ap.add_argument("--energies", type=int, default=64)
+    ap.add_argument("--energies", type=int, default=96)
     ap.add_argument("--side", type=int, default=128)
-    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--final-step", type=int, default=FINAL_STEP)
-    ap.add_argument("--max-error", type=float, default=0.002)
+    # The classification allows 0.5 % of a grid's valid cells to disagree with the
+    # plain form; about two thirds of the cells are still running at the decision,
+    # so wrong confident decisions on 0.3 % of those orbits use ~0.2 % of the cells,
+    # leaving the rest of the allowance to the fast form's own disagreement and to
+    # the difference between the validation energies and a grid's.
+    ap.add_argument("--max-error", type=float, default=0.003)
     args = ap.parse_args()
     torch.cuda.set_device(0)
     from . import build as cuda_build
@@ -217,7 +234,8 @@ def main():
     acc = float(np.mean((pv >= 0.5) == (lv > 0.5)))
     conf, frac, err = choose_confidence(pv, lv, args.max_error)
     meta = dict(train_orbits=int(n - nv), val_orbits=int(nv), val_accuracy=acc, confidence=conf,
-                val_decided_fraction=frac, val_error_fraction=err, generation_seconds=t_gen,
+                val_decided_fraction=frac, val_error_fraction=err, max_error=args.max_error,
+                val_by_confidence=confidence_table(pv, lv), epochs=args.epochs, generation_seconds=t_gen,
                 training_seconds=t_train, energies=[float(energies[0]), float(energies[-1])],
                 grid_side=args.side, final_step=args.final_step, decide_step=DECIDE_STEP,
                 chaotic_fraction=float(np.mean(label.cpu().numpy())))
