@@ -394,7 +394,10 @@ chs_status chs_indicators(chs_system s, const chs_params* p, const chs_ensemble*
  * ic_status may be NULL.  Supported: FPUT with N in {4, 8, 16, 32, 64} (the
  * vectors live in shared memory; RK4 propagates them by its exact one-step
  * propagator, DOP853 column by column with the stages in registers), and
- * HENON_HEILES, HARMONIC, INVERTED.  FP64 throughout.  For FPUT under RK4,
+ * HENON_HEILES, HARMONIC, INVERTED.  FP64 throughout.  For FPUT under DOP853
+ * the blocks are fixed (one warp of orbits for N <= 16, one orbit above) except
+ * at N = 64: 256 threads per orbit by default (0 or 256), the 128-thread form
+ * with 128, the same results.  For FPUT under RK4,
  * p->block_threads (0, or 32, 64, 128 and at least 2N; at N = 64 also 256)
  * sets the block size (block_threads / 2N orbits per block for N = 16, 32,
  * block_threads / threads_per_orbit at N = 4, 8; one orbit at N = 64, with two

@@ -625,10 +625,10 @@ static chs_status lyap_check(chs_system s, const chs_params* p, int64_t n, const
     if (p->vec_precision != CHS_VEC_FP64) return fail(CHS_E_UNSUPPORTED, "the Lyapunov path is FP64 only");
     if (p->integrator != CHS_RK4 && p->integrator != CHS_DOP853)
         return fail(CHS_E_INVALID, "integrator must be CHS_RK4 or CHS_DOP853");
-    const bool n64_wide = s->sp.model == CHS_FPUT && s->sp.n_dof == 64 && p->integrator == CHS_RK4;
+    const bool n64_wide = s->sp.model == CHS_FPUT && s->sp.n_dof == 64;
     if (p->block_threads != 0 && p->block_threads != 32 && p->block_threads != 64 && p->block_threads != 128 &&
         !(p->block_threads == 256 && n64_wide))
-        return fail(CHS_E_INVALID, "block_threads must be 0, 32, 64 or 128 (or 256 for the RK4 FPUT spectrum at N = 64)");
+        return fail(CHS_E_INVALID, "block_threads must be 0, 32, 64 or 128 (or 256 for the FPUT spectrum at N = 64)");
     if (p->clock_budget < 0) return fail(CHS_E_INVALID, "clock_budget must be >= 0 (0 = no limit)");
     if (p->threads_per_orbit != 0 &&
         !(s->sp.model == CHS_FPUT && p->integrator == CHS_RK4 &&

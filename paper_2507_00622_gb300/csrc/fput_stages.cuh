@@ -64,16 +64,25 @@ __device__ __forceinline__ double d2v(const Coef& fc, double r)
 // Phase 1 for component l of one orbit (every thread of the block calls it; one
 // barrier per stage).  xb: [2][2N] stage-state buffers; cs: [S][N + 1] stage
 // stiffnesses.  Returns x_l + h sum_s b_s F_s; with ERR the error sums
-// err5 = sum_s e5_s F_s and err3 = sum_s (b_s - b3_s) F_s (DOP853 only).
-template <int N, class Tab, bool ERR>
+// err5 = sum_s e5_s F_s and err3 = sum_s (b_s - b3_s) F_s (DOP853 only).  With
+// GUARD a thread whose `act` is false (a block wider than the orbit's 2N
+// threads) only meets the barriers and returns xi.
+template <int N, class Tab, bool ERR, bool GUARD = false>
 __device__ __forceinline__ double orbit_stages(const double xi, const double h, const int l, double* xb,
-                                               double* cs, const Coef& fc, double& e5, double& e3)
+                                               double* cs, const Coef& fc, double& e5, double& e3,
+                                               const bool act = true)
 {
     constexpr int D = 2 * N;
     double F[Tab::S] = {};
     double acc = 0.0, a5 = 0.0, a3 = 0.0;
     dp::static_for<0, Tab::S>([&](auto sc) {
         constexpr int s = decltype(sc)::value;
+        if constexpr (GUARD) {
+            if (!act) {
+                __syncthreads();
+                return;
+            }
+        }
         double sum = 0.0;
         dp::static_for<0, s>([&](auto jc) {
             constexpr int j = decltype(jc)::value;
@@ -119,6 +128,9 @@ __device__ __forceinline__ double orbit_stages(const double xi, const double h, 
     if constexpr (ERR) {
         e5 = a5;
         e3 = a3;
+    }
+    if constexpr (GUARD) {
+        if (!act) return xi;
     }
     return fma(h, acc, xi);
 }

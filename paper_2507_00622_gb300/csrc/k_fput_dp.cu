@@ -127,6 +127,80 @@ __device__ __forceinline__ void qr_step_split(double* slab, const int l, double&
     __syncthreads();
 }
 
+// The split Gram-Schmidt of qr_step_split run by 256 threads (two per column,
+// the wide N = 64 kernel below): warp w takes rows 32 (w % 4) .. 32 (w % 4) + 31
+// of the column groups m = w / 4 and w / 4 + 2 (columns lane + 32 m), the two
+// warps of a row block meeting at a named barrier before each pivot.  The same
+// partial dot products, summed in the same order, and the same updates as
+// qr_step_split: identical results.  Threads t < 128 (t = l) add ln R_ll to S.
+__device__ __forceinline__ void pair_sync(const int rb)
+{
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + rb) : "memory");
+}
+
+__device__ __forceinline__ void qr_step_split_wide(double* slab, const int t, double& S)
+{
+    constexpr int N = 64;
+    using Cfg = FputDpCfg<N>;
+    using Sl = FputDpSlab<N>;
+    constexpr int D = Cfg::D, WS = Cfg::WS, Q = D / 32;
+    double* W = slab + Sl::W;
+    double* P = slab + Sl::QP;
+    const int w = t / 32, lane = t % 32, rb = w % 4, ch = w / 4, r0 = 32 * rb;
+    double n2[2] = {1.0, 1.0};  // squared norms of the thread's two columns
+    double nl = 1.0;            // squared norm of column t (t < 128)
+    for (int j = 0; j < D; ++j) {
+        pair_sync(rb);  // rows of column j in this row block are final
+        double* Pb = P + (j & 1) * Q * D;
+        const double* wj = W + j * WS + r0;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = lane + 32 * (ch + 2 * u);
+            if (c >= j) {
+                const double* wc = W + c * WS + r0;
+                double a0 = 0.0, a1 = 0.0;
+#pragma unroll 4
+                for (int i = 0; i < 32; i += 2) {
+                    a0 = fma(wj[i], wc[i], a0);
+                    a1 = fma(wj[i + 1], wc[i + 1], a1);
+                }
+                Pb[rb * D + c] = a0 + a1;
+            }
+        }
+        __syncthreads();
+        double nj = Pb[j];
+#pragma unroll
+        for (int q = 1; q < Q; ++q) nj += Pb[q * D + j];
+        const double inv_nj = 1.0 / nj;  // one division per pivot, not per column
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = lane + 32 * (ch + 2 * u);
+            if (c > j) {
+                double r = Pb[c];
+#pragma unroll
+                for (int q = 1; q < Q; ++q) r += Pb[q * D + c];
+                const double cfac = -r * inv_nj;
+                double* wc = W + c * WS + r0;
+#pragma unroll 4
+                for (int i = 0; i < 32; ++i) wc[i] = fma(cfac, wj[i], wc[i]);
+            } else if (c == j) {
+                n2[u] = nj;
+            }
+        }
+        if (t == j) nl = nj;
+    }
+    if (t < D) S += 0.5 * log(nl);
+    __syncwarp();  // this warp's columns' rows were last written by this warp
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const double inv = rsqrt(n2[u]);
+        double* wc = W + (lane + 32 * (ch + 2 * u)) * WS + r0;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) wc[i] *= inv;
+    }
+    __syncthreads();
+}
+
 // Modified Gram-Schmidt of the orbit's W (thread l owns column l), when `mine`
 // is set for the orbit; every thread takes part in the barriers.  S += ln R_ll.
 // At N = 64 (one orbit per block, so `mine` is set whenever this runs) the
@@ -181,7 +255,7 @@ __device__ __forceinline__ void qr_step(double* slab, const int l, const bool mi
 }
 
 template <int N>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 1)
 k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double* __restrict__ ics,
                const int32_t* __restrict__ ic_status, double* __restrict__ lambda,
                int32_t* __restrict__ status_out)
@@ -250,9 +324,89 @@ k_fput_lyap_dp(const StepArgs a, const SysPar sp, const int64_t n, const double*
     }
 }
 
+// N = 64 with 256 threads per orbit (one orbit per block and per SM, as in
+// k_fput_lyap_dp<64>): two warps per sub-partition instead of one, so that one
+// warp's shared-memory traffic and barriers overlap the other's FP64 work.  The
+// orbit's stages run on threads t < 128 exactly as in k_fput_lyap_dp (the others
+// only meet the barriers); phase 2 spreads the 128 columns over 8 warps instead
+// of 4; the QR is qr_step_split_wide.  Every column, stage and dot product is
+// computed as in k_fput_lyap_dp<64>: identical results.
+constexpr int kDpWideThreads = 256;
+
+__global__ void __launch_bounds__(kDpWideThreads, 1)
+k_fput_lyap_dp_wide(const StepArgs a, const SysPar sp, const int64_t n, const double* __restrict__ ics,
+                    const int32_t* __restrict__ ic_status, double* __restrict__ lambda,
+                    int32_t* __restrict__ status_out)
+{
+    constexpr int N = 64;
+    using Cfg = FputDpCfg<N>;
+    using Sl = FputDpSlab<N>;
+    constexpr int D = Cfg::D, PER = Cfg::PER, WS = Cfg::WS;
+    extern __shared__ double smem[];
+    const int t = threadIdx.x, l = t % D, half = t / D;
+    const bool lead = t < D;
+    const int64_t o = blockIdx.x;
+    const bool valid = o < n;
+    double* slab = smem;
+    double* red = slab + Sl::CTL;
+
+    const fs::Coef fc = fs::coef_of(sp);
+    int32_t st = valid ? (ic_status ? ic_status[o] : CHS_ORBIT_OK) : CHS_ORBIT_FORBIDDEN;
+    double xi = (valid && lead) ? ics[(int64_t)l * n + o] : 0.0;
+
+    auto orbit_any = [&](bool pred) {
+        if (t == 0) red[1] = 0.0;
+        __syncthreads();
+        if (pred) red[1] = 1.0;
+        __syncthreads();
+        const bool r = red[1] != 0.0;
+        __syncthreads();
+        return r;
+    };
+    if (orbit_any(lead && !isfinite(xi)) && st == CHS_ORBIT_OK) st = CHS_ORBIT_NONFINITE;
+    if (st != CHS_ORBIT_OK) xi = 0.0;
+
+#pragma unroll 4
+    for (int i = 64 * half; i < 64 * half + 64; ++i) slab[Sl::W + l * WS + i] = (i == l) ? 1.0 : 0.0;
+    double S = 0.0;
+    __syncthreads();
+
+    const double h = a.dt;
+    int64_t until_qr = a.qr_every;
+    int64_t until = a.sample_every > 0 ? a.sample_every : -1;
+    const long long t_start = clock64();
+    for (int64_t step = 1; step <= a.n_steps; ++step) {
+        double e5, e3;
+        xi = fs::orbit_stages<N, fs::TabDop853, false, true>(xi, h, l, slab + Sl::XB, slab + Sl::CS, fc, e5, e3,
+                                                             lead);
+        __syncthreads();  // every stage stiffness is written
+        fs::columns<N, fs::TabDop853, 1, PER, WS, Sl::CS, false>(smem, D, [&](int, const double*) { return h; });
+        __syncthreads();  // W complete; stage stiffnesses free
+        if (--until_qr == 0 || step == a.n_steps) {
+            until_qr = a.qr_every;
+            qr_step_split_wide(slab, t, S);
+        }
+        if (--until == 0) {
+            until = a.sample_every;
+            if (orbit_any(lead && !(isfinite(xi) && isfinite(S))) && st == CHS_ORBIT_OK) st = CHS_ORBIT_NONFINITE;
+            // block-uniform: the orbit's threads stop together
+            if (a.clock_budget > 0 && __syncthreads_or(budget_spent(a, t_start))) {
+                if (st == CHS_ORBIT_OK) st = CHS_ORBIT_STEP_BUDGET;
+                break;
+            }
+        }
+    }
+    if (valid && lead) {
+        const double T = (double)a.n_steps * a.dt;
+        lambda[(int64_t)l * n + o] =
+            (st == CHS_ORBIT_OK) ? S / T : __longlong_as_double(0x7ff8000000000000LL);
+        if (l == 0) status_out[o] = st;
+    }
+}
+
 // Adaptive DOP 8(5): every orbit from t = 0 to ad.t_final with its own steps.
 template <int N>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 1)
 k_fput_lyap_adapt(const StepArgs a, const AdaptArgs ad, const SysPar sp, const int64_t n,
                   const double* __restrict__ ics, const int32_t* __restrict__ ic_status,
                   double* __restrict__ lambda, int32_t* __restrict__ status_out,
@@ -390,6 +544,10 @@ cudaError_t prepare_dp_n()
     if (err == cudaSuccess)
         err = cudaFuncSetAttribute(k_fput_lyap_adapt<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)FputDpCfg<N>::SMEM);
+    if constexpr (N == 64)
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(k_fput_lyap_dp_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)FputDpCfg<N>::SMEM);
     if (err == cudaSuccess) done[dev] = true;
     return err;
 }
@@ -401,6 +559,15 @@ cudaError_t fput_dp_n(const SysPar& sp, const StepArgs& a, int64_t n, const doub
     using Cfg = FputDpCfg<N>;
     const cudaError_t err = prepare_dp_n<N>();
     if (err != cudaSuccess) return err;
+    // N = 64: 256 threads per orbit by default (block_threads 0 or 256), the
+    // 128-thread form with block_threads 128; both give the same results
+    if constexpr (N == 64) {
+        if (a.block == 0 || a.block == kDpWideThreads) {
+            k_fput_lyap_dp_wide<<<blocks_for(n, 1), kDpWideThreads, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status,
+                                                                                  lambda, status);
+            return cudaGetLastError();
+        }
+    }
     k_fput_lyap_dp<N><<<blocks_for(n, Cfg::G), Cfg::THREADS, Cfg::SMEM, st>>>(a, sp, n, ics, ic_status,
                                                                              lambda, status);
     return cudaGetLastError();

@@ -107,8 +107,8 @@ def test_fput_n64_two_threads_per_vector_is_bit_identical():
         S.close()
 
 
-def test_fput_block_256_only_at_n64_rk4():
-    for N, integ in ((32, chs.RK4), (64, chs.DOP853)):
+def test_fput_block_256_only_at_n64():
+    for N, integ in ((32, chs.RK4), (32, chs.DOP853), (16, chs.RK4)):
         S = chs.System(chs.FPUT, N, (1.0, 0.0, 1.0))
         ics = torch.zeros((2 * N, 2), dtype=torch.float64, device="cuda")
         lam = torch.empty((2 * N, 2), dtype=torch.float64, device="cuda")
@@ -117,6 +117,32 @@ def test_fput_block_256_only_at_n64_rk4():
             chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, 10, qr_every=10, block_threads=256, integrator=integ),
                                       2, ics, None, lam, sto)
         assert e.value.code == chs.CHS_E_INVALID
+        S.close()
+
+
+def test_fput_dop853_n64_two_threads_per_vector_is_bit_identical():
+    """DOP853 at N = 64 with 256 threads per orbit (the default) against the
+    128-thread form: FPUT-alpha+beta, QR every 7 steps with a last partial
+    interval, health checks, one orbit made NONFINITE: identical exponents and
+    statuses."""
+    N, n = 64, 5
+    Q, P = normal_mode_draws(641, N, n)
+    ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(n, 0.1 * N))
+    ics[3, 2] = np.nan
+    ics = torch.from_numpy(ics).cuda()
+    for sp in ((1.0, 0.0, 1.0), (1.0, 0.25, 1.0)):
+        S = chs.System(chs.FPUT, N, sp)
+        outs = []
+        for b in (0, 256, 128):
+            lam = torch.empty((2 * N, n), dtype=torch.float64, device="cuda")
+            sto = torch.empty(n, dtype=torch.int32, device="cuda")
+            chs.chs_lyapunov_spectrum(S.h, chs.params(0.05, 45, qr_every=7, sample_every=20, block_threads=b,
+                                                      integrator=chs.DOP853), n, ics, None, lam, sto)
+            outs.append((lam.cpu().numpy(), sto.cpu().numpy()))
+        assert outs[0][1][2] == chs.ORBIT_NONFINITE and (outs[0][1] == chs.ORBIT_OK).sum() == n - 1
+        for lam, sto in outs[1:]:
+            np.testing.assert_array_equal(lam, outs[0][0])
+            np.testing.assert_array_equal(sto, outs[0][1])
         S.close()
 
 

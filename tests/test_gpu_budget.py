@@ -127,7 +127,7 @@ def test_tiny_budget_fput_ensembles(integ, adaptive):
     (HH, 2, chs.RK4, False), (HH, 2, chs.DOP853, False), (HH, 2, chs.DOP853, True),
     (chs.FPUT, 4, chs.RK4, False), (chs.FPUT, 8, chs.RK4, False), (chs.FPUT, 16, chs.RK4, False),
     (chs.FPUT, 64, chs.RK4, False),
-    (chs.FPUT, 8, chs.DOP853, False), (chs.FPUT, 8, chs.DOP853, True)])
+    (chs.FPUT, 8, chs.DOP853, False), (chs.FPUT, 8, chs.DOP853, True), (chs.FPUT, 64, chs.DOP853, False)])
 def test_tiny_budget_lyapunov(model, N, integ, adaptive):
     """Lyapunov runs stop at their first check with NaN exponents; an ample
     budget gives the exponents of a run without one."""
