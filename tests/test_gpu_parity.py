@@ -360,6 +360,24 @@ def test_fput_alpha_beta_lyapunov_matches_oracle(N):
     assert np.abs(g - r).max() < 1e-8
 
 
+@pytest.mark.parametrize("integ", ["rk4", "dop853"])
+@pytest.mark.parametrize("N", [4, 8, 16, 32, 64])
+def test_fput_lyapunov_single_orbit(N, integ):
+    """An ensemble of one orbit (one block whose other orbit slots and lanes are
+    empty) under RK4 and DOP853, FPUT-alpha+beta, QR every 7 steps with a last
+    partial interval: every exponent within 1e-8 of the oracle."""
+    Q, P = normal_mode_draws(500 + N, N, 1)
+    ics = O.fput_mode_ics(O.fput(N), Q, P, np.full(1, 0.1 * N))
+    gi, oi = (chs.DOP853, O.DOP853) if integ == "dop853" else (chs.RK4, O.RK4)
+    g, gs = _gpu_lyap(chs.FPUT, N, ics, chs.params(0.05, 60, qr_every=7, sample_every=20, integrator=gi),
+                      (1.0, 0.25, 1.0))
+    r, rs = O.lyapunov(O.fput(N, beta=1.0, alpha=0.25),
+                       O.params(0.05, 60, qr_every=7, sample_every=20, integrator=oi), ics)
+    np.testing.assert_array_equal(gs, rs)
+    assert rs[0] == chs.ORBIT_OK
+    assert np.abs(g - r).max() < 1e-8
+
+
 @pytest.mark.parametrize("N", [4, 8, 64])
 def test_fput_lyapunov_nonfinite_orbit(N):
     """A NaN in one component of one orbit (a component of the third of the
