@@ -497,7 +497,7 @@ typedef struct {
  * example of Sec. Examples) -- typically FPUT chains of different N, each a
  * differently shaped kernel -- as one CUDA graph whose branches run
  * concurrently, so that blocks of different chain lengths share the SMs (an
- * N = 64 block holds 143 KB of shared memory and leaves room for smaller
+ * N = 64 block holds 154 KB of shared memory and leaves room for smaller
  * ones).  Results are identical to separate chs_lyapunov_spectrum calls.  All
  * jobs must be on the current device; at most 16 jobs. */
 chs_status chs_lyapunov_batch(const chs_lyap_job* jobs, int32_t n_jobs, void* stream);
