@@ -749,7 +749,8 @@ def run_gpu(args):
                                         surrogate_agreement=fs["agreement"],
                                         surrogate_judge_sample=fs["judge_sample"],
                                         surrogate_judge_agreement=fs["judge_agreement"],
-                                        surrogate_confidence=fs["confidence"])
+                                        surrogate_confidence=fs["confidence"],
+                                        surrogate_second_decision=fs["second_decision"])
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -1074,8 +1075,11 @@ def classify_result(n_side: int, final_steps: int, confidence=None) -> dict:
         with np.load(SG.WEIGHTS) as z:
             meta = _json.loads(str(z["meta"]))
         sur = SG.Surrogate.load()
+        sur2 = SG.Surrogate.load_second()
         conf = float(confidence or meta.get("confidence", 0.999))
-        fs = CL.run_fast(g, surrogate=sur, confidence=conf, judge_fraction=0.02)
+        conf2 = float(meta.get("confidence2", 0.999))
+        fs = CL.run_fast(g, surrogate=sur, confidence=conf, judge_fraction=0.02, surrogate2=sur2,
+                         confidence2=conf2)
         # the judge: a 2 % random sample of the orbits the surrogate stopped,
         # re-integrated by the plain form to the final time on a second stream
         # beside the rest of the fast form; its cost is inside the surrogate
@@ -1086,8 +1090,12 @@ def classify_result(n_side: int, final_steps: int, confidence=None) -> dict:
             "seconds": fs.seconds, "orbit_steps": fs.orbit_steps, "confidence": conf,
             "speedup": plain.seconds / fs.seconds, "agreement": CL.agreement(plain, fs, plain.status),
             "stopped_by_surrogate": int(fs.extra["surrogate_stopped"]),
+            "second_decision": None if sur2 is None else {
+                "t": SG.DT * SG.DECIDE2_STEP, "confidence": conf2,
+                "stopped": int(fs.extra["surrogate2_stopped"])},
             "judge": "plain FP64 re-integration to the final time of a random 2 % of the orbits "
-                     "the surrogate stopped, on a second stream from the decision on",
+                     "the surrogate stopped (at either decision), on a second stream from the first "
+                     "decision on",
             "judge_sample": int(judge.size),
             "judge_orbit_steps": int(fs.extra.get("judge_orbit_steps", 0)),
             "judge_agreement": float(np.mean(fs.label[judge] == jl)) if judge.size else None,

@@ -129,50 +129,80 @@ def run_plain_cells(g: GridSpec, cells: np.ndarray) -> RunResult:
 
 
 def run_fast(g: GridSpec, chunk: int = 2000, surrogate=None, confidence: float = 0.999,
-             judge_fraction: float = 0.0, judge_seed: int = 0) -> RunResult:
+             judge_fraction: float = 0.0, judge_seed: int = 0, surrogate2=None,
+             confidence2: float = 0.999) -> RunResult:
     """FP32 frame, early exit, compacted graph chunks; with a surrogate, the orbits
     still running at the decision time (t = 500) whose final label it predicts
-    with probability >= confidence stop there and keep that label.
+    with probability >= confidence stop there and keep that label; with a second
+    surrogate the orbits still running at t = 2000 get a second decision.
 
-    With judge_fraction > 0 the plain form is the judge of the surrogate's
-    error: right after the decision a seeded random sample of that fraction of
-    the orbits the surrogate stopped is re-integrated by the plain form to the
-    final time, on a second stream beside the rest of the fast form.  The wall
-    time includes it; extra["judge_cells"] / extra["judge_label"] hold the sample
-    and its plain labels.  (Starting the judge at t = 0 on a random sample of
-    all cells measured slower: its orbits then share the SMs with the whole
-    fast form, not only with its undecided tail.)"""
+    With judge_fraction > 0 the plain form is the judge of the surrogates'
+    error: right after the first decision a seeded random sample of that
+    fraction of the orbits the surrogate stopped, and (with a second surrogate)
+    of that fraction of the orbits still undecided, is re-integrated by the
+    plain form to the final time, on a second stream beside the rest of the
+    fast form.  The undecided orbits of the sample that the second surrogate
+    stops at t = 2000 are a random sample of its decisions, judged with the
+    first ones: starting them at the first decision keeps the judge's run, one
+    orbit's 1e6 FP64 steps long, inside the first one's time.  The wall time
+    includes the judge; extra["judge_cells"] / extra["judge_label"] hold the
+    judged orbits and their plain labels.  (Starting the judge at t = 0 on a
+    random sample of all cells measured slower: its orbits then share the SMs
+    with the whole fast form, not only with its undecided tail.)"""
     from . import surrogate as sg
     S = chs.System(chs.HENON_HEILES, 2)
     ics, st = _grid(S, g)
     n = ics.shape[1]
     E = torch.full((n,), g.E, dtype=torch.float64, device="cuda")
-    on_decision = None
+    on_decision = on_decision2 = None
     if surrogate is not None and judge_fraction > 0.0:
         side = torch.cuda.Stream()
 
         def on_decision(status_dec, status):
-            stopped = torch.nonzero((status_dec == chs.ORBIT_OK) & (status != chs.ORBIT_OK)).squeeze(1)
-            stopped = stopped.cpu().numpy()
-            if stopped.size == 0:
-                return None
+            ok_dec = status_dec == chs.ORBIT_OK
+            stopped = torch.nonzero(ok_dec & (status != chs.ORBIT_OK)).squeeze(1).cpu().numpy()
             rng = np.random.default_rng(judge_seed)
-            cells = np.sort(rng.choice(stopped, max(1, int(judge_fraction * stopped.size)), replace=False))
+            pick = [rng.choice(stopped, max(1, int(judge_fraction * stopped.size)), replace=False)
+                    if stopped.size else np.zeros(0, dtype=np.int64)]
+            later = np.zeros(0, dtype=np.int64)
+            if surrogate2 is not None:
+                undecided = torch.nonzero(status == chs.ORBIT_OK).squeeze(1).cpu().numpy()
+                if undecided.size:
+                    later = np.sort(rng.choice(undecided, max(1, int(judge_fraction * undecided.size)),
+                                               replace=False))
+                pick.append(later)
+            cells = np.unique(np.concatenate(pick))
+            if cells.size == 0:
+                return None
             side.wait_stream(torch.cuda.current_stream())
-            return cells, start_plain_cells(g, ics, st, cells, side)
+            return cells, start_plain_cells(g, ics, st, cells, side), np.sort(pick[0]), later
+
+        if surrogate2 is not None:
+            def on_decision2(status_dec2, status):
+                # the orbits the second surrogate stopped (on the device, read after the run)
+                return (status_dec2 == chs.ORBIT_OK) & (status != chs.ORBIT_OK)
 
     run = sg.run_sampled(ics, st, k=g.k, seed=g.seed, final_step=g.n_steps, chunk=chunk,
-                         surrogate=surrogate, E=E, confidence=confidence, on_decision=on_decision)
+                         surrogate=surrogate, E=E, confidence=confidence, on_decision=on_decision,
+                         surrogate2=surrogate2, confidence2=confidence2, on_decision2=on_decision2)
     status = run["status"].cpu().numpy()
     n_exec = run["n_exec"].cpu().numpy()
-    extra = {"surrogate_stopped": int(np.sum(status == chs.ORBIT_PREDICTED_REGULAR))
-             + int(np.sum((status == chs.ORBIT_EARLY_CHAOTIC) & (n_exec == sg.DECIDE_STEP)))}
+    by_net = (status == chs.ORBIT_PREDICTED_REGULAR) | ((status == chs.ORBIT_EARLY_CHAOTIC)
+                                                       & ((n_exec == sg.DECIDE_STEP) | (n_exec == sg.DECIDE2_STEP)))
+    extra = {"surrogate_stopped": int(np.sum(by_net & (n_exec == sg.DECIDE_STEP))),
+             "surrogate2_stopped": int(np.sum(by_net & (n_exec == sg.DECIDE2_STEP))) if surrogate2 is not None else 0}
     steps = int(n_exec.sum())
     if run["on_decision"] is not None:
-        cells, jr = run["on_decision"]
+        cells, jr, first, later = run["on_decision"]
+        judged = first
+        if surrogate2 is not None and later.size:
+            stopped2 = run["on_decision2"].cpu().numpy()
+            judged = np.unique(np.concatenate([first, later[stopped2[later]]]))
+        jl_all = jr["label"].cpu().numpy()
+        pos = np.searchsorted(cells, judged)
         jn = jr["ensemble"].n_exec.cpu().numpy()
-        extra.update(judge_cells=cells, judge_label=jr["label"].cpu().numpy(), judge_orbit_steps=int(jn.sum()),
-                     judge_sampled=int(cells.size))
+        extra.update(judge_cells=judged, judge_label=jl_all[pos], judge_orbit_steps=int(jn.sum()),
+                     judge_sampled=int(judged.size), judge_run=int(cells.size))
         steps += int(jn.sum())
     return RunResult(run["label"].cpu().numpy(), status, n_exec, run["seconds"], steps, extra)
 

@@ -29,7 +29,16 @@ DT = 0.01
 SAMPLE_EVERY = 5_000        # SALI samples every 50 time units
 N_SAMPLES = 10              # ... up to the decision time t = 500
 DECIDE_STEP = SAMPLE_EVERY * N_SAMPLES
+SAMPLE2_EVERY = 20_000      # second decision: SALI samples every 200 time units
+DECIDE2_STEP = SAMPLE2_EVERY * N_SAMPLES  # ... up to t = 2000
 FINAL_STEP = 1_000_000      # final time 1e4
+
+
+def _first_series_row(step: int) -> int:
+    """Row of the first decision's series sampled at `step`, or -1."""
+    if step <= DECIDE_STEP and step % SAMPLE_EVERY == 0:
+        return step // SAMPLE_EVERY - 1
+    return -1
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "surrogate_weights.npz")
 
 
@@ -54,13 +63,20 @@ def grid_ics(energies, side: int):
 
 
 def run_sampled(ics, st, k: int = 2, seed: int = 1, final_step: int = FINAL_STEP, chunk: int = 2000,
-                surrogate=None, E=None, confidence: float = 0.999, on_decision=None):
+                surrogate=None, E=None, confidence: float = 0.999, on_decision=None, second: bool = False,
+                surrogate2=None, confidence2: float = 0.999, on_decision2=None):
     """Fast-form run with SALI samples up to the decision step.  Returns a dict of
     device tensors: series [10][n], ld_dec, status_dec (at the decision step),
     sali, label (final), n_exec, and the wall time (to the end of all device
     work, whatever stream it runs on).  on_decision(status_dec, status), when
     given, is called right after the surrogate's decision, before the run
-    continues; its return value comes back as "on_decision"."""
+    continues; its return value comes back as "on_decision".
+
+    With `second` (or a second surrogate), when the run ends after t = 2000, it
+    goes on sampling SALI every 200 time units to a second decision at t = 2000
+    (the samples at t = 200 and 400 are those of the first series): series2,
+    ld_dec2 and status_dec2 come back as well, surrogate2 decides there for the
+    orbits still running, and on_decision2 is called as on_decision is."""
     S = chs.System(chs.HENON_HEILES, 2)
     n = ics.shape[1]
     kw = dict(n_dev=k, ld_p=0.5, escape_r2=4.0, seed=seed, sali_threshold=1e-8,
@@ -85,25 +101,51 @@ def run_sampled(ics, st, k: int = 2, seed: int = 1, final_step: int = FINAL_STEP
     if surrogate is not None:
         surrogate.decide(series, ens.ld, ens.status, E, DT * DECIDE_STEP, confidence)
     side = on_decision(status_dec, ens.status) if on_decision is not None else None
-    chs.chs_integrate_compacted(S.h, chs.params(DT, final_step - step, step0=step, **kw), abi, chunk, work)
+    series2 = ld_dec2 = status_dec2 = side2 = None
+    if (second or surrogate2 is not None) and final_step > DECIDE2_STEP:
+        series2 = torch.empty((N_SAMPLES, n), dtype=torch.float64, device="cuda")
+        for i in range(N_SAMPLES):
+            target = (i + 1) * SAMPLE2_EVERY
+            row = _first_series_row(target)
+            if row >= 0:
+                series2[i].copy_(series[row])
+                continue
+            chs.chs_integrate_compacted(S.h, chs.params(DT, target - step, step0=step, **kw), abi, chunk, work)
+            step = target
+            chs.chs_indicators(S.h, chs.params(DT, 0, **kw), abi, sali=series2[i])
+        ld_dec2 = ens.ld.clone()
+        status_dec2 = ens.status.clone()
+        if surrogate2 is not None:
+            surrogate2.decide(series2, ens.ld, ens.status, E, DT * DECIDE2_STEP, confidence2)
+        side2 = on_decision2(status_dec2, ens.status) if on_decision2 is not None else None
+    if final_step > step:
+        chs.chs_integrate_compacted(S.h, chs.params(DT, final_step - step, step0=step, **kw), abi, chunk, work)
     chs.chs_indicators(S.h, chs.params(DT, 0, **kw), abi, sali=sali, label=label)
     torch.cuda.synchronize()  # the whole device: every stream's work is done
     sec = time.perf_counter() - t0
     return dict(series=series, ld_dec=ld_dec, status_dec=status_dec, sali=sali, label=label,
-                status=ens.status, n_exec=ens.n_exec, seconds=sec, on_decision=side)
+                status=ens.status, n_exec=ens.n_exec, seconds=sec, on_decision=side,
+                series2=series2, ld_dec2=ld_dec2, status_dec2=status_dec2, on_decision2=side2)
 
 
-def make_dataset(run, E):
+def make_dataset(run, E, second: bool = False, among=None):
     """Features (library kernel) and targets of the orbits still running at the
-    decision step whose final label is regular (0) or chaotic (1)."""
+    decision step (the second one with `second`) whose final label is regular
+    (0) or chaotic (1), restricted to the orbits where the boolean device mask
+    `among` is set when it is given.  Returns X, label, target and the orbits'
+    indices."""
     n = E.shape[0]
     X = torch.empty((12, n), dtype=torch.float32, device="cuda")
-    chs.chs_mlp_features(run["series"], N_SAMPLES, run["ld_dec"], DT * DECIDE_STEP, E, n, X)
+    series, ld, status, t = ((run["series2"], run["ld_dec2"], run["status_dec2"], DT * DECIDE2_STEP) if second
+                             else (run["series"], run["ld_dec"], run["status_dec"], DT * DECIDE_STEP))
+    chs.chs_mlp_features(series, N_SAMPLES, ld, t, E, n, X)
     lab = run["label"].long()
-    keep = (run["status_dec"] == chs.ORBIT_OK) & ((lab == 0) | (lab == 1))
+    keep = (status == chs.ORBIT_OK) & ((lab == 0) | (lab == 1))
+    if among is not None:
+        keep &= among
     target = torch.log10(torch.clamp(run["sali"], min=1e-20)).float() / 8.0
     idx = torch.nonzero(keep).squeeze(1)
-    return X[:, idx].contiguous(), lab[idx].float().contiguous(), target[idx].contiguous()
+    return X[:, idx].contiguous(), lab[idx].float().contiguous(), target[idx].contiguous(), idx
 
 
 class Surrogate:
@@ -118,8 +160,17 @@ class Surrogate:
         with np.load(path) as z:
             return cls(z["params"])
 
-    def save(self, path: str = WEIGHTS, meta: dict | None = None):
-        np.savez(path, params=self.master.cpu().numpy(), meta=json.dumps(meta or {}))
+    @classmethod
+    def load_second(cls, path: str = WEIGHTS) -> "Surrogate | None":
+        """The second decision's network (t = 2000), if the file holds one."""
+        with np.load(path) as z:
+            return cls(z["params2"]) if "params2" in z.files else None
+
+    def save(self, path: str = WEIGHTS, meta: dict | None = None, second: "Surrogate | None" = None):
+        arrays = dict(params=self.master.cpu().numpy(), meta=json.dumps(meta or {}))
+        if second is not None:
+            arrays["params2"] = second.master.cpu().numpy()
+        np.savez(path, **arrays)
 
     def decide(self, series, ld, status, E, t_decide: float, confidence: float) -> None:
         n = status.shape[0]
@@ -196,6 +247,27 @@ def choose_confidence(prob: np.ndarray, label: np.ndarray, max_error: float) -> 
     return 0.9999, 0.0, 0.0
 
 
+def _fit(X, label, target, epochs: int, max_error: float, seed: int = 0):
+    """Train on 90 % of the orbits, choose the confidence on the held-out 10 %."""
+    n = X.shape[1]
+    rng = np.random.default_rng(seed)
+    order = torch.from_numpy(rng.permutation(n)).cuda()
+    nv = n // 10
+    val, tr = order[:nv], order[nv:]
+    t1 = time.perf_counter()
+    net = train(X[:, tr].contiguous(), label[tr].contiguous(), target[tr].contiguous(), epochs=epochs)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    pv = net.probabilities(X[:, val].contiguous())
+    lv = label[val].cpu().numpy()
+    conf, frac, err = choose_confidence(pv, lv, max_error)
+    meta = dict(train_orbits=int(n - nv), val_orbits=int(nv), val_accuracy=float(np.mean((pv >= 0.5) == (lv > 0.5))),
+                confidence=conf, val_decided_fraction=frac, val_error_fraction=err, max_error=max_error,
+                val_by_confidence=confidence_table(pv, lv), epochs=epochs, training_seconds=t_train,
+                chaotic_fraction=float(np.mean(label.cpu().numpy())))
+    return net, meta
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--out", default=WEIGHTS)
@@ -209,6 +281,11 @@ def main():
     # leaving the rest of the allowance to the fast form's own disagreement and to
     # the difference between the validation energies and a grid's.
     ap.add_argument("--max-error", type=float, default=0.003)
+    # The second decision (t = 2000) sees only the orbits the first one left
+    # undecided, about a seventh of a grid's valid cells: wrong decisions on
+    # 0.5 % of them cost ~0.07 % of the cells.
+    ap.add_argument("--max-error2", type=float, default=0.005)
+    ap.add_argument("--no-second", action="store_true", help="train the first decision's network only")
     args = ap.parse_args()
     torch.cuda.set_device(0)
     from . import build as cuda_build
@@ -217,29 +294,26 @@ def main():
     energies = 0.10 + (np.arange(args.energies) + 0.5) * (0.166 - 0.10) / args.energies
     ics, st, E = grid_ics(energies, args.side)
     t0 = time.perf_counter()
-    run = run_sampled(ics, st, final_step=args.final_step)
+    run = run_sampled(ics, st, final_step=args.final_step, second=not args.no_second)
     t_gen = time.perf_counter() - t0
-    X, label, target = make_dataset(run, E)
-    n = X.shape[1]
-    rng = np.random.default_rng(0)
-    order = torch.from_numpy(rng.permutation(n)).cuda()
-    nv = n // 10
-    val, tr = order[:nv], order[nv:]
-    t1 = time.perf_counter()
-    net = train(X[:, tr].contiguous(), label[tr].contiguous(), target[tr].contiguous(), epochs=args.epochs)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t1
-    pv = net.probabilities(X[:, val].contiguous())
-    lv = label[val].cpu().numpy()
-    acc = float(np.mean((pv >= 0.5) == (lv > 0.5)))
-    conf, frac, err = choose_confidence(pv, lv, args.max_error)
-    meta = dict(train_orbits=int(n - nv), val_orbits=int(nv), val_accuracy=acc, confidence=conf,
-                val_decided_fraction=frac, val_error_fraction=err, max_error=args.max_error,
-                val_by_confidence=confidence_table(pv, lv), epochs=args.epochs, generation_seconds=t_gen,
-                training_seconds=t_train, energies=[float(energies[0]), float(energies[-1])],
-                grid_side=args.side, final_step=args.final_step, decide_step=DECIDE_STEP,
-                chaotic_fraction=float(np.mean(label.cpu().numpy())))
-    net.save(args.out, meta)
+    X, label, target, idx = make_dataset(run, E)
+    net, meta = _fit(X, label, target, args.epochs, args.max_error)
+    meta.update(generation_seconds=t_gen, energies=[float(energies[0]), float(energies[-1])],
+                grid_side=args.side, final_step=args.final_step, decide_step=DECIDE_STEP)
+    net2 = None
+    if not args.no_second:
+        # the orbits the first network leaves undecided at its confidence are the
+        # second network's data, as they are its inputs in a classification run
+        p1 = net.probabilities(X)
+        undecided = (p1 < meta["confidence"]) & (p1 > 1.0 - meta["confidence"])
+        among = torch.zeros(E.shape[0], dtype=torch.bool, device="cuda")
+        among[idx[torch.from_numpy(undecided).cuda()]] = True
+        X2, label2, target2, _ = make_dataset(run, E, second=True, among=among)
+        net2, meta2 = _fit(X2, label2, target2, args.epochs, args.max_error2, seed=1)
+        meta2.update(decide_step=DECIDE2_STEP)
+        meta["second"] = meta2
+        meta["confidence2"] = meta2["confidence"]
+    net.save(args.out, meta, second=net2)
     print(json.dumps(meta))
 
 
